@@ -1,0 +1,409 @@
+#!/usr/bin/env python
+"""RT-CDF sort benchmark: GKeys/s and fraction of the 8n-byte HBM roofline.
+
+One step is one pass of the whole hot path (histogram, local-CDF/offset scan,
+output generation) over the sweep workload: twelve int32 arrays of n = 1e8
+keys with minVal = -1000, range sizes R in {2^7, 2^10, 2^14, 2^18} and the
+uniform / normal / all-equal shapes of the paper's evaluation.  Inputs are
+generated on the device by the seeded generator and stay resident in HBM;
+each array (400 MB) is larger than L2, so no flush is needed between steps.
+
+Prints one JSON line (rank 0).  ``--impl reference`` times the CPU oracle on
+the host cores instead (the reference arm of this comparison).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_SWEEP = 100_000_000
+MIN_SWEEP = -1000
+SWEEP_R = [1 << 7, 1 << 10, 1 << 14, 1 << 18]
+DIST_NAMES = ["uniform", "normal", "all_equal"]
+WORKLOAD = ("sweep: n=1e8 int32 keys per array, minVal=-1000, R in {2^7,2^10,2^14,2^18} x "
+            "{uniform, normal(mean minVal+R/2, sd R/8), all-equal(minVal+R/3)}; 12 arrays per step")
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            p = json.load(f)
+        return float(p["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def sweep_cases():
+    from paper_2609_00843_gb300 import gen
+    cases = []
+    for R in SWEEP_R:
+        for d, name in enumerate(DIST_NAMES):
+            cases.append(dict(R=R, dist=d, dist_name=name,
+                              seed=gen.derive_seed(1, d, R.bit_length() - 1)))
+    return cases
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "100"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def traffic_for(kernel: str, src_files, workload_key: str):
+    """DRAM bytes per launch from a committed ncu summary, if it was captured
+    from the current kernel source; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            table = json.load(f)
+    except Exception:
+        return None
+    h = hashlib.sha256()
+    for p in src_files:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    ent = table.get(kernel, {}).get(workload_key)
+    if not ent or ent.get("source_sha256") != h.hexdigest():
+        return None
+    return ent.get("dram_bytes_per_launch")
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the CPU oracle on the host cores, on the sweep workload."""
+    import numpy as np
+
+    import oracle
+    from paper_2609_00843_gb300 import gen
+    if rank != 0:
+        return 0
+    # Bounded sample per step: every array of the sweep at n_sample keys,
+    # sized so that warm-up + timed steps finish within a few minutes.
+    total_steps = args.steps + args.warmup
+    n_sample = int(max(1_000_000, min(N_SWEEP, 12_000_000 * 10 // max(1, total_steps))))
+    cases = sweep_cases()
+    inputs = [gen.keys_host(n_sample, MIN_SWEEP, c["R"], c["dist"], c["seed"]) for c in cases]
+    lib = oracle.load()
+    times = []
+    for step in range(total_steps):
+        t0 = time.perf_counter()
+        for c, a in zip(cases, inputs):
+            oracle.counting_sort(a, MIN_SWEEP, MIN_SWEEP + c["R"], lib)
+        dt = time.perf_counter() - t0
+        if step >= args.warmup:
+            times.append(dt)
+    keys = n_sample * len(cases)
+    t = sum(times) / len(times)
+    value = keys / t / 1e9
+    line = {
+        "metric": "sort throughput (GKeys/s) on the RT-CDF sweep",
+        "value": value, "unit": "GKeys/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "impl": "reference",
+        "config": {"workload": WORKLOAD, "n_per_array": n_sample, "arrays": len(cases)},
+        "cpu_baseline": {"value": value, "unit": "GKeys/s", "cores": 1, "kind": "oracle",
+                         "sample": f"12 sweep arrays at n={n_sample} keys each per step"},
+        "e2e": {"value": value, "unit": "GKeys/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+        "gpu_launches": 0,
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline_sweep(host_inputs, cases):
+    """The oracle, as it stands, on one pass over the 12 full-size arrays."""
+    import oracle
+    lib = oracle.load()
+    t0 = time.perf_counter()
+    for c, a in zip(cases, host_inputs):
+        oracle.counting_sort(a, MIN_SWEEP, MIN_SWEEP + c["R"], lib)
+    dt = time.perf_counter() - t0
+    keys = sum(a.size for a in host_inputs)
+    return {"value": keys / dt / 1e9, "unit": "GKeys/s", "cores": 1, "kind": "oracle",
+            "sample": f"one pass over the 12 sweep arrays (n=1e8 each, {keys} keys), "
+                      f"{dt:.1f} s single-threaded"}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    torch.cuda.set_device(local_rank)
+    dist_on = world > 1
+    if dist_on:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist_on:
+            torch.distributed.barrier()
+
+    from paper_2609_00843_gb300 import _build
+    if rank == 0 or not dist_on:
+        _build.build()
+    barrier()
+    from paper_2609_00843_gb300 import gen, rtcdf
+
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    cases = sweep_cases()
+    n = N_SWEEP
+    ins, outs = [], []
+    with torch.cuda.stream(stream):
+        for c in cases:
+            x = torch.empty(n, dtype=torch.int32, device="cuda")
+            seed = gen.derive_seed(c["seed"], rank) if rank else c["seed"]
+            gen.keys_device(x.data_ptr(), n, MIN_SWEEP, c["R"], c["dist"], seed, stream=sh)
+            ins.append(x)
+            outs.append(torch.empty(n, dtype=torch.int32, device="cuda"))
+    stream.synchronize()
+
+    R_max = max(SWEEP_R)
+    ws_bytes = rtcdf.rtcdf_workspace_size(R_max)
+    ws = torch.zeros(ws_bytes // 4 + 64, dtype=torch.int32, device="cuda")
+    # Four stage events per sort per timed step, so the timed region has no
+    # host synchronisation: before hist, after hist, after scan, after fill.
+    nsteps = args.steps
+    evs = [[[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in cases]
+           for _ in range(nsteps)]
+    for per_step in evs:
+        for quad in per_step:
+            for e in quad:
+                e.record(stream)  # creates the underlying cudaEvent_t
+    stream.synchronize()
+    dbgs = []
+    for per_step in evs:
+        row = []
+        for quad in per_step:
+            d = rtcdf.Debug()
+            for j in range(4):
+                d.stage_events[j] = quad[j].cuda_event
+            row.append(d)
+        dbgs.append(row)
+
+    def step(dbg_row):
+        for i, c in enumerate(cases):
+            rc = rtcdf.rtcdf_sort_ex(ins[i].data_ptr(), outs[i].data_ptr(), n, MIN_SWEEP,
+                                     MIN_SWEEP + c["R"], None, ws.data_ptr(), ws_bytes,
+                                     dbg_row[i] if dbg_row is not None else None, sh)
+            if rc != rtcdf.OK:
+                raise rtcdf.RtcdfError(rc, "rtcdf_sort_ex")
+
+    # Warm-up: W steps plus about half a second of load so clocks settle.
+    for _ in range(args.warmup):
+        step(None)
+    stream.synchronize()
+    t_end = time.time() + 0.5
+    while time.time() < t_end:
+        step(None)
+        stream.synchronize()
+    rc, bits = rtcdf.rtcdf_ws_status_get(ws.data_ptr(), sh)
+    if rc != rtcdf.OK:
+        raise rtcdf.RtcdfError(rc, "device status after warm-up")
+
+    sampler = ClockSampler(local_rank)
+    sampler.start()
+    time.sleep(0.3)
+    t0 = torch.cuda.Event(enable_timing=True)
+    t1 = torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    t0.record(stream)
+    for k in range(nsteps):
+        step(dbgs[k])
+    t1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    time.sleep(0.1)
+    clocks = sampler.stop()
+    total_ms = t0.elapsed_time(t1)
+    if dist_on:
+        tt = torch.tensor([total_ms], device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        total_ms = float(tt.item())
+    rc, bits = rtcdf.rtcdf_ws_status_get(ws.data_ptr(), sh)
+    if rc != rtcdf.OK:
+        raise rtcdf.RtcdfError(rc, "device status after timed region")
+
+    stage_ms = [[0.0, 0.0, 0.0] for _ in cases]
+    per_case_ms = [0.0 for _ in cases]
+    for k in range(nsteps):
+        for i in range(len(cases)):
+            e = evs[k][i]
+            for j in range(3):
+                stage_ms[i][j] += e[j].elapsed_time(e[j + 1])
+            per_case_ms[i] += e[0].elapsed_time(e[3])
+    sort_ms = total_ms / nsteps  # whole step, max over ranks
+    keys_per_step = n * len(cases) * world
+    value = keys_per_step / (sort_ms * 1e-3) / 1e9
+
+    hbm, peak_kind = peaks()
+    per_config = []
+    for i, c in enumerate(cases):
+        ms = per_case_ms[i] / nsteps
+        per_config.append({"R": c["R"], "dist": c["dist_name"], "ms": round(ms, 5),
+                           "GKeys_s": round(n / (ms * 1e-3) / 1e9, 2),
+                           "frac_8n_roofline": round(8 * n / (ms * 1e-3) / 1e9 / hbm, 4),
+                           "hist_ms": round(stage_ms[i][0] / nsteps, 5),
+                           "scan_ms": round(stage_ms[i][1] / nsteps, 5),
+                           "fill_ms": round(stage_ms[i][2] / nsteps, 5)})
+    hist_total = sum(s[0] for s in stage_ms)
+    fill_total = sum(s[2] for s in stage_ms)
+    launches = len(cases) * nsteps
+    if hist_total >= fill_total:
+        kname, ktime = "hist_kernel", hist_total
+        ksrc = ["paper_2609_00843_gb300/csrc/hist.cu", "paper_2609_00843_gb300/csrc/rtcdf_internal.h"]
+    else:
+        kname, ktime = "fill_kernel", fill_total
+        ksrc = ["paper_2609_00843_gb300/csrc/fill.cu", "paper_2609_00843_gb300/csrc/rtcdf_internal.h"]
+    avg_launch_s = ktime / launches * 1e-3
+    achieved = 4 * n / avg_launch_s / 1e9  # algorithmic: 4n bytes read (hist) or written (fill)
+    roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
+                "frac": round(achieved / hbm, 4),
+                "traffic": traffic_for(kname, ksrc, "sweep_n1e8"),
+                "kernel": kname, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
+                "algorithmic_bytes_per_launch": 4 * n}
+    whole = {"achieved_8n_GBs": round(8 * n * len(cases) / (sort_ms * 1e-3) / 1e9, 1)}
+    whole["frac_8n_roofline"] = round(whole["achieved_8n_GBs"] / hbm, 4)
+
+    line = {
+        "metric": "sort throughput (GKeys/s) on the RT-CDF sweep; fraction of 8n-byte HBM roofline per R",
+        "value": round(value, 2), "unit": "GKeys/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(sort_ms, 4), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int32", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_per_array": n, "arrays": len(cases),
+                   "l2": "inputs larger than L2 (400 MB per array), no flush",
+                   "parallelism": f"replicas x{world} (independent arrays per GPU)"},
+        "roofline": roofline,
+        "whole_sort_roofline": whole,
+        "per_config": per_config,
+        "clocks": clocks,
+        "gpu_launches": 3 * len(cases) * args.steps,
+        "timed_region_ms": round(total_ms, 3),
+    }
+
+    # End to end through the C ABI: pinned host input -> device -> sort -> host.
+    if not args.no_e2e:
+        pin_in = [torch.empty(n, dtype=torch.int32, pin_memory=True) for _ in cases]
+        for p, x in zip(pin_in, ins):
+            p.copy_(x.cpu())
+        pin_out = torch.empty(n, dtype=torch.int32, pin_memory=True)
+        dev_in = torch.empty(n, dtype=torch.int32, device="cuda")
+        dev_out = torch.empty(n, dtype=torch.int32, device="cuda")
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                for i, c in enumerate(cases):
+                    dev_in.copy_(pin_in[i], non_blocking=True)
+                    rc = rtcdf.rtcdf_sort(dev_in.data_ptr(), dev_out.data_ptr(), n, MIN_SWEEP,
+                                          MIN_SWEEP + c["R"], sh)
+                    if rc != rtcdf.OK:
+                        raise rtcdf.RtcdfError(rc, "rtcdf_sort")
+                    pin_out.copy_(dev_out, non_blocking=True)
+
+        e2e_step()
+        stream.synchronize()
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for _ in range(args.e2e_steps):
+            e2e_step()
+        a1.record(stream)
+        stream.synchronize()
+        e_ms = a0.elapsed_time(a1) / args.e2e_steps
+        line["e2e"] = {"value": round(n * len(cases) * world / (e_ms * 1e-3) / 1e9, 3),
+                       "unit": "GKeys/s", "h2d_bytes_per_step": 4 * n * len(cases),
+                       "d2h_bytes_per_step": 4 * n * len(cases), "ms_per_step": round(e_ms, 3)}
+        del pin_in, pin_out
+
+    if rank == 0 and not args.no_cpu_baseline:
+        host = [x.cpu().numpy() for x in ins]
+        line["cpu_baseline"] = cpu_baseline_sweep(host, cases)
+
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist_on:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

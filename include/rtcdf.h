@@ -1,0 +1,165 @@
+/*
+ * rtcdf.h -- C ABI of librtcdf, a GB300 (sm_103a) implementation of
+ * Range-Tiled CDF sort (RT-CDF) from "Shared-Memory Range-Tiled CDF Sort for
+ * Small-Range Integer Keys on GPUs" (Ando, Takase, Fujimoto, Wada).
+ *
+ * Problem (Section 2.1): sort n int32 keys that all lie in a known range
+ * [minVal, maxVal) of size R = maxVal - minVal into nondecreasing order.  The
+ * sort is unstable; for keys alone every correct output is the same array, so
+ * results are bit-exact.
+ *
+ * Method (Section 3, Algorithms 4-7): the value range is cut into tiles of at
+ * most T values; each tile's histogram is built in shared memory (Algorithm 5),
+ * prefix-summed into a local CDF, offset by the number of smaller keys
+ * (Algorithm 6), and the output is generated from the local CDFs alone
+ * (Algorithm 7) -- the input is never rescanned after the histogram.
+ *
+ * Conventions for every entry point
+ *  - Pointers named `in`, `out`, `workspace` are DEVICE pointers (cudaMalloc,
+ *    torch CUDA tensors, ...) on the current CUDA device; the caller owns them.
+ *  - `in` and `out` must be 4-byte aligned; any further alignment is handled.
+ *    `in == out` (in-place) is allowed because output generation never reads
+ *    the input; any other overlap is rejected with RTCDF_ERR_INVALID_ARG.
+ *  - Calls are asynchronous and ordered on `stream` (0 = legacy default
+ *    stream).  Errors detectable on the host return immediately and enqueue
+ *    nothing.  Errors found by the device (a key outside [minVal, maxVal), a
+ *    bounded wait that ran out) are recorded in a device status word that
+ *    rtcdf_status_get / rtcdf_ws_status_get read; `out` is then unspecified.
+ *  - minVal >= INT32_MIN and maxVal <= 2^31 (the range lies in the int32 key
+ *    space), 1 <= R <= RTCDF_MAX_R, n < 2^32.  n == 0 returns RTCDF_OK.
+ *  - No entry point synchronizes the device except rtcdf_status_get /
+ *    rtcdf_ws_status_get and first-use workspace growth outside stream
+ *    capture (which only orders on `stream`).
+ */
+#ifndef RTCDF_H
+#define RTCDF_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct CUstream_st *rtcdf_stream_t; /* same handle as cudaStream_t */
+
+typedef enum {
+    RTCDF_OK = 0,
+    RTCDF_ERR_INVALID_ARG = 1,      /* null pointer, misalignment, overlap, bad size */
+    RTCDF_ERR_RANGE = 2,            /* R <= 0, R > RTCDF_MAX_R, or range outside int32 */
+    RTCDF_ERR_KEY_OUT_OF_RANGE = 3, /* device status: a key outside [minVal, maxVal) */
+    RTCDF_ERR_CUDA = 4,             /* a CUDA runtime call failed */
+    RTCDF_ERR_NO_MEMORY = 5,        /* workspace allocation failed or too small */
+    RTCDF_ERR_TIMEOUT = 6           /* device status: a bounded wait gave up */
+} rtcdf_status;
+
+/* Device status bits reported by rtcdf_status_get / rtcdf_ws_status_get. */
+#define RTCDF_DEV_KEY_OUT_OF_RANGE 0x1
+#define RTCDF_DEV_TIMEOUT 0x2
+
+/* Largest supported range size.  Ranges wider than one shared-memory tile are
+ * handled by several tiles (Algorithm 4, m = ceil(R / T) > 1). */
+#define RTCDF_MAX_R (1LL << 24)
+
+/*
+ * rtcdf_sort -- sort n keys of `in` into `out` (Algorithm 4 end to end).
+ * Uses a workspace owned by the library, cached per (device, stream) and grown
+ * on demand (stream-ordered allocation; inside CUDA graph capture it must
+ * already be large enough, see rtcdf_reserve).  Calls on the same stream reuse
+ * one workspace; calls on different streams never share one.
+ */
+rtcdf_status rtcdf_sort(const int32_t *in, int32_t *out, uint64_t n, int64_t minVal,
+                        int64_t maxVal, rtcdf_stream_t stream);
+
+/*
+ * rtcdf_reserve -- grow the library-owned workspace of `stream` so that any
+ * later rtcdf_sort with range size <= max_R runs without allocating (needed
+ * before capturing rtcdf_sort into a CUDA graph).
+ */
+rtcdf_status rtcdf_reserve(int64_t max_R, rtcdf_stream_t stream);
+
+/*
+ * Workspace sizing for the caller-owned variant.  The workspace holds the
+ * histogram H[0..R-1] (Algorithm 5), the run table derived from the local CDFs
+ * and tile offsets (Algorithm 6), the scan's lookback state and the status
+ * word: O(R) bytes, independent of n (Section 3.2: workspace O(R + m)).
+ */
+rtcdf_status rtcdf_workspace_size(int64_t R, size_t *bytes);
+
+/*
+ * rtcdf_sort_ws -- rtcdf_sort with a caller-owned device workspace of
+ * `ws_bytes` >= rtcdf_workspace_size(R).  No allocation happens inside, so the
+ * call can be captured in a CUDA graph.  The workspace must be zero-filled
+ * before its first use (cudaMemsetAsync(workspace, 0, ws_bytes, stream));
+ * every call leaves it zero-filled again except for the status word.  Calls
+ * that share one workspace must be ordered (same stream or events).
+ */
+rtcdf_status rtcdf_sort_ws(const int32_t *in, int32_t *out, uint64_t n, int64_t minVal,
+                           int64_t maxVal, void *workspace, size_t ws_bytes,
+                           rtcdf_stream_t stream);
+
+/*
+ * rtcdf_status_get -- wait for `stream`, then return in *device_status the
+ * RTCDF_DEV_* bits recorded by sorts on the library-owned workspace of
+ * `stream` since the last read, and clear them.  Returns
+ * RTCDF_ERR_KEY_OUT_OF_RANGE / RTCDF_ERR_TIMEOUT when a bit is set.
+ */
+rtcdf_status rtcdf_status_get(rtcdf_stream_t stream, int32_t *device_status);
+
+/* Same for a caller-owned workspace. */
+rtcdf_status rtcdf_ws_status_get(void *workspace, rtcdf_stream_t stream,
+                                 int32_t *device_status);
+
+/* Human-readable name of a status code (static string). */
+const char *rtcdf_status_str(rtcdf_status status);
+
+/*
+ * Launch parameters of one sort (Section 3.3, Table "Kernel launch
+ * configurations"): tile width T (values per range tile, m = ceil(R / T)),
+ * histogram CTAs per tile (g_hist), threads per histogram CTA, output CTAs.
+ * Zero in a field means "choose automatically".
+ */
+typedef struct {
+    int32_t tile_width;      /* T; 0 = largest that fits shared memory */
+    int32_t hist_ctas_per_tile;
+    int32_t hist_threads;    /* 256, 512 or 1024 */
+    int32_t fill_ctas;
+    int32_t fill_threads;    /* 256, 512 or 1024 */
+    int32_t reserved[3];
+} rtcdf_params;
+
+/* The parameters rtcdf_sort would use for (n, R) on the current device. */
+rtcdf_status rtcdf_plan(uint64_t n, int64_t R, rtcdf_params *params);
+
+/*
+ * rtcdf_sort_ex -- rtcdf_sort_ws with explicit launch parameters (for tuning
+ * and tests).  `params` may be NULL.  When `debug` is non-NULL it receives
+ * device copies of the intermediates (device pointers, caller-owned):
+ *   debug->tile_hist[0..R-1]  H after the histogram step (Algorithm 5)
+ *   debug->cdf[0..R-1]        O[t] + local CDF, i.e. the inclusive CDF
+ *   debug->tile_offset[0..m-1] O (Algorithm 6)
+ * Any of the three may be NULL, as may each stage event.
+ */
+typedef struct {
+    uint32_t *tile_hist;
+    uint32_t *cdf;
+    uint32_t *tile_offset;
+    /* Optional cudaEvent_t handles (caller-created, may be NULL) recorded on
+     * `stream` before the histogram kernel, after it, after the scan and after
+     * the output kernel: per-stage CUDA-event timing on the launching stream. */
+    void *stage_events[4];
+} rtcdf_debug;
+
+rtcdf_status rtcdf_sort_ex(const int32_t *in, int32_t *out, uint64_t n, int64_t minVal,
+                           int64_t maxVal, const rtcdf_params *params, void *workspace,
+                           size_t ws_bytes, const rtcdf_debug *debug,
+                           rtcdf_stream_t stream);
+
+/* Library version string. */
+const char *rtcdf_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RTCDF_H */

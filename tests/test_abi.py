@@ -1,0 +1,90 @@
+"""C-ABI checks that need no GPU: the libraries load, export every declared
+symbol, and reject bad arguments on the host before touching the device."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2609_00843_gb300 import _build, rtcdf
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+
+
+def _declared(header):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    return sorted(set(re.findall(r"^\s*(?:const\s+)?\w+\s*\*?\s*(rtcdf_\w+)\s*\(", text, re.M)))
+
+
+def test_rtcdf_exports_every_declared_symbol():
+    names = _declared("rtcdf.h")
+    assert "rtcdf_sort" in names and "rtcdf_sort_ws" in names and len(names) >= 10
+    lib = ctypes.CDLL(rtcdf.LIB_PATH)
+    for name in names:
+        assert hasattr(lib, name), name
+    assert names == rtcdf.declared_functions()
+
+
+def test_gen_exports_every_declared_symbol():
+    from paper_2609_00843_gb300 import gen
+    lib = ctypes.CDLL(gen.lib_path())
+    for name in _declared("rtcdf_gen.h"):
+        assert hasattr(lib, name), name
+
+
+def test_version_and_status_strings():
+    assert "sm_103a" in rtcdf.rtcdf_version()
+    for code in range(7):
+        assert rtcdf.rtcdf_status_str(code) != "unknown status"
+    assert rtcdf.rtcdf_status_str(99) == "unknown status"
+
+
+def test_workspace_size_is_linear_in_R_and_independent_of_n():
+    s1 = rtcdf.rtcdf_workspace_size(128)
+    s2 = rtcdf.rtcdf_workspace_size(1 << 18)
+    assert 0 < s1 < s2
+    # O(R): three 4-byte arrays of R entries plus small fixed regions.
+    assert 12 * (1 << 18) <= s2 < 12 * (1 << 18) + 64 * 1024
+    with pytest.raises(rtcdf.RtcdfError):
+        rtcdf.rtcdf_workspace_size(0)
+    with pytest.raises(rtcdf.RtcdfError):
+        rtcdf.rtcdf_workspace_size(rtcdf.MAX_R + 1)
+
+
+@pytest.mark.parametrize("minVal,maxVal,code", [
+    (5, 5, rtcdf.ERR_RANGE),
+    (5, 4, rtcdf.ERR_RANGE),
+    (0, rtcdf.MAX_R + 1, rtcdf.ERR_RANGE),
+    (-(1 << 31) - 1, 0, rtcdf.ERR_RANGE),
+    ((1 << 31) - 2, (1 << 31) + 1, rtcdf.ERR_RANGE),
+])
+def test_range_errors_on_host(minVal, maxVal, code):
+    assert rtcdf.rtcdf_sort(4096, 8192, 10, minVal, maxVal, 0) == code
+
+
+def test_argument_errors_on_host():
+    # null pointers, misalignment, partial overlap, n >= 2^32 -- all rejected
+    # before any CUDA call, so they run without a GPU.
+    assert rtcdf.rtcdf_sort(0, 8192, 10, 0, 128, 0) == rtcdf.ERR_INVALID_ARG
+    assert rtcdf.rtcdf_sort(4096, 0, 10, 0, 128, 0) == rtcdf.ERR_INVALID_ARG
+    assert rtcdf.rtcdf_sort(4098, 8192, 10, 0, 128, 0) == rtcdf.ERR_INVALID_ARG
+    assert rtcdf.rtcdf_sort(4096, 4100, 10, 0, 128, 0) == rtcdf.ERR_INVALID_ARG
+    assert rtcdf.rtcdf_sort(4096, 8192, 1 << 32, 0, 128, 0) == rtcdf.ERR_INVALID_ARG
+    # n == 0 is a no-op
+    assert rtcdf.rtcdf_sort(0, 0, 0, 0, 128, 0) == rtcdf.OK
+    # caller workspace: null or misaligned workspace, too small
+    assert rtcdf.rtcdf_sort_ws(4096, 1 << 20, 10, 0, 128, 0, 1 << 20, 0) == rtcdf.ERR_INVALID_ARG
+    assert rtcdf.rtcdf_sort_ws(4096, 1 << 20, 10, 0, 128, 1 << 24 | 8, 1 << 20, 0) == rtcdf.ERR_INVALID_ARG
+    assert rtcdf.rtcdf_sort_ws(4096, 1 << 20, 10, 0, 128, 1 << 24, 16, 0) == rtcdf.ERR_NO_MEMORY
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(rtcdf, "_lib", None)
+    monkeypatch.setattr(rtcdf, "LIB_PATH", str(tmp_path / "nope.so"))
+    with pytest.raises(RuntimeError, match="no CPU fallback"):
+        rtcdf.rtcdf_sort(0, 0, 0, 0, 1, 0)
