@@ -155,6 +155,33 @@ rtcdf_status rtcdf_sort_ex(const int32_t *in, int32_t *out, uint64_t n, int64_t 
                            size_t ws_bytes, const rtcdf_debug *debug,
                            rtcdf_stream_t stream);
 
+/*
+ * rtcdf_sort_static -- the sort without any allocation, for callers that
+ * cannot allocate device memory: code running under another framework's
+ * memory manager that owns all device memory, serving loops whose memory
+ * budget is fixed up front, and hot paths that cannot afford the implicit
+ * synchronisation of an allocation.  The paper has no counterpart; this is an
+ * integration entry point.
+ *
+ * The caller passes `in` and `out` as for rtcdf_sort.  The scratch the sort
+ * needs beyond them lives in one array of RTCDF_STATIC_WS_BYTES bytes compiled
+ * into the library; every GPU that loads the library holds that array until
+ * the process exits.  Ranges wider than RTCDF_STATIC_MAX_R return
+ * RTCDF_ERR_RANGE.  Nothing is allocated and no allocating routine is called.
+ *
+ * The first call on a device looks up the array's device address (once per
+ * device, on the current device); make that first call before any CUDA graph
+ * capture.  All calls on a device share the array and it keeps what the last
+ * call left, so each call clears the part that must start at zero; calls that
+ * overlap on the GPU (unordered streams) race and must not be issued.  Device-
+ * detected errors (a key outside [minVal, maxVal)) are not reported by this
+ * entry point: the caller guarantees the range, as Section 2.1 assumes.
+ */
+#define RTCDF_STATIC_MAX_R (1LL << 16)
+#define RTCDF_STATIC_WS_BYTES (1u << 20)
+rtcdf_status rtcdf_sort_static(const int32_t *in, int32_t *out, uint64_t n, int64_t minVal,
+                               int64_t maxVal, rtcdf_stream_t stream);
+
 /* Library version string. */
 const char *rtcdf_version(void);
 

@@ -237,6 +237,31 @@ rtcdf_status read_status(void *ws, cudaStream_t s, int32_t *out) {
 
 }  // namespace
 
+namespace rtcdf {
+
+// Sort in a workspace whose previous contents are unknown: the regions that
+// must start at zero (control block, lookback state, histogram) are cleared
+// on `s` first.  Used by rtcdf_sort_static.
+rtcdf_status sort_with_workspace(const int32_t *in, int32_t *out, uint64_t n, int64_t minVal,
+                                 int64_t maxVal, void *ws, size_t ws_bytes, cudaStream_t s) {
+    uint32_t R = 0;
+    rtcdf_status st = check_range(minVal, maxVal, &R);
+    if (st) return st;
+    if (n == 0) return RTCDF_OK;
+    st = check_args(in, out, n);
+    if (st) return st;
+    if (!ws || ws_bytes < ws_required(R)) return RTCDF_ERR_NO_MEMORY;
+    const WsLayout L = ws_layout(R, ws_bytes);
+    const size_t zero_bytes = L.hist + (size_t)L.scan_chunks * kScanChunk * 4;
+    if (cudaMemsetAsync(ws, 0, zero_bytes, s) != cudaSuccess) return RTCDF_ERR_CUDA;
+    Plan pl;
+    st = make_plan(n, R, (uintptr_t)in, (uintptr_t)out, nullptr, &pl);
+    if (st) return st;
+    return run_pipeline(in, out, n, minVal, R, pl, ws, ws_bytes, nullptr, s);
+}
+
+}  // namespace rtcdf
+
 extern "C" {
 
 const char *rtcdf_version(void) { return "rtcdf 0.1 (sm_103a)"; }

@@ -26,6 +26,7 @@ ERR_TIMEOUT = 6
 DEV_KEY_OUT_OF_RANGE = 0x1
 DEV_TIMEOUT = 0x2
 MAX_R = 1 << 24
+STATIC_MAX_R = 1 << 16
 
 _lock = threading.Lock()
 _lib = None
@@ -78,9 +79,10 @@ def lib():
             L.rtcdf_status_get.argtypes = [vp, ctypes.POINTER(i32)]
             L.rtcdf_ws_status_get.argtypes = [vp, vp, ctypes.POINTER(i32)]
             L.rtcdf_plan.argtypes = [u64, i64, ctypes.POINTER(Params)]
+            L.rtcdf_sort_static.argtypes = [vp, vp, u64, i64, i64, vp]
             for f in ("rtcdf_sort", "rtcdf_sort_ws", "rtcdf_sort_ex", "rtcdf_reserve",
                       "rtcdf_workspace_size", "rtcdf_status_get", "rtcdf_ws_status_get",
-                      "rtcdf_plan"):
+                      "rtcdf_plan", "rtcdf_sort_static"):
                 getattr(L, f).restype = ctypes.c_int
             L.rtcdf_status_str.argtypes = [ctypes.c_int]
             L.rtcdf_status_str.restype = ctypes.c_char_p
@@ -103,6 +105,11 @@ def rtcdf_sort_ex(in_ptr, out_ptr, n, minVal, maxVal, params: Params | None, ws_
     p = ctypes.byref(params) if params is not None else None
     d = ctypes.byref(debug) if debug is not None else None
     return lib().rtcdf_sort_ex(in_ptr, out_ptr, n, minVal, maxVal, p, ws_ptr, ws_bytes, d, stream)
+
+
+def rtcdf_sort_static(in_ptr: int, out_ptr: int, n: int, minVal: int, maxVal: int,
+                      stream: int = 0) -> int:
+    return lib().rtcdf_sort_static(in_ptr, out_ptr, n, minVal, maxVal, stream)
 
 
 def rtcdf_reserve(max_R: int, stream: int = 0) -> int:
