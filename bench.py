@@ -186,6 +186,54 @@ def cpu_baseline_sweep(host_inputs, cases):
                       f"{dt:.1f} s single-threaded"}
 
 
+def cub_comparison(cases, ins, outs, n, stream, nsteps, ours_ms):
+    import ctypes
+
+    import torch
+    from paper_2609_00843_gb300 import _build
+    path = os.path.join(ROOT, "paper_2609_00843_gb300", "cub_baseline", "_build", "librtcdf_cub.so")
+    lib = ctypes.CDLL(path)
+    vp, u64, i64 = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_int64
+    lib.rtcdf_cub_temp_bytes.argtypes = [u64, i64, ctypes.POINTER(ctypes.c_size_t)]
+    lib.rtcdf_cub_normalize.argtypes = [vp, vp, u64, i64, vp]
+    lib.rtcdf_cub_sort_keys.argtypes = [vp, vp, vp, ctypes.c_size_t, u64, i64, vp]
+    lib.rtcdf_cub_denormalize.argtypes = [vp, vp, u64, i64, vp]
+    sh = stream.cuda_stream
+    k_in = torch.empty(n, dtype=torch.int32, device="cuda")
+    k_out = torch.empty(n, dtype=torch.int32, device="cuda")
+    res = torch.empty(n, dtype=torch.int32, device="cuda")
+    tb = ctypes.c_size_t(0)
+    lib.rtcdf_cub_temp_bytes(n, 1 << 18, ctypes.byref(tb))
+    temp = torch.empty(tb.value + 256, dtype=torch.uint8, device="cuda")
+    rows = []
+    for i, c in enumerate(cases):
+        R = c["R"]
+        ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(nsteps)]
+        def once(e=None):
+            if e: e[0].record(stream)
+            assert lib.rtcdf_cub_normalize(ins[i].data_ptr(), k_in.data_ptr(), n, MIN_SWEEP, sh) == 0
+            if e: e[1].record(stream)
+            assert lib.rtcdf_cub_sort_keys(k_in.data_ptr(), k_out.data_ptr(), temp.data_ptr(),
+                                           tb.value, n, R, sh) == 0
+            if e: e[2].record(stream)
+            assert lib.rtcdf_cub_denormalize(k_out.data_ptr(), res.data_ptr(), n, MIN_SWEEP, sh) == 0
+            if e: e[3].record(stream)
+        for _ in range(3):
+            once()
+        for k in range(nsteps):
+            once(ev[k])
+        stream.synchronize()
+        st = [sum(ev[k][j].elapsed_time(ev[k][j + 1]) for k in range(nsteps)) / nsteps for j in range(3)]
+        same = bool(torch.equal(res, outs[i]))
+        rows.append({"R": R, "dist": c["dist_name"], "cub_sortkeys_ms": round(st[1], 5),
+                     "normalize_ms": round(st[0], 5), "denormalize_ms": round(st[2], 5),
+                     "rtcdf_ms": round(ours_ms[i], 5),
+                     "speedup_vs_cub_sortkeys": round(st[1] / ours_ms[i], 3),
+                     "outputs_equal": same})
+    del k_in, k_out, res, temp
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -194,7 +242,12 @@ def main():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cub", action="store_true", help="skip the CUB radix-sort comparison")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--preheat-s", type=float, default=0.5,
+                    help="seconds of untimed load after warm-up so clocks settle")
+    ap.add_argument("--only", default="",
+                    help="comma list of R:dist (e.g. 16384:normal) to run a subset of the sweep")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -225,6 +278,11 @@ def main():
     stream = torch.cuda.Stream()
     sh = stream.cuda_stream
     cases = sweep_cases()
+    if args.only:
+        keep = {tuple(x.split(":")) for x in args.only.split(",")}
+        cases = [c for c in cases if (str(c["R"]), c["dist_name"]) in keep]
+        if not cases:
+            raise SystemExit(f"--only {args.only} selects no sweep array")
     n = N_SWEEP
     ins, outs = [], []
     with torch.cuda.stream(stream):
@@ -271,7 +329,7 @@ def main():
     for _ in range(args.warmup):
         step(None)
     stream.synchronize()
-    t_end = time.time() + 0.5
+    t_end = time.time() + args.preheat_s
     while time.time() < t_end:
         step(None)
         stream.synchronize()
@@ -282,19 +340,41 @@ def main():
     sampler = ClockSampler(local_rank)
     sampler.start()
     time.sleep(0.3)
+    # Timed region: K steps back to back, no events between the kernels (an
+    # event between two kernels would stop the programmatic dependent launch
+    # that overlaps their launch latency).
     t0 = torch.cuda.Event(enable_timing=True)
     t1 = torch.cuda.Event(enable_timing=True)
     barrier()
     torch.cuda.synchronize()
     t0.record(stream)
     for k in range(nsteps):
-        step(dbgs[k])
+        step(None)
     t1.record(stream)
     torch.cuda.synchronize()
     barrier()
+    total_ms = t0.elapsed_time(t1)
+    # Per array: K back-to-back sorts of the same array, uninstrumented.
+    solo_ms = []
+    for i, c in enumerate(cases):
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for k in range(nsteps):
+            rc = rtcdf.rtcdf_sort_ex(ins[i].data_ptr(), outs[i].data_ptr(), n, MIN_SWEEP,
+                                     MIN_SWEEP + c["R"], None, ws.data_ptr(), ws_bytes, None, sh)
+            if rc != rtcdf.OK:
+                raise rtcdf.RtcdfError(rc, "rtcdf_sort_ex")
+        a1.record(stream)
+        stream.synchronize()
+        solo_ms.append(a0.elapsed_time(a1) / nsteps)
+    # Instrumented region: the same K steps with CUDA events on the launching
+    # stream before and after every kernel, for the per-kernel durations.
+    for k in range(nsteps):
+        step(dbgs[k])
+    torch.cuda.synchronize()
     time.sleep(0.1)
     clocks = sampler.stop()
-    total_ms = t0.elapsed_time(t1)
     if dist_on:
         tt = torch.tensor([total_ms], device="cuda")
         torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
@@ -318,10 +398,11 @@ def main():
     hbm, peak_kind = peaks()
     per_config = []
     for i, c in enumerate(cases):
-        ms = per_case_ms[i] / nsteps
+        ms = solo_ms[i]
         per_config.append({"R": c["R"], "dist": c["dist_name"], "ms": round(ms, 5),
                            "GKeys_s": round(n / (ms * 1e-3) / 1e9, 2),
                            "frac_8n_roofline": round(8 * n / (ms * 1e-3) / 1e9 / hbm, 4),
+                           "ms_instrumented": round(per_case_ms[i] / nsteps, 5),
                            "hist_ms": round(stage_ms[i][0] / nsteps, 5),
                            "scan_ms": round(stage_ms[i][1] / nsteps, 5),
                            "fill_ms": round(stage_ms[i][2] / nsteps, 5)})
@@ -359,6 +440,11 @@ def main():
         "gpu_launches": 3 * len(cases) * args.steps,
         "timed_region_ms": round(total_ms, 3),
     }
+
+    # On-GPU comparison: CUB DeviceRadixSort restricted to bits [0, ceil(log2 R))
+    # on keys normalised to uint32 (normalise / denormalise timed apart).
+    if not args.no_cub and rank == 0:
+        line["cub_comparison"] = cub_comparison(cases, ins, outs, n, stream, nsteps, solo_ms)
 
     # End to end through the C ABI: pinned host input -> device -> sort -> host.
     if not args.no_e2e:

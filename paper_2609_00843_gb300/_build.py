@@ -2,7 +2,9 @@
 
 ``build()`` compiles every translation unit of ``csrc/`` in parallel with nvcc
 (``-gencode arch=compute_103a,code=sm_103a``, static CUDA runtime) and links
-``_build/librtcdf.so``; it also builds ``gen/_build/librtcdf_gen.so``.  A
+``_build/librtcdf.so``; it also builds ``gen/_build/librtcdf_gen.so`` (input
+generator) and ``cub_baseline/_build/librtcdf_cub.so`` (the CUB comparison
+used by the benchmark).  A
 library is rebuilt only when a source or header is newer than it.
 """
 from __future__ import annotations
@@ -73,6 +75,9 @@ def build(jobs: int | None = None) -> dict:
     gsrc = [os.path.join(HERE, "gen", "gen.cu")]
     out["gen"] = _build_lib(gsrc, [os.path.join(ROOT, "include", "rtcdf_gen.h")],
                             os.path.join(HERE, "gen", "_build", "librtcdf_gen.so"), jobs)
+    csrc_cub = [os.path.join(HERE, "cub_baseline", "cub_sort.cu")]
+    out["cub"] = _build_lib(csrc_cub, [], os.path.join(HERE, "cub_baseline", "_build",
+                                                     "librtcdf_cub.so"), jobs)
     return out
 
 

@@ -7,16 +7,27 @@
 // run_val[k] = that value's key): it copies a window of consecutive runs into
 // shared memory, then every thread writes 16-byte vectors of its positions,
 // finding the run of a position with the same rule (smallest k with
-// run_end[k] >= p + 1), starting from the run of its previous vector.  When a
-// whole vector lies inside one run -- the common case -- that is one shared
-// load and one compare before the store.  Vectors cut by the window edge or
-// by the array's ends are written element by element.
+// run_end[k] >= p + 1), starting from the run of its previous vector (the
+// next run is tried first, then a binary search).  When a whole vector lies
+// inside one run -- the common case -- that is one shared load and one
+// compare before the store.  The few positions of a window that
+// do not fill a whole aligned vector are written one by one.
 //
-// The CTA also clears the scan's lookback state so the workspace is ready for
-// the next sort.
+// All positions are below n < 2^32, so the index arithmetic is 32-bit.  The
+// CTA also clears the scan's lookback state so the workspace is ready for the
+// next sort.
 #include "rtcdf_internal.h"
 
 namespace rtcdf {
+
+// Smallest j in [lo, hi] with s_end[j] > p, given s_end[hi] > p.
+__device__ __forceinline__ int first_run_after(const uint32_t *s_end, int lo, int hi, uint32_t p) {
+    while (lo < hi) {
+        int mid = (lo + hi) >> 1;
+        if (s_end[mid] > p) hi = mid; else lo = mid + 1;
+    }
+    return lo;
+}
 
 template <int WIN>
 __global__ void __launch_bounds__(WIN) fill_kernel(FillArgs a) {
@@ -25,16 +36,18 @@ __global__ void __launch_bounds__(WIN) fill_kernel(FillArgs a) {
     const int tid = threadIdx.x;
     const uint32_t c = blockIdx.x;
 
+    // Programmatic dependent of the scan: wait for its results.
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     for (uint32_t i = c * WIN + tid; i < a.scan_chunks; i += a.fill_ctas * WIN) a.scan_state[i] = 0;
     if (c == 0 && tid == 0) a.ctl->scan_ticket = 0;
 
-    const int64_t n = (int64_t)a.n, head = a.head;
-    const int64_t P0 = (c == 0) ? 0 : head + (int64_t)c * (int64_t)a.fill_chunk;
-    const int64_t P1 = (c + 1 == a.fill_ctas) ? n : head + (int64_t)(c + 1) * (int64_t)a.fill_chunk;
+    const uint32_t n = (uint32_t)a.n, head = a.head, fc = (uint32_t)a.fill_chunk;
+    const uint32_t P0 = (c == 0) ? 0u : head + c * fc;
+    const uint32_t P1 = (c + 1 == a.fill_ctas) ? n : head + (c + 1) * fc;
     const uint32_t D = a.ctl->num_runs;
     uint32_t k_cur = a.start_run[c];
     int4 *vout = reinterpret_cast<int4 *>(a.out + head);  // 16-byte aligned frame
-    int64_t pos = P0;
+    uint32_t pos = P0;
 
     while (pos < P1 && k_cur < D) {
         const int nw = (int)min((uint32_t)WIN, D - k_cur);
@@ -44,81 +57,97 @@ __global__ void __launch_bounds__(WIN) fill_kernel(FillArgs a) {
             s_val[tid] = a.run_val[k_cur + tid];
         }
         __syncthreads();
-        const int64_t hi = min(P1, (int64_t)s_end[nw - 1]);
-        // Vectors w cover positions [head + 4w, head + 4w + 4); w may be -1 for
-        // the unaligned head.
-        const int64_t w_first = (pos - head >= 0) ? (pos - head) / 4 : -1;
-        const int64_t w_last = (hi - 1 - head >= 0) ? (hi - 1 - head) / 4 : -1;
+        const uint32_t hi = min(P1, s_end[nw - 1]);
+        // Whole vectors w cover [head + 4w, head + 4w + 4) inside [pos, hi).
+        const uint32_t w_lo = pos >= head ? (pos - head + 3) >> 2 : 0u;
+        const uint32_t w_hi = hi >= head ? (hi - head) >> 2 : 0u;
 
         if (s_end[0] >= hi) {
             // One run covers the whole round: constant stores.
             const int32_t v = s_val[0];
             const int4 vv = make_int4(v, v, v, v);
-            int64_t w = w_first + tid;
-            for (; w <= w_last; w += WIN) {
-                const int64_t q = head + 4 * w;
-                if (q >= pos && q + 4 <= hi) {
-                    __stcs(vout + w, vv);
-                } else {
-#pragma unroll
-                    for (int e = 0; e < 4; e++) {
-                        const int64_t p = q + e;
-                        if (p >= pos && p < hi) a.out[p] = v;
-                    }
-                }
+            uint32_t w = w_lo + tid;
+            for (; w + 3 * WIN < w_hi; w += 4 * WIN) {
+                __stcs(vout + w, vv);
+                __stcs(vout + w + WIN, vv);
+                __stcs(vout + w + 2 * WIN, vv);
+                __stcs(vout + w + 3 * WIN, vv);
             }
+            for (; w < w_hi; w += WIN) __stcs(vout + w, vv);
         } else {
-            int j = 0;  // run index within the window, nondecreasing per thread
-            for (int64_t w = w_first + tid; w <= w_last; w += WIN) {
-                const int64_t q = head + 4 * w;
-                const int64_t q0 = q > pos ? q : pos;
-                // Smallest j with s_end[j] > q0 (binary search above the last hit).
-                if ((int64_t)s_end[j] <= q0) {
-                    int lo = j + 1, hi_i = nw - 1;
-                    while (lo < hi_i) {
-                        int mid = (lo + hi_i) >> 1;
-                        if ((int64_t)s_end[mid] > q0) hi_i = mid; else lo = mid + 1;
-                    }
-                    j = lo;
+            // Each warp takes a contiguous share of the vectors and its lanes
+            // interleave inside it: every store instruction still covers 512
+            // contiguous bytes, while a lane's successive vectors are only 128
+            // positions apart, so its run index usually stays put or moves to
+            // the next run.
+            const int lane = tid & 31, warp = tid >> 5;
+            const uint32_t nvec = w_hi > w_lo ? w_hi - w_lo : 0u;
+            const uint32_t per_warp = ((nvec + (WIN / 32) - 1) / (WIN / 32) + 31) & ~31u;
+            const uint32_t wb = w_lo + warp * per_warp;
+            const uint32_t we = min(w_hi, wb + per_warp);
+            int j = 0;  // run of this lane's last vector; nondecreasing
+            for (uint32_t w = wb + lane; w < we; w += 32) {
+                const uint32_t q = head + 4 * w;
+                if (s_end[j] <= q) {
+                    // s_end[nw - 1] > q, so j + 1 <= nw - 1.
+                    j = (s_end[j + 1] > q) ? j + 1 : first_run_after(s_end, j + 2, nw - 1, q);
                 }
-                if (q >= pos && q + 4 <= hi) {
-                    if ((int64_t)s_end[j] >= q + 4) {
-                        const int32_t v = s_val[j];
-                        __stcs(vout + w, make_int4(v, v, v, v));
-                    } else {
-                        int32_t r[4];
-                        int jj = j;
-#pragma unroll
-                        for (int e = 0; e < 4; e++) {
-                            while ((int64_t)s_end[jj] <= q + e) jj++;
-                            r[e] = s_val[jj];
-                        }
-                        __stcs(vout + w, make_int4(r[0], r[1], r[2], r[3]));
-                    }
+                if (s_end[j] >= q + 4) {
+                    const int32_t v = s_val[j];
+                    __stcs(vout + w, make_int4(v, v, v, v));
                 } else {
+                    int32_t r[4];
                     int jj = j;
+#pragma unroll
                     for (int e = 0; e < 4; e++) {
-                        const int64_t p = q + e;
-                        if (p < pos || p >= hi) continue;
-                        while ((int64_t)s_end[jj] <= p) jj++;
-                        a.out[p] = s_val[jj];
+                        while (s_end[jj] <= q + e) jj++;
+                        r[e] = s_val[jj];
                     }
+                    __stcs(vout + w, make_int4(r[0], r[1], r[2], r[3]));
                 }
             }
+        }
+        // Positions of [pos, hi) outside whole vectors: at most three before
+        // the first vector and three after the last.
+        if (tid < 8) {
+            const uint32_t q_lo = head + 4 * w_lo, q_hi = head + 4 * w_hi;
+            uint32_t p;
+            if (w_lo >= w_hi) {
+                p = pos + tid;  // no whole vector: hi - pos < 8
+            } else {
+                const uint32_t n_front = q_lo - pos;
+                p = (uint32_t)tid < n_front ? pos + tid : q_hi + (tid - n_front);
+            }
+            if (p >= pos && p < hi && (w_lo >= w_hi || p < q_lo || p >= q_hi))
+                a.out[p] = s_val[first_run_after(s_end, 0, nw - 1, p)];
         }
         pos = hi;
         k_cur += nw;
     }
 }
 
+template <int WIN>
+cudaError_t launch_fill_t(const FillArgs &a, cudaStream_t s) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.fill_ctas);
+    cfg.blockDim = dim3(WIN);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, fill_kernel<WIN>, a);
+}
+
 cudaError_t launch_fill(const FillArgs &a, int threads, cudaStream_t s) {
     switch (threads) {
-        case 256: fill_kernel<256><<<a.fill_ctas, 256, 0, s>>>(a); break;
-        case 512: fill_kernel<512><<<a.fill_ctas, 512, 0, s>>>(a); break;
-        case 1024: fill_kernel<1024><<<a.fill_ctas, 1024, 0, s>>>(a); break;
+        case 256: return launch_fill_t<256>(a, s);
+        case 512: return launch_fill_t<512>(a, s);
+        case 1024: return launch_fill_t<1024>(a, s);
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
 }
 
 }  // namespace rtcdf

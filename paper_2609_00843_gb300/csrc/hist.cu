@@ -1,16 +1,22 @@
 // Range-tile histogram (Algorithm 5, all m tiles in one launch as in Section 3.3).
 //
-// CTA b works on tile t = b mod m and input chunk q = b / m (the paper's
-// interleaving, which keeps the m CTAs that read the same chunk co-resident so
-// that all but the first read of a chunk hit L2).  Each CTA keeps a private
-// histogram S[0..w_t-1] of 32-bit counters in shared memory, streams its chunk
-// with 16-byte loads, adds 1 to S[x - b_t] for every key whose normalised value
-// x lies in the tile, and finally adds each non-zero S[x] to H[b_t + x] with one
-// global atomic.  Keys outside [minVal, maxVal) set the device status bit.
+// CTA b works on tile t = b mod m and is the q-th (q = b / m) of the g CTAs of
+// that tile -- the paper's interleaving, which keeps the m CTAs that read the
+// same part of the input co-resident so that every read after the first is an
+// L2 hit.  Each CTA keeps a private histogram S[0..w_t-1] of 32-bit counters
+// in shared memory, sweeps the input grid-stride with 16-byte loads, adds 1 to
+// S[y] for every key whose position y = key - minVal - b_t inside the tile is
+// below w_t (one unsigned compare tests both ends; keys outside [minVal,
+// maxVal) fall outside every tile), and finally adds each non-zero S[y] to
+// H[b_t + y] with one global atomic.
 //
-// On GB300 a single shared-memory copy per CTA already sustains the HBM read
-// rate for every input shape measured (uniform, normal, all-equal), so there
-// is no per-warp replication; occupancy comes from 1024-thread CTAs.
+// Out-of-range keys need no per-key test: they are counted by no tile, so the
+// histogram total falls short of n, which the scan detects.
+//
+// On GB300 a single shared-memory copy per CTA sustains the HBM read rate for
+// uniform, normal and all-equal inputs alike, so there is no replication.
+// Bytes in flight come from unrolled 16-byte loads (bulk L2 prefetches issued
+// ahead of the loads were measured and gave nothing).
 #include <map>
 #include <mutex>
 #include <tuple>
@@ -25,7 +31,19 @@ __device__ __forceinline__ int4 load_vec(const int4 *p) {
     return __ldg(p);                  // re-read by the other tiles' CTAs: keep in L2
 }
 
-template <bool STREAMING>
+// S[y] += 1 when y < w, as a predicated shared-memory reduction (no branch).
+// No "memory" clobber: S is only otherwise touched on the far side of a
+// __syncthreads(), and the clobber would stop the next loads from being
+// scheduled early.
+__device__ __forceinline__ void count_key(uint32_t s_base, uint32_t y, uint32_t w) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.lt.u32 p, %0, %1;\n\t"
+        "@p red.shared.add.u32 [%2], 1;\n\t}"
+        ::"r"(y), "r"(w), "r"(s_base + 4u * y));
+}
+
+template <bool STREAMING, int UNROLL>
 __global__ void __launch_bounds__(1024) hist_kernel(HistArgs a) {
     extern __shared__ uint32_t S[];
     const uint32_t t = blockIdx.x % a.m;
@@ -37,52 +55,73 @@ __global__ void __launch_bounds__(1024) hist_kernel(HistArgs a) {
     for (uint32_t i = tid; i < w; i += nt) S[i] = 0;
     __syncthreads();
 
-    const uint32_t min_u = a.min_u, R = a.R;
-    bool bad = false;
-    auto count = [&](int32_t key) {
-        uint32_t x = (uint32_t)key - min_u;  // normalised value, wraps when key < minVal
-        bad |= (x >= R);
-        uint32_t y = x - b;                  // position inside the tile
-        if (y < w) atomicAdd(&S[y], 1u);
-    };
+    const uint32_t base = a.min_u + b;  // key - base = position inside the tile
+    const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(S);
 
+    // Grid-stride over 16-byte vectors: the g CTAs of a tile sweep the input
+    // together, and the CTAs of the other tiles with the same q read the same
+    // addresses at the same time (served from L2 after the first).
     const int4 *vin = reinterpret_cast<const int4 *>(a.in + a.head);
-    const uint64_t v0 = (uint64_t)q * a.vec_per_cta;
-    const uint64_t v1 = min(a.nvec, v0 + a.vec_per_cta);
-    uint64_t v = v0 + tid;
-    for (; v + 3ull * nt < v1; v += 4ull * nt) {
-        int4 k0 = load_vec<STREAMING>(vin + v);
-        int4 k1 = load_vec<STREAMING>(vin + v + nt);
-        int4 k2 = load_vec<STREAMING>(vin + v + 2 * nt);
-        int4 k3 = load_vec<STREAMING>(vin + v + 3 * nt);
-        count(k0.x); count(k0.y); count(k0.z); count(k0.w);
-        count(k1.x); count(k1.y); count(k1.z); count(k1.w);
-        count(k2.x); count(k2.y); count(k2.z); count(k2.w);
-        count(k3.x); count(k3.y); count(k3.z); count(k3.w);
+    const uint64_t stride = (uint64_t)a.g * nt;
+    const uint64_t nvec = a.nvec;
+    uint64_t v = (uint64_t)q * nt + tid;
+    for (; v + (UNROLL - 1) * stride < nvec; v += UNROLL * stride) {
+        int4 k[UNROLL];
+#pragma unroll
+        for (int u = 0; u < UNROLL; u++) k[u] = load_vec<STREAMING>(vin + v + u * stride);
+#pragma unroll
+        for (int u = 0; u < UNROLL; u++) {
+            count_key(s_base, (uint32_t)k[u].x - base, w);
+            count_key(s_base, (uint32_t)k[u].y - base, w);
+            count_key(s_base, (uint32_t)k[u].z - base, w);
+            count_key(s_base, (uint32_t)k[u].w - base, w);
+        }
     }
-    for (; v < v1; v += nt) {
+    for (; v < nvec; v += stride) {
         int4 k0 = load_vec<STREAMING>(vin + v);
-        count(k0.x); count(k0.y); count(k0.z); count(k0.w);
+        count_key(s_base, (uint32_t)k0.x - base, w);
+        count_key(s_base, (uint32_t)k0.y - base, w);
+        count_key(s_base, (uint32_t)k0.z - base, w);
+        count_key(s_base, (uint32_t)k0.w - base, w);
     }
     if (q == 0) {
         // Unaligned head and ragged tail, scalar.
-        if ((uint32_t)tid < a.head) count(a.in[tid]);
-        for (uint64_t i = a.head + 4 * a.nvec + tid; i < a.n; i += nt) count(a.in[i]);
+        if ((uint32_t)tid < a.head) count_key(s_base, (uint32_t)a.in[tid] - base, w);
+        for (uint64_t i = a.head + 4 * nvec + tid; i < a.n; i += nt)
+            count_key(s_base, (uint32_t)a.in[i] - base, w);
     }
+    // The scan may be scheduled now; it waits for this grid to finish before
+    // reading H.
+    asm volatile("griddepcontrol.launch_dependents;");
 
-    if (__syncthreads_or(bad) && tid == 0) atomicOr(&a.ctl->status, kDevKeyOutOfRange);
+    __syncthreads();
+    uint32_t *H = a.H + b;
     for (uint32_t i = tid; i < w; i += nt) {
         uint32_t c = S[i];
-        if (c) atomicAdd(&a.H[b + i], c);
+        if (c) atomicAdd(&H[i], c);
     }
 }
+
+template <bool STREAMING>
+const void *hist_fn(int unroll) {
+    return unroll == 8 ? (const void *)hist_kernel<STREAMING, 8> : (const void *)hist_kernel<STREAMING, 4>;
+}
+
+// Eight loads in flight per thread when only one CTA fits on an SM.
+int hist_unroll(size_t smem) { return smem > 114 * 1024 ? 8 : 4; }
 
 cudaError_t launch_hist(const HistArgs &a, int threads, size_t smem, bool streaming,
                         cudaStream_t s) {
     // hist_max_ctas_per_sm() has raised the shared-memory limit for this size.
     dim3 grid(a.m * a.g);
-    if (streaming) hist_kernel<true><<<grid, threads, smem, s>>>(a);
-    else hist_kernel<false><<<grid, threads, smem, s>>>(a);
+    const bool deep = hist_unroll(smem) == 8;
+    if (streaming) {
+        if (deep) hist_kernel<true, 8><<<grid, threads, smem, s>>>(a);
+        else hist_kernel<true, 4><<<grid, threads, smem, s>>>(a);
+    } else {
+        if (deep) hist_kernel<false, 8><<<grid, threads, smem, s>>>(a);
+        else hist_kernel<false, 4><<<grid, threads, smem, s>>>(a);
+    }
     return cudaGetLastError();
 }
 
@@ -102,11 +141,14 @@ cudaError_t hist_max_ctas_per_sm(int threads, size_t smem, bool streaming, int *
         *ctas = it->second;
         return cudaSuccess;
     }
-    const void *f = streaming ? (const void *)hist_kernel<true> : (const void *)hist_kernel<false>;
+    const void *f = streaming ? hist_fn<true>(hist_unroll(smem)) : hist_fn<false>(hist_unroll(smem));
     size_t &lim = smem_limit[std::make_pair(dev, streaming)];
     if (smem > lim) {
-        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
+        for (int u : {4, 8}) {
+            const void *fu = streaming ? hist_fn<true>(u) : hist_fn<false>(u);
+            e = cudaFuncSetAttribute(fu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+            if (e != cudaSuccess) return e;
+        }
         lim = smem;
     }
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas, f, threads, smem);

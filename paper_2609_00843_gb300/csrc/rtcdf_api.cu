@@ -56,7 +56,7 @@ struct Plan {
     size_t hist_smem;
     bool streaming;
     uint32_t head;
-    uint64_t nvec, vec_per_cta;
+    uint64_t nvec;
     int fill_threads;
     uint32_t fill_ctas;
     uint64_t fill_chunk;
@@ -89,7 +89,13 @@ rtcdf_status make_plan(uint64_t n, uint32_t R, uintptr_t in_addr, uintptr_t out_
     // Largest tile whose 32-bit histogram fits the opt-in shared memory.
     const uint32_t t_max = (uint32_t)(dev.smem_optin / 4) & ~1023u;
     uint32_t T = q.tile_width > 0 ? (uint32_t)q.tile_width : 0;
-    if (T == 0) T = R <= t_max ? R : t_max;
+    if (T == 0) {
+        // Fewest tiles that fit, then equal widths (rounded up to 1024 values):
+        // every tile costs a full input scan, and balanced tiles leave more
+        // shared memory per SM for L1.
+        const uint32_t m = (R + t_max - 1) / t_max;
+        T = m == 1 ? R : std::min(t_max, ((R + m - 1) / m + 1023) & ~1023u);
+    }
     if (T > t_max) return RTCDF_ERR_INVALID_ARG;
     if (T > R) T = R;
     pl->T = T;
@@ -113,7 +119,6 @@ rtcdf_status make_plan(uint64_t n, uint32_t R, uintptr_t in_addr, uintptr_t out_
     g = std::min(g, g_n);
     if (q.hist_ctas_per_tile > 0) g = (uint64_t)q.hist_ctas_per_tile;
     pl->g = (uint32_t)g;
-    pl->vec_per_cta = std::max<uint64_t>(1, (pl->nvec + g - 1) / g);
 
     // Output: contiguous position ranges, CTA boundaries on 16-byte vectors of `out`.
     // Not clamped to n: positions below head_out are written one by one, and
@@ -122,9 +127,13 @@ rtcdf_status make_plan(uint64_t n, uint32_t R, uintptr_t in_addr, uintptr_t out_
     pl->fill_threads = q.fill_threads ? q.fill_threads : 512;
     if (pl->fill_threads != 256 && pl->fill_threads != 512 && pl->fill_threads != 1024)
         return RTCDF_ERR_INVALID_ARG;
-    uint64_t want = q.fill_ctas > 0 ? (uint64_t)q.fill_ctas : (uint64_t)dev.sms * 4;
-    want = std::min<uint64_t>(want, kMaxFillCtas);
+    // Many more CTAs than fit at once (about 32K positions each, at least four
+    // waves' worth): the block scheduler then balances CTAs whose positions
+    // cross many short runs against CTAs inside one long run.
     uint64_t body = n > head_out ? n - head_out : 0;
+    uint64_t want = q.fill_ctas > 0 ? (uint64_t)q.fill_ctas
+                                    : std::max<uint64_t>((uint64_t)dev.sms * 4, body / 32768);
+    want = std::min<uint64_t>(want, kMaxFillCtas);
     uint64_t chunk = std::max<uint64_t>(4 * (uint64_t)pl->fill_threads, (body + want - 1) / want);
     chunk = (chunk + 3) / 4 * 4;
     pl->fill_chunk = chunk;
@@ -166,7 +175,7 @@ rtcdf_status run_pipeline(const int32_t *in, int32_t *out, uint64_t n, int64_t m
     if (ev[0] && cudaEventRecord(ev[0], s) != cudaSuccess) return RTCDF_ERR_CUDA;
 
     HistArgs h;
-    h.in = in; h.n = n; h.nvec = pl.nvec; h.vec_per_cta = pl.vec_per_cta; h.head = pl.head;
+    h.in = in; h.n = n; h.nvec = pl.nvec; h.head = pl.head;
     h.min_u = (uint32_t)(int32_t)minVal; h.R = R; h.T = pl.T; h.m = pl.m; h.g = pl.g;
     h.H = H; h.ctl = ctl;
     if (launch_hist(h, pl.hist_threads, pl.hist_smem, pl.streaming, s) != cudaSuccess)
@@ -252,8 +261,7 @@ rtcdf_status sort_with_workspace(const int32_t *in, int32_t *out, uint64_t n, in
     if (st) return st;
     if (!ws || ws_bytes < ws_required(R)) return RTCDF_ERR_NO_MEMORY;
     const WsLayout L = ws_layout(R, ws_bytes);
-    const size_t zero_bytes = L.hist + (size_t)L.scan_chunks * kScanChunk * 4;
-    if (cudaMemsetAsync(ws, 0, zero_bytes, s) != cudaSuccess) return RTCDF_ERR_CUDA;
+    if (cudaMemsetAsync(ws, 0, L.zero_bytes, s) != cudaSuccess) return RTCDF_ERR_CUDA;
     Plan pl;
     st = make_plan(n, R, (uintptr_t)in, (uintptr_t)out, nullptr, &pl);
     if (st) return st;

@@ -46,15 +46,22 @@ constexpr uint32_t kMaxScanChunks = (1u << 24) / kScanChunk;
 struct WsLayout {
     size_t ctl, scan_state, hist, run_end, run_val, start_run, total;
     uint32_t scan_chunks;
+    size_t zero_bytes;  // [0, zero_bytes) must be zero when a sort starts
 };
 
 inline size_t align_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
 
 constexpr size_t kWsHistOffset = 256 + (size_t)kMaxScanChunks * 8;
 
+// H is padded to whole scan chunks.  Its size never decreases as R grows, so a
+// sort's run table (anchored at the top) never reaches the part of H
+// (anchored at the bottom) that a sort with a smaller range expects zeroed.
+inline size_t hist_region_bytes(uint64_t R) {
+    return (size_t)((R + kScanChunk - 1) / kScanChunk) * kScanChunk * 4;
+}
+
 inline size_t ws_required(uint64_t R) {
-    size_t chunks = (size_t)((R + kScanChunk - 1) / kScanChunk);
-    return kWsHistOffset + chunks * kScanChunk * 4 + align_up((size_t)kMaxFillCtas * 4, 256) +
+    return kWsHistOffset + hist_region_bytes(R) + align_up((size_t)kMaxFillCtas * 4, 256) +
            2 * align_up((size_t)R * 4, 256);
 }
 
@@ -64,6 +71,7 @@ inline WsLayout ws_layout(uint64_t R, size_t total) {
     L.ctl = 0;
     L.scan_state = 256;
     L.hist = kWsHistOffset;
+    L.zero_bytes = L.hist + hist_region_bytes(R);
     size_t top = total / 256 * 256;
     L.run_val = top - align_up((size_t)R * 4, 256);
     L.run_end = L.run_val - align_up((size_t)R * 4, 256);
@@ -77,7 +85,6 @@ struct HistArgs {
     const int32_t *in;
     uint64_t n;
     uint64_t nvec;         // 16-byte vectors after the unaligned head
-    uint64_t vec_per_cta;  // contiguous vectors per CTA of one tile
     uint32_t head;         // elements before the first 16-byte aligned address
     uint32_t min_u;        // (uint32_t)minVal
     uint32_t R, T, m, g;   // range size, tile width, tiles, CTAs per tile

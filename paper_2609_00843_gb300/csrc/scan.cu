@@ -9,13 +9,20 @@
 // with c_v > 0 is given a run index k (a second prefix count packed in the
 // high half of the same 64-bit scan word) and the run table
 //     run_end[k] = sum_{u<=v} c_u,   run_val[k] = minVal + v
-// is written, so that output generation never walks empty values.  The value
-// containing the first position of every output CTA is recorded in start_run.
-// H is zeroed as it is read, leaving the workspace ready for the next sort.
+// is written, so that output generation never walks empty values.
 //
+// Each output CTA needs the run holding its first position.  Every scan CTA
+// keeps its chunk's CDF in shared memory and, for the output CTAs whose first
+// position falls inside the chunk's positions, finds that run with the rule of
+// Algorithm 7 (smallest value whose CDF exceeds the position) by binary
+// search -- a handful of steps per output CTA whatever the distribution.
+//
+// H is zeroed as it is read, leaving the workspace ready for the next sort.
 // Chunks of kScanChunk bins are handed out by an atomic ticket so that a chunk
 // only ever waits for chunks already owned by running CTAs; every wait is
-// bounded by kMaxSpin and records kDevTimeout when it gives up.
+// bounded by kMaxSpin and records kDevTimeout when it gives up.  The total
+// count is compared with n: every in-range key is counted by exactly one tile,
+// so a shortfall means some key lies outside [minVal, maxVal).
 #include "rtcdf_internal.h"
 
 namespace rtcdf {
@@ -50,21 +57,68 @@ __device__ __forceinline__ uint64_t warp_sum(uint64_t x) {
     return x;
 }
 
+// Exclusive prefix of the chunks before `chunk` (decoupled lookback, warp 0).
+__device__ uint64_t lookback(uint64_t *state, uint32_t chunk, uint64_t total, int lane, Ctl *ctl) {
+    if (chunk == 0) {
+        if (lane == 0) store_release(&state[0], kStateIncl | total);
+        return 0;
+    }
+    if (lane == 0) store_release(&state[chunk], kStateAgg | total);
+    uint64_t prefix = 0;
+    int64_t look = (int64_t)chunk - 1;
+    uint32_t spins = 0;
+    bool timed_out = false;
+    while (true) {
+        const int64_t idx = look - lane;
+        uint64_t st = (idx >= 0) ? load_acquire(&state[idx]) : kStateIncl;
+        // Wait until every lane's predecessor has published something.
+        while (!__all_sync(0xffffffffu, (st >> 62) != 0)) {
+            if (++spins > kMaxSpin) { timed_out = true; break; }
+            __nanosleep(64);
+            if ((st >> 62) == 0) st = load_acquire(&state[idx]);
+        }
+        if (timed_out) break;
+        const unsigned incl_mask = __ballot_sync(0xffffffffu, (st >> 62) == 2);
+        if (incl_mask) {
+            const int first = __ffs(incl_mask) - 1;  // nearest inclusive predecessor
+            prefix += warp_sum((lane <= first) ? (st & kValueMask) : 0);
+            break;
+        }
+        prefix += warp_sum(st & kValueMask);
+        look -= 32;
+    }
+    if (timed_out && lane == 0) atomicOr(&ctl->status, kDevTimeout);
+    if (lane == 0) store_release(&state[chunk], kStateIncl | (prefix + total));
+    return prefix;
+}
+
 __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs a) {
     __shared__ uint32_t s_chunk;
     __shared__ uint64_t s_warp[kScanThreads / 32];
     __shared__ uint64_t s_prefix;
+    __shared__ uint32_t s_cdf[kScanChunk];   // sum_{u<=v} c_u for the chunk's values
+    __shared__ uint32_t s_runs[kScanChunk];  // non-empty values u <= v
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    if (tid == 0) s_chunk = atomicAdd(&a.ctl->scan_ticket, 1u);
-    __syncthreads();
-    const uint32_t chunk = s_chunk;
-    const uint32_t base = chunk * kScanChunk + tid * kScanItems;
+    // Launched as a programmatic dependent of the histogram: wait until that
+    // grid has finished and its writes are visible, then let the output
+    // kernel be scheduled (it waits for this grid in the same way).
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    const bool single = (a.chunks == 1);  // R <= kScanChunk: no lookback at all
+    if (!single) {
+        if (tid == 0) s_chunk = atomicAdd(&a.ctl->scan_ticket, 1u);
+        __syncthreads();
+    }
+    const uint32_t chunk = single ? 0u : s_chunk;
+    const uint32_t cbase = chunk * kScanChunk;
+    const uint32_t base = cbase + tid * kScanItems;
 
-    // Load four counts (H is padded to whole chunks) and zero them behind us.
-    uint4 h4 = *reinterpret_cast<const uint4 *>(a.H + base);
-    *reinterpret_cast<uint4 *>(a.H + base) = make_uint4(0, 0, 0, 0);
-    uint32_t c[kScanItems] = {h4.x, h4.y, h4.z, h4.w};
+    // Four counts (H is padded to whole chunks), zeroed behind us.
+    uint4 *h4p = reinterpret_cast<uint4 *>(a.H + base);
+    const uint4 h4 = *h4p;
+    *h4p = make_uint4(0, 0, 0, 0);
+    const uint32_t c[kScanItems] = {h4.x, h4.y, h4.z, h4.w};
     if (a.dbg_hist) {
 #pragma unroll
         for (int i = 0; i < kScanItems; i++)
@@ -79,84 +133,83 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs a) {
         run += ((uint64_t)(c[i] > 0) << 32) | c[i];
         incl[i] = run;
     }
-    // Block scan of the thread totals.
-    uint64_t winc = warp_incl_scan(run, lane);
+    // Block scan of the thread totals, then the chunk prefix.
+    const uint64_t winc = warp_incl_scan(run, lane);
     if (lane == 31) s_warp[warp] = winc;
     __syncthreads();
     if (warp == 0) {
-        uint64_t wt = s_warp[lane];
-        uint64_t wi = warp_incl_scan(wt, lane);
+        const uint64_t wt = s_warp[lane];
+        const uint64_t wi = warp_incl_scan(wt, lane);
         s_warp[lane] = wi - wt;  // exclusive prefix of each warp
-        uint64_t total = __shfl_sync(0xffffffffu, wi, 31);
-
-        // Decoupled lookback across chunks (warp 0 only).
-        uint64_t prefix = 0;
-        if (chunk == 0) {
-            if (lane == 0) store_release(&a.state[0], kStateIncl | total);
-        } else {
-            if (lane == 0) store_release(&a.state[chunk], kStateAgg | total);
-            int64_t look = (int64_t)chunk - 1;
-            uint32_t spins = 0;
-            bool timed_out = false;
-            while (true) {
-                int64_t idx = look - lane;
-                uint64_t st = (idx >= 0) ? load_acquire(&a.state[idx]) : (kStateIncl | 0ull);
-                // Wait until every lane's predecessor has published something.
-                while (!__all_sync(0xffffffffu, (st >> 62) != 0)) {
-                    if (++spins > kMaxSpin) { timed_out = true; break; }
-                    __nanosleep(64);
-                    if ((st >> 62) == 0) st = load_acquire(&a.state[idx]);
-                }
-                if (timed_out) break;
-                unsigned incl_mask = __ballot_sync(0xffffffffu, (st >> 62) == 2);
-                if (incl_mask) {
-                    int first = __ffs(incl_mask) - 1;  // nearest inclusive predecessor
-                    uint64_t v = (lane <= first) ? (st & kValueMask) : 0;
-                    prefix += warp_sum(v);
-                    break;
-                }
-                prefix += warp_sum(st & kValueMask);
-                look -= 32;
-            }
-            if (timed_out && lane == 0) atomicOr(&a.ctl->status, kDevTimeout);
-            if (lane == 0) store_release(&a.state[chunk], kStateIncl | (prefix + total));
-        }
+        const uint64_t total = __shfl_sync(0xffffffffu, wi, 31);
+        const uint64_t prefix = single ? 0 : lookback(a.state, chunk, total, lane, a.ctl);
         if (lane == 0) s_prefix = prefix;
     }
     __syncthreads();
 
-    const uint64_t texcl = s_prefix + s_warp[warp] + (winc - run);
+    const uint64_t chunk_prefix = s_prefix;
+    const uint64_t texcl = chunk_prefix + s_warp[warp] + (winc - run);
 #pragma unroll
     for (int i = 0; i < kScanItems; i++) {
         const uint32_t v = base + i;
-        if (v >= a.R) break;
         const uint64_t p = texcl + incl[i];
-        const uint32_t cnt_end = (uint32_t)p;           // sum_{u<=v} c_u
-        const uint32_t runs = (uint32_t)(p >> 32);      // values u<=v with c_u > 0
+        const uint32_t cnt_end = (uint32_t)p;       // sum_{u<=v} c_u
+        const uint32_t runs = (uint32_t)(p >> 32);  // values u<=v with c_u > 0
+        s_cdf[tid * kScanItems + i] = cnt_end;
+        s_runs[tid * kScanItems + i] = runs;
+        if (v >= a.R) continue;
         if (a.dbg_cdf) a.dbg_cdf[v] = cnt_end;
         if (a.dbg_offset && (v % a.T) == 0) a.dbg_offset[v / a.T] = cnt_end - c[i];
-        if (v == a.R - 1) a.ctl->num_runs = runs;
-        if (c[i] == 0) continue;
-        const uint32_t k = runs - 1;
-        a.run_end[k] = cnt_end;
-        a.run_val[k] = (int32_t)((uint32_t)a.minVal + v);
-        // Output CTAs whose first position lies in [cnt_end - c, cnt_end):
-        // CTA 0 starts at 0, CTA j >= 1 at head + j * fill_chunk.
-        const uint64_t s = cnt_end - c[i], e = cnt_end;
-        if (s == 0) a.start_run[0] = k;
-        if (e > a.head) {
-            uint64_t lo = (s > a.head) ? (s - a.head + a.fill_chunk - 1) / a.fill_chunk : 1;
-            if (lo < 1) lo = 1;
-            uint64_t hi = (e - a.head + a.fill_chunk - 1) / a.fill_chunk;
-            if (hi > a.fill_ctas) hi = a.fill_ctas;
-            for (uint64_t j = lo; j < hi; j++) a.start_run[j] = k;
+        if (v == a.R - 1) {
+            a.ctl->num_runs = runs;
+            if (cnt_end != (uint32_t)a.n) atomicOr(&a.ctl->status, kDevKeyOutOfRange);
+        }
+        if (c[i] > 0) {
+            a.run_end[runs - 1] = cnt_end;
+            a.run_val[runs - 1] = (int32_t)((uint32_t)a.minVal + v);
+        }
+    }
+    __syncthreads();
+
+    // Output CTA j starts at P0(j): P0(0) = 0, P0(j) = head + j * fill_chunk.
+    // The chunk's values cover positions [pos_lo, pos_hi).
+    const uint32_t pos_lo = (uint32_t)chunk_prefix;
+    const uint32_t pos_hi = s_cdf[kScanChunk - 1];
+    if (pos_hi > pos_lo) {
+        const uint32_t fc = (uint32_t)a.fill_chunk, head = a.head;
+        // First CTA j with P0(j) >= pos (P0 is increasing in j).
+        auto first_cta_at_or_after = [&](uint32_t pos) -> uint32_t {
+            if (pos == 0) return 0u;
+            if ((uint64_t)pos <= (uint64_t)head + fc) return 1u;
+            return (uint32_t)(((uint64_t)pos - head + fc - 1) / fc);
+        };
+        const uint32_t j_lo = first_cta_at_or_after(pos_lo);
+        const uint32_t j_hi = min(first_cta_at_or_after(pos_hi), a.fill_ctas);
+        for (uint32_t j = j_lo + tid; j < j_hi; j += kScanThreads) {
+            const uint32_t p0 = (j == 0) ? 0u : head + j * fc;
+            // Smallest value of the chunk whose CDF exceeds p0 (Algorithm 7's rule).
+            int lo = 0, hi = kScanChunk - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi) >> 1;
+                if (s_cdf[mid] > p0) hi = mid; else lo = mid + 1;
+            }
+            a.start_run[j] = s_runs[lo] - 1;
         }
     }
 }
 
 cudaError_t launch_scan(const ScanArgs &a, cudaStream_t s) {
-    scan_kernel<<<a.chunks, kScanThreads, 0, s>>>(a);
-    return cudaGetLastError();
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(a.chunks);
+    cfg.blockDim = dim3(kScanThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, scan_kernel, a);
 }
 
 }  // namespace rtcdf

@@ -168,6 +168,24 @@ def test_caller_workspace_reused_across_ranges():
         assert_matches_oracle(x, out, 5, 5 + R)
 
 
+def test_workspace_exactly_sized_for_mixed_ranges():
+    """One caller workspace of exactly the largest requirement and ranges that
+    grow and shrink between calls: every sort must find its histogram region
+    zeroed by the previous one."""
+    Rs = [128, 20480, 128, 4097, 65536, 8192, 128, 1 << 17, 3000]
+    ws_bytes = max(rtcdf.rtcdf_workspace_size(R) for R in Rs)
+    ws = torch.zeros(ws_bytes // 4, dtype=torch.int32, device="cuda")
+    s = stream_handle()
+    for i, R in enumerate(Rs):
+        x = dev_keys(500_000 + 7 * i, -3, R, DISTS[i % 3], gen.derive_seed(18, i))
+        out = torch.empty_like(x)
+        rc = rtcdf.rtcdf_sort_ws(x.data_ptr(), out.data_ptr(), x.numel(), -3, -3 + R,
+                                 ws.data_ptr(), ws_bytes, s)
+        assert rc == rtcdf.OK
+        assert rtcdf.rtcdf_ws_status_get(ws.data_ptr(), s) == (rtcdf.OK, 0)
+        assert_matches_oracle(x, out, -3, -3 + R)
+
+
 def test_two_streams_do_not_share_workspace():
     s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
     xs = [dev_keys(2_000_000, 0, R, gen.UNIFORM, R) for R in (128, 1 << 18)]
