@@ -234,6 +234,99 @@ def cub_comparison(cases, ins, outs, n, stream, nsteps, ours_ms):
     return rows
 
 
+def batched_comparison(args, stream, num_segments=4096):
+    """Batched workload: 4096 segments, lengths log-uniform in [1e3, 1e6],
+    R log-uniform in [2^7, 2^16], minVal uniform in [-2^20, 2^20], mixed
+    shapes.  One persistent launch (graph-captured) against looped
+    rtcdf_sort calls (plain and graph-captured), keys/s of each."""
+    import numpy as np
+    import torch
+    from paper_2609_00843_gb300 import gen, rtcdf
+    sh = stream.cuda_stream
+    L, mn, R, dist, seeds = gen.batched_segments(gen.derive_seed(4), num_segments)
+    offs = np.zeros(num_segments + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(L)
+    total = int(offs[-1])
+    mx = mn + R
+    x = torch.empty(total, dtype=torch.int32, device="cuda")
+    out = torch.empty_like(x)
+    for i in range(num_segments):
+        gen.keys_device(x.data_ptr() + 4 * int(offs[i]), int(L[i]), int(mn[i]), int(R[i]),
+                        int(dist[i]), int(seeds[i]), stream=sh)
+    stream.synchronize()
+    plan = rtcdf.BatchPlan(offs, mn, mx)
+    wsb = plan.workspace_size()
+    ws = torch.zeros(wsb // 4 + 64, dtype=torch.int32, device="cuda")
+    steps = max(3, min(args.steps, 10))
+
+    def timed(fn, reps):
+        # Everything (including graph replays, which launch on torch's current
+        # stream) runs on `stream`, where the events are recorded.
+        with torch.cuda.stream(stream):
+            fn()
+            stream.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                fn()
+            e1.record(stream)
+            stream.synchronize()
+        return e0.elapsed_time(e1) / reps
+
+    def batched():
+        rc = plan.run(x.data_ptr(), out.data_ptr(), ws.data_ptr(), wsb, sh)
+        if rc != rtcdf.OK:
+            raise rtcdf.RtcdfError(rc, "rtcdf_sort_batched_ws")
+    ms_batched = timed(batched, steps)
+    rc, bits = rtcdf.rtcdf_batch_status_get(ws.data_ptr(), sh)
+    if rc != rtcdf.OK:
+        raise rtcdf.RtcdfError(rc, "batched device status")
+    ref = out.clone()
+
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        batched()
+    ms_batched_graph = timed(g.replay, steps)
+
+    # Looped single-array calls on one stream (library workspace reserved).
+    rtcdf.rtcdf_reserve(int(R.max()), sh)
+    o_ptr, x_ptr = out.data_ptr(), x.data_ptr()
+    segs = [(int(offs[i]), int(L[i]), int(mn[i]), int(mx[i])) for i in range(num_segments)]
+
+    def looped():
+        for off, n, a, b in segs:
+            rc = rtcdf.rtcdf_sort(x_ptr + 4 * off, o_ptr + 4 * off, n, a, b, sh)
+            if rc != rtcdf.OK:
+                raise rtcdf.RtcdfError(rc, "rtcdf_sort")
+    ms_looped = timed(looped, max(2, steps // 3))
+    same = bool(torch.equal(out, ref))
+    g2 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g2, stream=stream):
+        looped()
+    ms_looped_graph = timed(g2.replay, steps)
+    same = same and bool(torch.equal(out, ref))
+    info = plan.info()
+    plan.close()
+    res = {
+        "workload": "4096 segments: n log-uniform [1e3,1e6], R log-uniform [2^7,2^16], "
+                    "minVal uniform [-2^20,2^20], mixed uniform/normal/all-equal",
+        "total_keys": total,
+        "batched_graph_GKeys_s": round(total / (ms_batched_graph * 1e-3) / 1e9, 2),
+        "batched_GKeys_s": round(total / (ms_batched * 1e-3) / 1e9, 2),
+        "looped_GKeys_s": round(total / (ms_looped * 1e-3) / 1e9, 2),
+        "looped_graph_GKeys_s": round(total / (ms_looped_graph * 1e-3) / 1e9, 2),
+        "batched_graph_ms": round(ms_batched_graph, 4), "batched_ms": round(ms_batched, 4),
+        "looped_ms": round(ms_looped, 4), "looped_graph_ms": round(ms_looped_graph, 4),
+        "speedup_vs_looped_graph": round(ms_looped_graph / ms_batched_graph, 2),
+        "frac_8n_roofline": round(8 * total / (ms_batched_graph * 1e-3) / 1e9 / peaks()[0], 4),
+        "outputs_equal": same, "plan": info,
+    }
+    del x, out, ws, ref
+    torch.cuda.empty_cache()
+    return res
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -243,6 +336,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cub", action="store_true", help="skip the CUB radix-sort comparison")
+    ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-looped comparison")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--preheat-s", type=float, default=0.5,
                     help="seconds of untimed load after warm-up so clocks settle")
@@ -445,6 +539,9 @@ def main():
     # on keys normalised to uint32 (normalise / denormalise timed apart).
     if not args.no_cub and rank == 0:
         line["cub_comparison"] = cub_comparison(cases, ins, outs, n, stream, nsteps, solo_ms)
+
+    if not args.no_batched and rank == 0:
+        line["batched"] = batched_comparison(args, stream)
 
     # End to end through the C ABI: pinned host input -> device -> sort -> host.
     if not args.no_e2e:

@@ -156,6 +156,52 @@ rtcdf_status rtcdf_sort_ex(const int32_t *in, int32_t *out, uint64_t n, int64_t 
                            rtcdf_stream_t stream);
 
 /*
+ * Segmented sort: many independent arrays ("segments") sorted by one
+ * persistent launch.  Segment s is in[seg_offsets[s] .. seg_offsets[s+1]),
+ * its keys lie in [seg_minVal[s], seg_maxVal[s]) (R_s <= 2^20), and it is
+ * written sorted to the same positions of `out`.  The method per segment is
+ * Algorithms 4-7 unchanged; segments with fewer than 65536 keys (and R_s <=
+ * 65536) are sorted entirely inside one CTA, larger ones are split into
+ * histogram, scan and output work items with per-segment dependencies.
+ *
+ * rtcdf_batch_plan_create builds the work list from HOST arrays
+ * (seg_offsets: S+1 entries, nondecreasing; seg_minVal / seg_maxVal: S) and
+ * uploads it (this allocates and synchronises; do it once per segment layout).
+ * rtcdf_sort_batched_ws then runs it with no host work and no allocation
+ * (capturable in a CUDA graph; replay with new keys of the same shapes); its
+ * workspace (rtcdf_batch_workspace_size bytes, 256-byte aligned) must be
+ * zero-filled before first use and is left zero-filled except for the status
+ * word, read with rtcdf_batch_status_get.  rtcdf_sort_batched is the one-shot
+ * form: plan, allocate, run, read the status, free -- it synchronises.
+ */
+typedef struct rtcdf_batch_plan rtcdf_batch_plan;
+
+typedef struct {
+    uint32_t num_segments;
+    uint32_t small_segments;   /* sorted inside one CTA */
+    uint32_t large_segments;   /* split into work items */
+    uint32_t work_items;
+    uint32_t workers;          /* persistent CTAs (one per SM) */
+    uint32_t reserved;
+    uint64_t total_keys;
+    uint64_t workspace_bytes;
+} rtcdf_batch_info;
+
+rtcdf_status rtcdf_batch_plan_create(const int64_t *seg_offsets, const int64_t *seg_minVal,
+                                     const int64_t *seg_maxVal, int32_t num_segments,
+                                     rtcdf_batch_plan **plan);
+rtcdf_status rtcdf_batch_plan_destroy(rtcdf_batch_plan *plan);
+rtcdf_status rtcdf_batch_workspace_size(const rtcdf_batch_plan *plan, size_t *bytes);
+rtcdf_status rtcdf_batch_plan_info(const rtcdf_batch_plan *plan, rtcdf_batch_info *info);
+rtcdf_status rtcdf_sort_batched_ws(const rtcdf_batch_plan *plan, const int32_t *in, int32_t *out,
+                                   void *workspace, size_t ws_bytes, rtcdf_stream_t stream);
+rtcdf_status rtcdf_batch_status_get(void *workspace, rtcdf_stream_t stream,
+                                    int32_t *device_status);
+rtcdf_status rtcdf_sort_batched(const int32_t *in, int32_t *out, const int64_t *seg_offsets,
+                                const int64_t *seg_minVal, const int64_t *seg_maxVal,
+                                int32_t num_segments, rtcdf_stream_t stream);
+
+/*
  * rtcdf_sort_static -- the sort without any allocation, for callers that
  * cannot allocate device memory: code running under another framework's
  * memory manager that owns all device memory, serving loops whose memory

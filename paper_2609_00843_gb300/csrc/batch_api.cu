@@ -1,0 +1,246 @@
+// Host side of the segmented sort: the planner that turns per-segment shapes
+// into the persistent launch's work list, and the C entry points
+// (rtcdf_batch_* in include/rtcdf.h).
+//
+// The plan is built once from host-side segment metadata (offsets and ranges)
+// and uploaded; running it needs no host work, so it can be captured in a
+// CUDA graph and replayed for new keys with the same segment shapes.
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "../../include/rtcdf.h"
+#include "batched.h"
+
+using namespace rtcdf;
+
+struct rtcdf_batch_plan {
+    int device = 0;
+    int workers = 0;
+    uint32_t num_segs = 0, num_items = 0;
+    uint64_t total_keys = 0;
+    size_t ws_bytes = 0;          // caller workspace needed
+    size_t ctl_off = 0, segctl_off = 0;
+    BatchSeg *d_segs = nullptr;
+    BatchItem *d_items = nullptr;
+    // counts, for reporting
+    uint32_t small_segs = 0, large_segs = 0;
+    uint32_t hist_items = 0, fill_items = 0;
+};
+
+namespace {
+
+constexpr uint64_t kHistChunk = 1ull << 17;   // keys per HIST item
+constexpr uint32_t kFillChunk = 1u << 16;     // positions per FILL item
+
+size_t words_align(size_t words) { return (words + 63) / 64 * 64; }  // 256-byte units
+
+}  // namespace
+
+extern "C" {
+
+rtcdf_status rtcdf_batch_plan_create(const int64_t *seg_offsets, const int64_t *seg_minVal,
+                                     const int64_t *seg_maxVal, int32_t num_segments,
+                                     rtcdf_batch_plan **plan_out) {
+    if (!plan_out || num_segments < 0) return RTCDF_ERR_INVALID_ARG;
+    *plan_out = nullptr;
+    if (num_segments > 0 && (!seg_offsets || !seg_minVal || !seg_maxVal)) return RTCDF_ERR_INVALID_ARG;
+    const uint32_t S = (uint32_t)num_segments;
+    if (S > 0 && seg_offsets[0] < 0) return RTCDF_ERR_INVALID_ARG;
+    for (uint32_t s = 0; s < S; s++) {
+        if (seg_offsets[s + 1] < seg_offsets[s]) return RTCDF_ERR_INVALID_ARG;
+        if (seg_offsets[s + 1] - seg_offsets[s] >= (int64_t)1 << 32) return RTCDF_ERR_INVALID_ARG;
+        if (seg_minVal[s] < INT32_MIN || seg_maxVal[s] > ((int64_t)1 << 31)) return RTCDF_ERR_RANGE;
+        if (seg_maxVal[s] <= seg_minVal[s] || seg_maxVal[s] - seg_minVal[s] > (int64_t)kBatchMaxR)
+            return RTCDF_ERR_RANGE;
+    }
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RTCDF_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return RTCDF_ERR_CUDA;
+
+    rtcdf_batch_plan *p = new rtcdf_batch_plan();
+    p->device = dev;
+    p->workers = sms;  // one 1024-thread worker CTA per SM
+    p->num_segs = S;
+    std::vector<BatchSeg> segs(S);
+    std::vector<BatchItem> hist, small, scan, fill;
+
+    // Workspace (in 32-bit words): control block, per-segment control, then
+    // per large segment its histogram (zero between runs) and run tables.
+    size_t w = 0;
+    p->ctl_off = w;     w += words_align(sizeof(BatchCtl) / 4);
+    p->segctl_off = w;  w += words_align((size_t)S * sizeof(BatchSegCtl) / 4);
+    for (uint32_t s = 0; s < S; s++) {
+        BatchSeg &g = segs[s];
+        memset(&g, 0, sizeof(g));
+        g.off = (uint64_t)seg_offsets[s];
+        g.n = (uint32_t)(seg_offsets[s + 1] - seg_offsets[s]);
+        g.R = (uint32_t)(seg_maxVal[s] - seg_minVal[s]);
+        g.minVal = (int32_t)seg_minVal[s];
+        p->total_keys += g.n;
+        if (g.n == 0) continue;
+        if (g.n <= kBatchSmallMaxN && g.R <= kBatchSmallMaxR) {
+            small.push_back(BatchItem{kItemSmall, s, 0, 0, 0, 0});
+            p->small_segs++;
+            continue;
+        }
+        p->large_segs++;
+        g.m = (g.R + kBatchTileMax - 1) / kBatchTileMax;
+        g.T = (g.R + g.m - 1) / g.m;
+        const uint64_t chunks = (g.n + kHistChunk - 1) / kHistChunk;
+        g.hist_items = (uint32_t)(chunks * g.m);
+        for (uint64_t c = 0; c < chunks; c++)
+            for (uint32_t t = 0; t < g.m; t++)
+                hist.push_back(BatchItem{kItemHist, s, c * kHistChunk,
+                                         std::min<uint64_t>(g.n, (c + 1) * kHistChunk), t, 0});
+        scan.push_back(BatchItem{kItemScan, s, 0, 0, 0, 0});
+        g.fill_chunk = kFillChunk;
+        g.fill_items = (g.n + kFillChunk - 1) / kFillChunk;
+        for (uint32_t f = 0; f < g.fill_items; f++)
+            fill.push_back(BatchItem{kItemFill, s, (uint64_t)f * kFillChunk,
+                                     std::min<uint64_t>(g.n, (uint64_t)(f + 1) * kFillChunk), 0, f});
+        g.hist_off = w;      w += words_align((g.R + kBatchScanChunk - 1) / kBatchScanChunk * kBatchScanChunk);
+        g.run_end_off = w;   w += words_align(g.R);
+        g.run_val_off = w;   w += words_align(g.R);
+        g.start_run_off = w; w += words_align(g.fill_items);
+    }
+    p->ws_bytes = w * 4;
+    // Queue order: HIST (largest segments first), SMALL (largest first), SCAN,
+    // FILL -- every item a worker can wait on precedes it in the queue.
+    auto by_size = [&](const BatchItem &x, const BatchItem &y) {
+        const uint64_t cx = (uint64_t)segs[x.seg].n + segs[x.seg].R;
+        const uint64_t cy = (uint64_t)segs[y.seg].n + segs[y.seg].R;
+        return cx != cy ? cx > cy : x.seg < y.seg;
+    };
+    std::stable_sort(hist.begin(), hist.end(), [&](const BatchItem &x, const BatchItem &y) {
+        return x.seg != y.seg ? by_size(x, y) : false;
+    });
+    std::stable_sort(small.begin(), small.end(), by_size);
+    std::vector<BatchItem> items;
+    items.reserve(hist.size() + small.size() + scan.size() + fill.size());
+    items.insert(items.end(), hist.begin(), hist.end());
+    items.insert(items.end(), small.begin(), small.end());
+    items.insert(items.end(), scan.begin(), scan.end());
+    items.insert(items.end(), fill.begin(), fill.end());
+    p->num_items = (uint32_t)items.size();
+    p->hist_items = (uint32_t)hist.size();
+    p->fill_items = (uint32_t)fill.size();
+
+    if (S > 0 && cudaMalloc(&p->d_segs, sizeof(BatchSeg) * S) != cudaSuccess) {
+        delete p;
+        return RTCDF_ERR_NO_MEMORY;
+    }
+    if (!items.empty() && cudaMalloc(&p->d_items, sizeof(BatchItem) * items.size()) != cudaSuccess) {
+        cudaFree(p->d_segs);
+        delete p;
+        return RTCDF_ERR_NO_MEMORY;
+    }
+    if ((S > 0 && cudaMemcpy(p->d_segs, segs.data(), sizeof(BatchSeg) * S, cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (!items.empty() && cudaMemcpy(p->d_items, items.data(), sizeof(BatchItem) * items.size(),
+                                      cudaMemcpyHostToDevice) != cudaSuccess)) {
+        cudaFree(p->d_segs);
+        cudaFree(p->d_items);
+        delete p;
+        return RTCDF_ERR_CUDA;
+    }
+    *plan_out = p;
+    return RTCDF_OK;
+}
+
+rtcdf_status rtcdf_batch_plan_destroy(rtcdf_batch_plan *plan) {
+    if (!plan) return RTCDF_OK;
+    cudaFree(plan->d_segs);
+    cudaFree(plan->d_items);
+    delete plan;
+    return RTCDF_OK;
+}
+
+rtcdf_status rtcdf_batch_workspace_size(const rtcdf_batch_plan *plan, size_t *bytes) {
+    if (!plan || !bytes) return RTCDF_ERR_INVALID_ARG;
+    *bytes = plan->ws_bytes;
+    return RTCDF_OK;
+}
+
+rtcdf_status rtcdf_batch_plan_info(const rtcdf_batch_plan *plan, rtcdf_batch_info *info) {
+    if (!plan || !info) return RTCDF_ERR_INVALID_ARG;
+    memset(info, 0, sizeof(*info));
+    info->num_segments = plan->num_segs;
+    info->total_keys = plan->total_keys;
+    info->small_segments = plan->small_segs;
+    info->large_segments = plan->large_segs;
+    info->work_items = plan->num_items;
+    info->workers = (uint32_t)plan->workers;
+    info->workspace_bytes = plan->ws_bytes;
+    return RTCDF_OK;
+}
+
+rtcdf_status rtcdf_sort_batched_ws(const rtcdf_batch_plan *plan, const int32_t *in, int32_t *out,
+                                   void *workspace, size_t ws_bytes, rtcdf_stream_t stream) {
+    if (!plan) return RTCDF_ERR_INVALID_ARG;
+    if (plan->num_items == 0) return RTCDF_OK;
+    if (!in || !out || !workspace) return RTCDF_ERR_INVALID_ARG;
+    if (((uintptr_t)in & 3) || ((uintptr_t)out & 3) || ((uintptr_t)workspace & 255))
+        return RTCDF_ERR_INVALID_ARG;
+    if ((const void *)in != (const void *)out) {
+        const uintptr_t x = (uintptr_t)in, y = (uintptr_t)out, b = plan->total_keys * 4;
+        if (x < y + b && y < x + b) return RTCDF_ERR_INVALID_ARG;
+    }
+    if (ws_bytes < plan->ws_bytes) return RTCDF_ERR_NO_MEMORY;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RTCDF_ERR_CUDA;
+    if (dev != plan->device) return RTCDF_ERR_INVALID_ARG;
+    uint32_t *ws = (uint32_t *)workspace;
+    BatchArgs a;
+    a.in = in;
+    a.out = out;
+    a.segs = plan->d_segs;
+    a.items = plan->d_items;
+    a.num_items = plan->num_items;
+    a.num_segs = plan->num_segs;
+    a.ws_u32 = ws;
+    a.ctl = (BatchCtl *)(ws + plan->ctl_off);
+    a.seg_ctl = (BatchSegCtl *)(ws + plan->segctl_off);
+    if (launch_batched(a, plan->workers, (cudaStream_t)stream) != cudaSuccess) return RTCDF_ERR_CUDA;
+    return RTCDF_OK;
+}
+
+rtcdf_status rtcdf_batch_status_get(void *workspace, rtcdf_stream_t stream, int32_t *device_status) {
+    if (!workspace) return RTCDF_ERR_INVALID_ARG;
+    BatchCtl *ctl = (BatchCtl *)workspace;  // the control block is first
+    uint32_t v = 0;
+    if (cudaMemcpyAsync(&v, &ctl->status, 4, cudaMemcpyDeviceToHost, (cudaStream_t)stream) != cudaSuccess)
+        return RTCDF_ERR_CUDA;
+    if (cudaMemsetAsync(&ctl->status, 0, 4, (cudaStream_t)stream) != cudaSuccess) return RTCDF_ERR_CUDA;
+    if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return RTCDF_ERR_CUDA;
+    if (device_status) *device_status = (int32_t)v;
+    if (v & kDevKeyOutOfRange) return RTCDF_ERR_KEY_OUT_OF_RANGE;
+    if (v & kDevTimeout) return RTCDF_ERR_TIMEOUT;
+    return RTCDF_OK;
+}
+
+rtcdf_status rtcdf_sort_batched(const int32_t *in, int32_t *out, const int64_t *seg_offsets,
+                                const int64_t *seg_minVal, const int64_t *seg_maxVal,
+                                int32_t num_segments, rtcdf_stream_t stream) {
+    rtcdf_batch_plan *plan = nullptr;
+    rtcdf_status st = rtcdf_batch_plan_create(seg_offsets, seg_minVal, seg_maxVal, num_segments, &plan);
+    if (st) return st;
+    void *ws = nullptr;
+    cudaStream_t s = (cudaStream_t)stream;
+    const size_t bytes = std::max<size_t>(plan->ws_bytes, 256);
+    if (cudaMallocAsync(&ws, bytes, s) != cudaSuccess) {
+        rtcdf_batch_plan_destroy(plan);
+        return RTCDF_ERR_NO_MEMORY;
+    }
+    st = RTCDF_OK;
+    if (cudaMemsetAsync(ws, 0, bytes, s) != cudaSuccess) st = RTCDF_ERR_CUDA;
+    if (!st) st = rtcdf_sort_batched_ws(plan, in, out, ws, bytes, stream);
+    int32_t bits = 0;
+    const rtcdf_status dst = rtcdf_batch_status_get(ws, stream, &bits);  // synchronises `stream`
+    cudaFreeAsync(ws, s);
+    cudaStreamSynchronize(s);
+    rtcdf_batch_plan_destroy(plan);
+    return st ? st : dst;
+}
+
+}  // extern "C"

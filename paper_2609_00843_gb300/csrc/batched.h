@@ -1,0 +1,63 @@
+// Internal declarations of the segmented (batched) RT-CDF launch.
+#pragma once
+
+#include "rtcdf_internal.h"
+
+namespace rtcdf {
+
+constexpr int kBatchThreads = 1024;
+constexpr size_t kBatchSmemBytes = 192 * 1024;       // one worker CTA per SM
+constexpr uint32_t kBatchSmallMaxN = 65535;          // 16-bit counters are exact below 2^16
+constexpr uint32_t kBatchSmallMaxR = 65536;          // 16-bit counters fill 128 KB
+constexpr uint32_t kBatchTileMax = 49152;            // 32-bit tile histogram in 192 KB
+constexpr uint32_t kBatchScanChunk = 4096;           // bins per pass of a segment scan
+constexpr uint64_t kBatchMaxR = 1ull << 20;
+
+enum : uint32_t { kItemHist = 0, kItemSmall = 1, kItemScan = 2, kItemFill = 3 };
+
+// One segment (all offsets in 32-bit words of the workspace).
+struct BatchSeg {
+    uint64_t off;          // first element of the segment in `in` / `out`
+    uint32_t n, R;
+    int32_t minVal;
+    uint32_t T, m;         // tile width and tiles (large segments)
+    uint32_t hist_items;   // HIST items the SCAN waits for
+    uint32_t fill_items, fill_chunk;
+    uint64_t hist_off, run_end_off, run_val_off, start_run_off;
+};
+
+struct BatchItem {
+    uint32_t kind, seg;
+    uint64_t a, b;         // HIST: key range; FILL: position range (segment-relative)
+    uint32_t tile;         // HIST: range tile
+    uint32_t aux;          // FILL: index among the segment's FILL items
+};
+
+struct BatchSegCtl {
+    uint32_t hist_done;    // HIST items finished
+    uint32_t scan_done;    // 1 once the SCAN has published the run table
+    uint32_t num_runs;
+    uint32_t pad;
+};
+
+struct BatchCtl {
+    uint32_t status;
+    uint32_t queue_head;
+    uint32_t workers_done;
+    uint32_t pad[61];
+};
+
+struct BatchArgs {
+    const int32_t *in;
+    int32_t *out;
+    const BatchSeg *segs;
+    const BatchItem *items;
+    uint32_t num_items, num_segs;
+    uint32_t *ws_u32;       // workspace base
+    BatchCtl *ctl;
+    BatchSegCtl *seg_ctl;
+};
+
+cudaError_t launch_batched(const BatchArgs &a, int workers, cudaStream_t s);
+
+}  // namespace rtcdf

@@ -50,6 +50,13 @@ class Debug(ctypes.Structure):
                 ("tile_offset", ctypes.c_void_p), ("stage_events", ctypes.c_void_p * 4)]
 
 
+class BatchInfo(ctypes.Structure):
+    _fields_ = [("num_segments", ctypes.c_uint32), ("small_segments", ctypes.c_uint32),
+                ("large_segments", ctypes.c_uint32), ("work_items", ctypes.c_uint32),
+                ("workers", ctypes.c_uint32), ("reserved", ctypes.c_uint32),
+                ("total_keys", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64)]
+
+
 def declared_functions() -> list[str]:
     """Names of the functions declared in include/rtcdf.h."""
     text = open(HEADER).read()
@@ -80,9 +87,19 @@ def lib():
             L.rtcdf_ws_status_get.argtypes = [vp, vp, ctypes.POINTER(i32)]
             L.rtcdf_plan.argtypes = [u64, i64, ctypes.POINTER(Params)]
             L.rtcdf_sort_static.argtypes = [vp, vp, u64, i64, i64, vp]
+            L.rtcdf_batch_plan_create.argtypes = [vp, vp, vp, i32, ctypes.POINTER(vp)]
+            L.rtcdf_batch_plan_destroy.argtypes = [vp]
+            L.rtcdf_batch_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
+            L.rtcdf_batch_plan_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
+            L.rtcdf_sort_batched_ws.argtypes = [vp, vp, vp, vp, sz, vp]
+            L.rtcdf_batch_status_get.argtypes = [vp, vp, ctypes.POINTER(i32)]
+            L.rtcdf_sort_batched.argtypes = [vp, vp, vp, vp, vp, i32, vp]
             for f in ("rtcdf_sort", "rtcdf_sort_ws", "rtcdf_sort_ex", "rtcdf_reserve",
                       "rtcdf_workspace_size", "rtcdf_status_get", "rtcdf_ws_status_get",
-                      "rtcdf_plan", "rtcdf_sort_static"):
+                      "rtcdf_plan", "rtcdf_sort_static", "rtcdf_batch_plan_create",
+                      "rtcdf_batch_plan_destroy", "rtcdf_batch_workspace_size",
+                      "rtcdf_batch_plan_info", "rtcdf_sort_batched_ws", "rtcdf_batch_status_get",
+                      "rtcdf_sort_batched"):
                 getattr(L, f).restype = ctypes.c_int
             L.rtcdf_status_str.argtypes = [ctypes.c_int]
             L.rtcdf_status_str.restype = ctypes.c_char_p
@@ -110,6 +127,70 @@ def rtcdf_sort_ex(in_ptr, out_ptr, n, minVal, maxVal, params: Params | None, ws_
 def rtcdf_sort_static(in_ptr: int, out_ptr: int, n: int, minVal: int, maxVal: int,
                       stream: int = 0) -> int:
     return lib().rtcdf_sort_static(in_ptr, out_ptr, n, minVal, maxVal, stream)
+
+
+def _i64_array(xs):
+    import numpy as np
+    a = np.ascontiguousarray(np.asarray(xs, dtype=np.int64))
+    return a, a.ctypes.data_as(ctypes.c_void_p)
+
+
+class BatchPlan:
+    """A segmented-sort plan (rtcdf_batch_plan_create / _destroy)."""
+
+    def __init__(self, seg_offsets, seg_minVal, seg_maxVal):
+        self._keep = [_i64_array(seg_offsets), _i64_array(seg_minVal), _i64_array(seg_maxVal)]
+        S = len(self._keep[1][0])
+        if len(self._keep[0][0]) != S + 1 or len(self._keep[2][0]) != S:
+            raise ValueError("seg_offsets needs S+1 entries, seg_minVal/seg_maxVal S entries")
+        h = ctypes.c_void_p(0)
+        rc = lib().rtcdf_batch_plan_create(self._keep[0][1], self._keep[1][1], self._keep[2][1], S,
+                                           ctypes.byref(h))
+        if rc != OK:
+            raise RtcdfError(rc, "rtcdf_batch_plan_create")
+        self.handle = h
+
+    def workspace_size(self) -> int:
+        out = ctypes.c_size_t(0)
+        rc = lib().rtcdf_batch_workspace_size(self.handle, ctypes.byref(out))
+        if rc != OK:
+            raise RtcdfError(rc, "rtcdf_batch_workspace_size")
+        return out.value
+
+    def info(self) -> dict:
+        inf = BatchInfo()
+        rc = lib().rtcdf_batch_plan_info(self.handle, ctypes.byref(inf))
+        if rc != OK:
+            raise RtcdfError(rc, "rtcdf_batch_plan_info")
+        return {f: getattr(inf, f) for f, _ in BatchInfo._fields_ if f != "reserved"}
+
+    def run(self, in_ptr: int, out_ptr: int, ws_ptr: int, ws_bytes: int, stream: int = 0) -> int:
+        return lib().rtcdf_sort_batched_ws(self.handle, in_ptr, out_ptr, ws_ptr, ws_bytes, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            lib().rtcdf_batch_plan_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def rtcdf_batch_status_get(ws_ptr: int, stream: int = 0) -> tuple[int, int]:
+    bits = ctypes.c_int32(0)
+    rc = lib().rtcdf_batch_status_get(ws_ptr, stream, ctypes.byref(bits))
+    return rc, bits.value
+
+
+def rtcdf_sort_batched(in_ptr: int, out_ptr: int, seg_offsets, seg_minVal, seg_maxVal,
+                       stream: int = 0) -> int:
+    o, op = _i64_array(seg_offsets)
+    mn, mnp = _i64_array(seg_minVal)
+    mx, mxp = _i64_array(seg_maxVal)
+    return lib().rtcdf_sort_batched(in_ptr, out_ptr, op, mnp, mxp, len(mn), stream)
 
 
 def rtcdf_reserve(max_R: int, stream: int = 0) -> int:

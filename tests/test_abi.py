@@ -88,3 +88,22 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(rtcdf, "LIB_PATH", str(tmp_path / "nope.so"))
     with pytest.raises(RuntimeError, match="no CPU fallback"):
         rtcdf.rtcdf_sort(0, 0, 0, 0, 1, 0)
+
+
+def test_batched_plan_rejects_bad_metadata_on_host():
+    import ctypes
+    import numpy as np
+    lib = rtcdf.lib()
+    h = ctypes.c_void_p(0)
+
+    def create(offs, mn, mx):
+        o = np.asarray(offs, np.int64); a = np.asarray(mn, np.int64); b = np.asarray(mx, np.int64)
+        return lib.rtcdf_batch_plan_create(o.ctypes.data_as(ctypes.c_void_p),
+                                           a.ctypes.data_as(ctypes.c_void_p),
+                                           b.ctypes.data_as(ctypes.c_void_p), len(a), ctypes.byref(h))
+    assert create([0, 10, 5], [0, 0], [4, 4]) == rtcdf.ERR_INVALID_ARG       # offsets decrease
+    assert create([-1, 10], [0], [4]) == rtcdf.ERR_INVALID_ARG               # negative offset
+    assert create([0, 10], [3], [3]) == rtcdf.ERR_RANGE                      # R = 0
+    assert create([0, 10], [0], [(1 << 20) + 1]) == rtcdf.ERR_RANGE          # R too wide
+    assert create([0, 10], [-(1 << 31) - 1], [0]) == rtcdf.ERR_RANGE         # outside int32
+    assert lib.rtcdf_batch_plan_create(None, None, None, -1, ctypes.byref(h)) == rtcdf.ERR_INVALID_ARG

@@ -1,0 +1,135 @@
+"""Segmented (batched) sort: every segment against the CPU oracle, bit-exact."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2609_00843_gb300 import _build, gen, rtcdf
+from gpu_util import stream_handle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+    torch.cuda.init()
+
+
+def make_segments(lengths, Rs, mins, dists, seeds, pad_front=0):
+    offs = np.zeros(len(lengths) + 1, dtype=np.int64)
+    offs[1:] = np.cumsum(lengths)
+    offs += pad_front
+    total = int(offs[-1])
+    x = torch.empty(max(1, total), dtype=torch.int32, device="cuda")
+    s = stream_handle()
+    for i, n in enumerate(lengths):
+        if n:
+            gen.keys_device(x.data_ptr() + 4 * int(offs[i]), int(n), int(mins[i]), int(Rs[i]),
+                            int(dists[i]), int(seeds[i]), stream=s)
+    torch.cuda.synchronize()
+    return x, offs, np.asarray(mins, np.int64), np.asarray(mins, np.int64) + np.asarray(Rs, np.int64)
+
+
+def check_segments(x, out, offs, mins, maxs):
+    a = x.cpu().numpy()
+    b = out.cpu().numpy()
+    for s in range(len(mins)):
+        lo, hi = int(offs[s]), int(offs[s + 1])
+        want = oracle.counting_sort(a[lo:hi], int(mins[s]), int(maxs[s]))
+        got = b[lo:hi]
+        if not np.array_equal(got, want):
+            bad = np.nonzero(got != want)[0]
+            raise AssertionError(f"segment {s} (n={hi - lo}, R={maxs[s] - mins[s]}): {bad.size} "
+                                 f"positions differ, first {bad[:5].tolist()}")
+
+
+def run_plan(x, out, offs, mins, maxs):
+    plan = rtcdf.BatchPlan(offs, mins, maxs)
+    wsb = max(256, plan.workspace_size())
+    ws = torch.zeros(wsb // 4 + 64, dtype=torch.int32, device="cuda")
+    s = stream_handle()
+    rc = plan.run(x.data_ptr(), out.data_ptr(), ws.data_ptr(), wsb, s)
+    assert rc == rtcdf.OK, rtcdf.rtcdf_status_str(rc)
+    rc, bits = rtcdf.rtcdf_batch_status_get(ws.data_ptr(), s)
+    return plan, ws, wsb, rc, bits
+
+
+def test_mixed_small_and_large_segments():
+    lengths = [0, 1, 5, 1000, 65535, 65536, 200_001, 1_000_000, 3, 70_000, 50_000, 131_073]
+    Rs = [5, 1, 128, 4097, 65536, 128, 1 << 16, 1 << 14, 7, 70_000, 100_000, 1 << 20]
+    mins = [0, -5, 1000, -(1 << 20), 17, -(1 << 31), 0, -3, 5, 100, -100_000, -(1 << 19)]
+    dists = [i % 3 for i in range(len(lengths))]
+    seeds = [gen.derive_seed(30, i) for i in range(len(lengths))]
+    x, offs, mn, mx = make_segments(lengths, Rs, mins, dists, seeds)
+    out = torch.full_like(x, 0x7FFFFFFF)
+    plan, ws, wsb, rc, bits = run_plan(x, out, offs, mn, mx)
+    assert (rc, bits) == (rtcdf.OK, 0)
+    info = plan.info()
+    assert info["small_segments"] >= 4 and info["large_segments"] >= 4
+    check_segments(x, out, offs, mn, mx)
+
+
+def test_batched_workload_shapes_sample():
+    """512 segments with the batched workload's shapes (lengths log-uniform in
+    [1e3, 1e6], R log-uniform in [2^7, 2^16], minVal in [-2^20, 2^20], mixed
+    shapes), unaligned start, run twice on the same workspace."""
+    L, mn, R, dist, seeds = gen.batched_segments(gen.derive_seed(31), 512)
+    x, offs, mns, mxs = make_segments(L, R, mn, dist, seeds, pad_front=3)
+    out = torch.empty_like(x)
+    plan, ws, wsb, rc, bits = run_plan(x, out, offs, mns, mxs)
+    assert (rc, bits) == (rtcdf.OK, 0)
+    check_segments(x, out, offs, mns, mxs)
+    out.fill_(0)
+    s = stream_handle()
+    assert plan.run(x.data_ptr(), out.data_ptr(), ws.data_ptr(), wsb, s) == rtcdf.OK
+    assert rtcdf.rtcdf_batch_status_get(ws.data_ptr(), s) == (rtcdf.OK, 0)
+    check_segments(x, out, offs, mns, mxs)
+
+
+def test_graph_capture_and_replay_with_new_keys():
+    L, mn, R, dist, seeds = gen.batched_segments(gen.derive_seed(32), 200)
+    x, offs, mns, mxs = make_segments(L, R, mn, dist, seeds)
+    out = torch.empty_like(x)
+    plan = rtcdf.BatchPlan(offs, mns, mxs)
+    wsb = plan.workspace_size()
+    ws = torch.zeros(wsb // 4 + 64, dtype=torch.int32, device="cuda")
+    st = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        assert plan.run(x.data_ptr(), out.data_ptr(), ws.data_ptr(), wsb, st.cuda_stream) == 0
+    for rep in range(3):
+        seeds2 = [gen.derive_seed(33, rep, i) for i in range(len(L))]
+        x2, _, _, _ = make_segments(L, R, mn, dist, seeds2)
+        x.copy_(x2)
+        out.fill_(-1)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+        assert rtcdf.rtcdf_batch_status_get(ws.data_ptr(), st.cuda_stream) == (rtcdf.OK, 0)
+        check_segments(x, out, offs, mns, mxs)
+
+
+def test_one_shot_entry_point_and_in_place():
+    lengths = [10, 100_000, 70_000, 1]
+    Rs = [3, 1 << 12, 1 << 17, 1]
+    mins = [0, -10, 7, 4]
+    x, offs, mn, mx = make_segments(lengths, Rs, mins, [0, 1, 0, 2], [1, 2, 3, 4])
+    a = x.cpu().numpy().copy()
+    rc = rtcdf.rtcdf_sort_batched(x.data_ptr(), x.data_ptr(), offs, mn, mx, stream_handle())
+    assert rc == rtcdf.OK
+    b = x.cpu().numpy()
+    for s in range(len(lengths)):
+        lo, hi = offs[s], offs[s + 1]
+        np.testing.assert_array_equal(b[lo:hi], oracle.counting_sort(a[lo:hi], mn[s], mx[s]))
+
+
+def test_out_of_range_key_in_one_segment_reports_status():
+    lengths = [1000, 300_000]
+    for bad_seg in (0, 1):
+        x, offs, mn, mx = make_segments(lengths, [100, 1000], [0, 0], [0, 0], [5, 6])
+        x[int(offs[bad_seg]) + 17] = 100_000
+        out = torch.empty_like(x)
+        _, _, _, rc, bits = run_plan(x, out, offs, mn, mx)
+        assert rc == rtcdf.ERR_KEY_OUT_OF_RANGE and bits & rtcdf.DEV_KEY_OUT_OF_RANGE
