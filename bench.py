@@ -110,9 +110,10 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def traffic_for(kernel: str, src_files, workload_key: str):
-    """DRAM bytes per launch from a committed ncu summary, if it was captured
-    from the current kernel source; otherwise None."""
+def traffic_for(kernel: str, src_files):
+    """DRAM bytes per launch of `kernel` on the sweep arrays, averaged over the
+    ncu captures committed in profiles/ncu_traffic.json -- only if they were
+    taken from the current kernel source; otherwise None."""
     path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
     try:
         with open(path) as f:
@@ -123,10 +124,10 @@ def traffic_for(kernel: str, src_files, workload_key: str):
     for p in src_files:
         with open(os.path.join(ROOT, p), "rb") as f:
             h.update(f.read())
-    ent = table.get(kernel, {}).get(workload_key)
-    if not ent or ent.get("source_sha256") != h.hexdigest():
+    ents = [e for k, e in table.get(kernel, {}).items() if k.startswith("sweep_n1e8")]
+    if not ents or any(e.get("source_sha256") != h.hexdigest() for e in ents):
         return None
-    return ent.get("dram_bytes_per_launch")
+    return round(sum(e["dram_bytes_per_launch"] for e in ents) / len(ents))
 
 
 def run_reference(args, rank, world):
@@ -309,7 +310,7 @@ def batched_comparison(args, stream, num_segments=4096):
     info = plan.info()
     plan.close()
     res = {
-        "workload": "4096 segments: n log-uniform [1e3,1e6], R log-uniform [2^7,2^16], "
+        "workload": f"{num_segments} segments: n log-uniform [1e3,1e6], R log-uniform [2^7,2^16], "
                     "minVal uniform [-2^20,2^20], mixed uniform/normal/all-equal",
         "total_keys": total,
         "batched_graph_GKeys_s": round(total / (ms_batched_graph * 1e-3) / 1e9, 2),
@@ -337,6 +338,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cub", action="store_true", help="skip the CUB radix-sort comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-looped comparison")
+    ap.add_argument("--batched-segments", type=int, default=4096)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--preheat-s", type=float, default=0.5,
                     help="seconds of untimed load after warm-up so clocks settle")
@@ -513,7 +515,7 @@ def main():
     achieved = 4 * n / avg_launch_s / 1e9  # algorithmic: 4n bytes read (hist) or written (fill)
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4),
-                "traffic": traffic_for(kname, ksrc, "sweep_n1e8"),
+                "traffic": traffic_for(kname, ksrc),
                 "kernel": kname, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
                 "algorithmic_bytes_per_launch": 4 * n}
     whole = {"achieved_8n_GBs": round(8 * n * len(cases) / (sort_ms * 1e-3) / 1e9, 1)}
@@ -541,7 +543,7 @@ def main():
         line["cub_comparison"] = cub_comparison(cases, ins, outs, n, stream, nsteps, solo_ms)
 
     if not args.no_batched and rank == 0:
-        line["batched"] = batched_comparison(args, stream)
+        line["batched"] = batched_comparison(args, stream, args.batched_segments)
 
     # End to end through the C ABI: pinned host input -> device -> sort -> host.
     if not args.no_e2e:

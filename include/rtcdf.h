@@ -161,7 +161,7 @@ rtcdf_status rtcdf_sort_ex(const int32_t *in, int32_t *out, uint64_t n, int64_t 
  * its keys lie in [seg_minVal[s], seg_maxVal[s]) (R_s <= 2^20), and it is
  * written sorted to the same positions of `out`.  The method per segment is
  * Algorithms 4-7 unchanged; segments with fewer than 65536 keys (and R_s <=
- * 65536) are sorted entirely inside one CTA, larger ones are split into
+ * 55296) are sorted entirely inside one CTA, larger ones are split into
  * histogram, scan and output work items with per-segment dependencies.
  *
  * rtcdf_batch_plan_create builds the work list from HOST arrays
@@ -181,7 +181,7 @@ typedef struct {
     uint32_t small_segments;   /* sorted inside one CTA */
     uint32_t large_segments;   /* split into work items */
     uint32_t work_items;
-    uint32_t workers;          /* persistent CTAs (one per SM) */
+    uint32_t workers;          /* persistent CTAs (two per SM) */
     uint32_t reserved;
     uint64_t total_keys;
     uint64_t workspace_bytes;

@@ -61,7 +61,7 @@ rtcdf_status rtcdf_batch_plan_create(const int64_t *seg_offsets, const int64_t *
 
     rtcdf_batch_plan *p = new rtcdf_batch_plan();
     p->device = dev;
-    p->workers = sms;  // one 1024-thread worker CTA per SM
+    p->workers = sms * kBatchWorkersPerSM;
     p->num_segs = S;
     std::vector<BatchSeg> segs(S);
     std::vector<BatchItem> hist, small, scan, fill;

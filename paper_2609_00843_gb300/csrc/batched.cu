@@ -4,7 +4,7 @@
 // tile histogram, local CDF + offsets, output from the CDF); what is new is
 // the schedule.
 //
-// Worker CTAs (one per SM) take work items from a global queue in order:
+// Worker CTAs (two per SM) take work items from a global queue in order:
 //   1. HIST  (large segments)  histogram of a chunk of keys for one range
 //                              tile, merged into the segment's global H;
 //   2. SMALL (n_s < 65536)     the whole sort of one segment inside one CTA:
@@ -87,10 +87,29 @@ __device__ void do_small(const BatchArgs &a, const BatchSeg &g, uint32_t *sm) {
     __syncthreads();
     const int32_t *in = a.in + g.off;
     const uint32_t min_u = (uint32_t)g.minVal;
-    for (uint32_t i = tid; i < n; i += nt) {
-        const uint32_t x = (uint32_t)in[i] - min_u;
+    auto count1 = [&](int32_t key) {
+        const uint32_t x = (uint32_t)key - min_u;
         if (x < R) atomicAdd(&cnt[x >> 1], 1u << ((x & 1) * 16));
+    };
+    // 16-byte loads, eight in flight per thread, after the unaligned head.
+    const uint32_t lead_a = (uint32_t)(((16 - ((uintptr_t)in & 15)) & 15) / 4);
+    const uint32_t lead = lead_a < n ? lead_a : n;
+    const uint32_t nv = (n - lead) / 4;
+    const int4 *vin = reinterpret_cast<const int4 *>(in + lead);
+    uint32_t iv = tid;
+    for (; iv + 7 * nt < nv; iv += 8 * nt) {
+        int4 k[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) k[u] = __ldcs(vin + iv + u * nt);
+#pragma unroll
+        for (int u = 0; u < 8; u++) { count1(k[u].x); count1(k[u].y); count1(k[u].z); count1(k[u].w); }
     }
+    for (; iv < nv; iv += nt) {
+        const int4 k = __ldcs(vin + iv);
+        count1(k.x); count1(k.y); count1(k.z); count1(k.w);
+    }
+    if (tid < lead) count1(in[tid]);
+    for (uint32_t i = lead + 4 * nv + tid; i < n; i += nt) count1(in[i]);
     __syncthreads();
     // In-place inclusive CDF over the 16-bit counters (values <= n < 2^16).
     uint16_t *c16 = reinterpret_cast<uint16_t *>(cnt);
@@ -159,10 +178,12 @@ __device__ void do_hist(const BatchArgs &a, const BatchSeg &g, const BatchItem &
         y = (uint32_t)k.w - base; if (y < w) atomicAdd(&S[y], 1u);
     };
     uint64_t v = tid;
-    for (; v + 3 * nt < nv; v += 4 * nt) {
-        const int4 a0 = __ldcs(vin + v), a1 = __ldcs(vin + v + nt);
-        const int4 a2 = __ldcs(vin + v + 2 * nt), a3 = __ldcs(vin + v + 3 * nt);
-        count4(a0); count4(a1); count4(a2); count4(a3);
+    for (; v + 7 * nt < nv; v += 8 * nt) {
+        int4 k[8];
+#pragma unroll
+        for (int u = 0; u < 8; u++) k[u] = __ldcs(vin + v + u * nt);
+#pragma unroll
+        for (int u = 0; u < 8; u++) count4(k[u]);
     }
     for (; v < nv; v += nt) count4(__ldcs(vin + v));
     if (tid < lead) {
@@ -196,19 +217,30 @@ __device__ void do_scan(const BatchArgs &a, const BatchSeg &g, const BatchItem &
     uint32_t *s_cdf = sm;                      // kBatchScanChunk entries
     uint32_t *s_runs = sm + kBatchScanChunk;   // kBatchScanChunk entries
     uint32_t *s_tmp = sm + 2 * kBatchScanChunk;
-    const uint32_t items = kBatchScanChunk / nt;  // bins per thread per chunk
+    constexpr uint32_t items = kBatchScanChunk / kBatchThreads;  // bins per thread per chunk
+    static_assert(items % 4 == 0, "whole 16-byte vectors per thread");
     uint32_t cnt_prefix = 0, run_prefix = 0;
     for (uint32_t cb = 0; cb < g.R; cb += kBatchScanChunk) {
-        // This thread's bins: [cb + tid * items, + items).
+        // This thread's bins: [cb + tid * items, + items) -- H is padded to
+        // whole kBatchScanChunk blocks, so whole 16-byte vectors can be read
+        // (all loads first, then the zeroing stores).
         uint32_t cloc = 0, rloc = 0;
         const uint32_t v0 = cb + tid * items;
-        for (uint32_t i = 0; i < items; i++) {
-            const uint32_t v = v0 + i;
-            const uint32_t c = v < g.R ? H[v] : 0u;
-            if (v < g.R) H[v] = 0;  // H is left zeroed for the next run
-            s_cdf[tid * items + i] = c;
-            cloc += c;
-            rloc += (c > 0);
+        uint4 *hv = reinterpret_cast<uint4 *>(H + v0);
+        uint4 q[kBatchScanChunk / kBatchThreads / 4];
+#pragma unroll
+        for (uint32_t k = 0; k < items / 4; k++) q[k] = hv[k];
+#pragma unroll
+        for (uint32_t k = 0; k < items / 4; k++) hv[k] = make_uint4(0, 0, 0, 0);  // left zeroed
+#pragma unroll
+        for (uint32_t k = 0; k < items / 4; k++) {
+            const uint32_t c4[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                s_cdf[tid * items + 4 * k + e] = c4[e];
+                cloc += c4[e];
+                rloc += (c4[e] > 0);
+            }
         }
         uint32_t ctot = 0, rtot = 0;
         const uint32_t cex = block_excl_scan_u32(cloc, s_tmp, &ctot);
@@ -335,7 +367,7 @@ __device__ void do_fill(const BatchArgs &a, const BatchSeg &g, const BatchItem &
 
 }  // namespace
 
-__global__ void __launch_bounds__(kBatchThreads, 1) batched_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kBatchThreads, kBatchWorkersPerSM) batched_kernel(BatchArgs a) {
     extern __shared__ uint32_t sm[];
     __shared__ uint32_t s_item;
     for (;;) {

@@ -5,11 +5,12 @@
 
 namespace rtcdf {
 
-constexpr int kBatchThreads = 1024;
-constexpr size_t kBatchSmemBytes = 192 * 1024;       // one worker CTA per SM
+constexpr int kBatchThreads = 512;
+constexpr int kBatchWorkersPerSM = 2;                // one worker's stalls overlap the other's work
+constexpr size_t kBatchSmemBytes = 112 * 1024;       // per worker CTA
 constexpr uint32_t kBatchSmallMaxN = 65535;          // 16-bit counters are exact below 2^16
-constexpr uint32_t kBatchSmallMaxR = 65536;          // 16-bit counters fill 128 KB
-constexpr uint32_t kBatchTileMax = 49152;            // 32-bit tile histogram in 192 KB
+constexpr uint32_t kBatchSmallMaxR = 55296;          // 16-bit counters in 108 KB
+constexpr uint32_t kBatchTileMax = 27648;            // 32-bit tile histogram in 108 KB
 constexpr uint32_t kBatchScanChunk = 4096;           // bins per pass of a segment scan
 constexpr uint64_t kBatchMaxR = 1ull << 20;
 
