@@ -328,6 +328,57 @@ def batched_comparison(args, stream, num_segments=4096):
     return res
 
 
+def serving_comparison(count: int, budget_gb: float = 32.0):
+    """Serving workload: a Poisson stream of sort requests, n log-uniform in
+    [1e4, 1e8], R log-uniform in [2^7, 2^18], mixed shapes, 32 GB admission
+    budget.  The arrival rate is 0.9 x the throughput of sequential
+    per-request calls (measured first with every request present at t=0);
+    the same trace is then served sequentially and by the continuous-batching
+    server.  Latency = completion - arrival; a request's keys are written into
+    its device slot by the generator at admission (data arrival)."""
+    import numpy as np
+    from paper_2609_00843_gb300 import gen, rtcdf
+    seed = gen.derive_seed(5)
+    n, mn, R, dist, seeds = gen.serving_requests(seed, count)
+    mx = mn + R
+    fill = gen.fill_function_address()
+
+    def cfg():
+        return rtcdf.ServerConfig(budget_bytes=int(budget_gb * (1 << 30)), num_streams=4,
+                                  max_batch=256, single_min_keys=1 << 22, fill=fill, digests=0)
+    zero = np.zeros(count)
+    r0 = rtcdf.make_requests(n, mn, mx, dist, seeds, zero)
+    _, st0 = rtcdf.rtcdf_serve_sequential(cfg(), r0, count)
+    _, st1 = rtcdf.rtcdf_serve_trace(cfg(), r0, count)
+    rate = 0.9 * count / st0.makespan_s
+    arr = gen.poisson_arrivals(seed, count, rate)
+    reqs = rtcdf.make_requests(n, mn, mx, dist, seeds, arr)
+    out = {"workload": f"{count} requests, Poisson arrivals at 0.9 x sequential throughput "
+                       f"({rate:.0f}/s), n log-uniform [1e4,1e8], R log-uniform [2^7,2^18], "
+                       f"mixed shapes, {budget_gb:g} GB admission budget",
+           "total_keys": int(n.sum()), "arrival_rate_per_s": round(rate, 1),
+           "saturated": {"note": "every request present at t=0: capacity in keys/s",
+                         "sequential_GKeys_s": round(st0.total_keys / st0.makespan_s / 1e9, 2),
+                         "server_GKeys_s": round(st1.total_keys / st1.makespan_s / 1e9, 2),
+                         "server_vs_sequential": round(st0.makespan_s / st1.makespan_s, 3)}}
+    for name, fn in (("sequential", rtcdf.rtcdf_serve_sequential), ("server", rtcdf.rtcdf_serve_trace)):
+        res, st = fn(cfg(), reqs, count)
+        lat = np.array([res[i].done_s - arr[i] for i in range(count)])
+        ok = all(res[i].status == 0 for i in range(count))
+        out[name] = {"GKeys_s": round(st.total_keys / st.makespan_s / 1e9, 2),
+                     "makespan_s": round(st.makespan_s, 4),
+                     "p50_latency_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                     "p99_latency_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
+                     "all_ok": ok, "launches_batched": int(st.launches_batched),
+                     "launches_single": int(st.launches_single),
+                     "max_inflight": int(st.max_inflight), "peak_GB": round(st.peak_bytes / 1e9, 2)}
+    out["throughput_ratio_server_vs_sequential"] = round(
+        out["server"]["GKeys_s"] / max(1e-9, out["sequential"]["GKeys_s"]), 3)
+    out["p99_ratio_sequential_vs_server"] = round(
+        out["sequential"]["p99_latency_ms"] / max(1e-9, out["server"]["p99_latency_ms"]), 3)
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -339,6 +390,8 @@ def main():
     ap.add_argument("--no-cub", action="store_true", help="skip the CUB radix-sort comparison")
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-looped comparison")
     ap.add_argument("--batched-segments", type=int, default=4096)
+    ap.add_argument("--no-serve", action="store_true", help="skip the serving comparison")
+    ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--preheat-s", type=float, default=0.5,
                     help="seconds of untimed load after warm-up so clocks settle")
@@ -544,6 +597,9 @@ def main():
 
     if not args.no_batched and rank == 0:
         line["batched"] = batched_comparison(args, stream, args.batched_segments)
+
+    if not args.no_serve and rank == 0:
+        line["serve"] = serving_comparison(args.serve_requests)
 
     # End to end through the C ABI: pinned host input -> device -> sort -> host.
     if not args.no_e2e:

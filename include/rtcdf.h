@@ -202,6 +202,67 @@ rtcdf_status rtcdf_sort_batched(const int32_t *in, int32_t *out, const int64_t *
                                 int32_t num_segments, rtcdf_stream_t stream);
 
 /*
+ * Continuous-batching server.  A trace of sort requests (arrival times
+ * relative to its start) is served from one device slab of `budget_bytes`:
+ * requests are admitted in arrival order when their slot (input + output,
+ * 8n bytes) fits, their keys are written into the slot by `fill` (for
+ * synthetic traces: rtcdf_gen_keys has this signature), and admitted requests
+ * are launched as soon as one of `num_streams` streams is free -- a request of
+ * at least `single_min_keys` keys alone through the single-array pipeline, all
+ * other pending requests together in one segmented launch (at most
+ * `max_batch`).  Arrivals keep being admitted while launches run, and a
+ * request's memory is released when its launch completes.  With `digests`
+ * set, each result carries an order-dependent 64-bit digest of its sorted
+ * output (sum over positions i of SplitMix64's finaliser applied to
+ * (i << 32 | out[i]), mod 2^64).  Times are seconds from the trace start.
+ * rtcdf_serve_sequential serves the same trace one request at a time
+ * (rtcdf_sort_ws on one stream, waiting for each) as the comparison.
+ * Both allocate, synchronise and return when every request is done.
+ */
+typedef int (*rtcdf_fill_fn)(int32_t *dev_out, uint64_t n, uint64_t first, int64_t minVal,
+                             int64_t R, int dist, uint64_t seed, rtcdf_stream_t stream);
+
+typedef struct {
+    uint64_t budget_bytes;
+    int32_t num_streams;        /* 1..16 */
+    int32_t max_batch;          /* requests per segmented launch */
+    uint64_t single_min_keys;   /* requests this large run alone */
+    rtcdf_fill_fn fill;
+    int32_t digests;            /* nonzero: compute result digests */
+    int32_t reserved;
+} rtcdf_server_config;
+
+typedef struct {
+    uint64_t n;
+    int64_t minVal, maxVal;     /* R <= 2^20 */
+    int32_t dist;               /* passed to fill */
+    int32_t reserved;
+    uint64_t seed;              /* passed to fill */
+    double arrival_s;           /* nondecreasing along the trace */
+} rtcdf_request;
+
+typedef struct {
+    double admit_s, launch_s, done_s;
+    uint64_t digest;
+    int32_t status;             /* 0 done, else an rtcdf_status */
+    int32_t batch_id;           /* launch that served the request */
+} rtcdf_result;
+
+typedef struct {
+    double makespan_s;
+    uint64_t total_keys;
+    uint64_t launches_batched, launches_single, batched_requests;
+    uint64_t peak_bytes;
+    int32_t max_inflight;
+    int32_t reserved;
+} rtcdf_serve_stats;
+
+rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_request *reqs,
+                               int64_t count, rtcdf_result *results, rtcdf_serve_stats *stats);
+rtcdf_status rtcdf_serve_sequential(const rtcdf_server_config *cfg, const rtcdf_request *reqs,
+                                    int64_t count, rtcdf_result *results, rtcdf_serve_stats *stats);
+
+/*
  * rtcdf_sort_static -- the sort without any allocation, for callers that
  * cannot allocate device memory: code running under another framework's
  * memory manager that owns all device memory, serving loops whose memory

@@ -23,9 +23,7 @@ struct rtcdf_batch_plan {
     size_t ctl_off = 0, segctl_off = 0;
     BatchSeg *d_segs = nullptr;
     BatchItem *d_items = nullptr;
-    // counts, for reporting
     uint32_t small_segs = 0, large_segs = 0;
-    uint32_t hist_items = 0, fill_items = 0;
 };
 
 namespace {
@@ -37,55 +35,41 @@ size_t words_align(size_t words) { return (words + 63) / 64 * 64; }  // 256-byte
 
 }  // namespace
 
-extern "C" {
+namespace rtcdf {
 
-rtcdf_status rtcdf_batch_plan_create(const int64_t *seg_offsets, const int64_t *seg_minVal,
-                                     const int64_t *seg_maxVal, int32_t num_segments,
-                                     rtcdf_batch_plan **plan_out) {
-    if (!plan_out || num_segments < 0) return RTCDF_ERR_INVALID_ARG;
-    *plan_out = nullptr;
-    if (num_segments > 0 && (!seg_offsets || !seg_minVal || !seg_maxVal)) return RTCDF_ERR_INVALID_ARG;
-    const uint32_t S = (uint32_t)num_segments;
-    if (S > 0 && seg_offsets[0] < 0) return RTCDF_ERR_INVALID_ARG;
+int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P) {
     for (uint32_t s = 0; s < S; s++) {
-        if (seg_offsets[s + 1] < seg_offsets[s]) return RTCDF_ERR_INVALID_ARG;
-        if (seg_offsets[s + 1] - seg_offsets[s] >= (int64_t)1 << 32) return RTCDF_ERR_INVALID_ARG;
-        if (seg_minVal[s] < INT32_MIN || seg_maxVal[s] > ((int64_t)1 << 31)) return RTCDF_ERR_RANGE;
-        if (seg_maxVal[s] <= seg_minVal[s] || seg_maxVal[s] - seg_minVal[s] > (int64_t)kBatchMaxR)
-            return RTCDF_ERR_RANGE;
+        if (spec[s].n >= (1ull << 32)) return 1;
+        if (spec[s].minVal < INT32_MIN || spec[s].maxVal > ((int64_t)1 << 31)) return 2;
+        if (spec[s].maxVal <= spec[s].minVal || spec[s].maxVal - spec[s].minVal > (int64_t)kBatchMaxR)
+            return 2;
     }
-    int dev = 0, sms = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess) return RTCDF_ERR_CUDA;
-    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-        return RTCDF_ERR_CUDA;
-
-    rtcdf_batch_plan *p = new rtcdf_batch_plan();
-    p->device = dev;
-    p->workers = sms * kBatchWorkersPerSM;
-    p->num_segs = S;
-    std::vector<BatchSeg> segs(S);
+    P->segs.assign(S, BatchSeg{});
+    P->items.clear();
+    P->small_segs = P->large_segs = 0;
+    P->total_keys = 0;
     std::vector<BatchItem> hist, small, scan, fill;
-
     // Workspace (in 32-bit words): control block, per-segment control, then
     // per large segment its histogram (zero between runs) and run tables.
     size_t w = 0;
-    p->ctl_off = w;     w += words_align(sizeof(BatchCtl) / 4);
-    p->segctl_off = w;  w += words_align((size_t)S * sizeof(BatchSegCtl) / 4);
+    P->ctl_off = w;     w += words_align(sizeof(BatchCtl) / 4);
+    P->segctl_off = w;  w += words_align((size_t)S * sizeof(BatchSegCtl) / 4);
     for (uint32_t s = 0; s < S; s++) {
-        BatchSeg &g = segs[s];
+        BatchSeg &g = P->segs[s];
         memset(&g, 0, sizeof(g));
-        g.off = (uint64_t)seg_offsets[s];
-        g.n = (uint32_t)(seg_offsets[s + 1] - seg_offsets[s]);
-        g.R = (uint32_t)(seg_maxVal[s] - seg_minVal[s]);
-        g.minVal = (int32_t)seg_minVal[s];
-        p->total_keys += g.n;
+        g.off = spec[s].in_off;
+        g.out_off = spec[s].out_off;
+        g.n = (uint32_t)spec[s].n;
+        g.R = (uint32_t)(spec[s].maxVal - spec[s].minVal);
+        g.minVal = (int32_t)spec[s].minVal;
+        P->total_keys += g.n;
         if (g.n == 0) continue;
         if (g.n <= kBatchSmallMaxN && g.R <= kBatchSmallMaxR) {
             small.push_back(BatchItem{kItemSmall, s, 0, 0, 0, 0});
-            p->small_segs++;
+            P->small_segs++;
             continue;
         }
-        p->large_segs++;
+        P->large_segs++;
         g.m = (g.R + kBatchTileMax - 1) / kBatchTileMax;
         g.T = (g.R + g.m - 1) / g.m;
         const uint64_t chunks = (g.n + kHistChunk - 1) / kHistChunk;
@@ -105,9 +89,10 @@ rtcdf_status rtcdf_batch_plan_create(const int64_t *seg_offsets, const int64_t *
         g.run_val_off = w;   w += words_align(g.R);
         g.start_run_off = w; w += words_align(g.fill_items);
     }
-    p->ws_bytes = w * 4;
+    P->ws_words = w;
     // Queue order: HIST (largest segments first), SMALL (largest first), SCAN,
     // FILL -- every item a worker can wait on precedes it in the queue.
+    const std::vector<BatchSeg> &segs = P->segs;
     auto by_size = [&](const BatchItem &x, const BatchItem &y) {
         const uint64_t cx = (uint64_t)segs[x.seg].n + segs[x.seg].R;
         const uint64_t cy = (uint64_t)segs[y.seg].n + segs[y.seg].R;
@@ -117,28 +102,64 @@ rtcdf_status rtcdf_batch_plan_create(const int64_t *seg_offsets, const int64_t *
         return x.seg != y.seg ? by_size(x, y) : false;
     });
     std::stable_sort(small.begin(), small.end(), by_size);
-    std::vector<BatchItem> items;
-    items.reserve(hist.size() + small.size() + scan.size() + fill.size());
-    items.insert(items.end(), hist.begin(), hist.end());
-    items.insert(items.end(), small.begin(), small.end());
-    items.insert(items.end(), scan.begin(), scan.end());
-    items.insert(items.end(), fill.begin(), fill.end());
-    p->num_items = (uint32_t)items.size();
-    p->hist_items = (uint32_t)hist.size();
-    p->fill_items = (uint32_t)fill.size();
+    P->items.reserve(hist.size() + small.size() + scan.size() + fill.size());
+    P->items.insert(P->items.end(), hist.begin(), hist.end());
+    P->items.insert(P->items.end(), small.begin(), small.end());
+    P->items.insert(P->items.end(), scan.begin(), scan.end());
+    P->items.insert(P->items.end(), fill.begin(), fill.end());
+    return 0;
+}
 
+}  // namespace rtcdf
+
+extern "C" {
+
+rtcdf_status rtcdf_batch_plan_create(const int64_t *seg_offsets, const int64_t *seg_minVal,
+                                     const int64_t *seg_maxVal, int32_t num_segments,
+                                     rtcdf_batch_plan **plan_out) {
+    if (!plan_out || num_segments < 0) return RTCDF_ERR_INVALID_ARG;
+    *plan_out = nullptr;
+    if (num_segments > 0 && (!seg_offsets || !seg_minVal || !seg_maxVal)) return RTCDF_ERR_INVALID_ARG;
+    const uint32_t S = (uint32_t)num_segments;
+    if (S > 0 && seg_offsets[0] < 0) return RTCDF_ERR_INVALID_ARG;
+    std::vector<SegSpec> spec(S);
+    for (uint32_t s = 0; s < S; s++) {
+        if (seg_offsets[s + 1] < seg_offsets[s]) return RTCDF_ERR_INVALID_ARG;
+        spec[s] = SegSpec{(uint64_t)seg_offsets[s], (uint64_t)seg_offsets[s],
+                          (uint64_t)(seg_offsets[s + 1] - seg_offsets[s]), seg_minVal[s], seg_maxVal[s]};
+    }
+    HostPlan hp;
+    const int rc = build_host_plan(spec.data(), S, &hp);
+    if (rc) return (rtcdf_status)rc;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RTCDF_ERR_CUDA;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return RTCDF_ERR_CUDA;
+
+    rtcdf_batch_plan *p = new rtcdf_batch_plan();
+    p->device = dev;
+    p->workers = sms * kBatchWorkersPerSM;
+    p->num_segs = S;
+    p->num_items = (uint32_t)hp.items.size();
+    p->total_keys = hp.total_keys;
+    p->ws_bytes = hp.ws_words * 4;
+    p->ctl_off = hp.ctl_off;
+    p->segctl_off = hp.segctl_off;
+    p->small_segs = hp.small_segs;
+    p->large_segs = hp.large_segs;
     if (S > 0 && cudaMalloc(&p->d_segs, sizeof(BatchSeg) * S) != cudaSuccess) {
         delete p;
         return RTCDF_ERR_NO_MEMORY;
     }
-    if (!items.empty() && cudaMalloc(&p->d_items, sizeof(BatchItem) * items.size()) != cudaSuccess) {
+    if (!hp.items.empty() && cudaMalloc(&p->d_items, sizeof(BatchItem) * hp.items.size()) != cudaSuccess) {
         cudaFree(p->d_segs);
         delete p;
         return RTCDF_ERR_NO_MEMORY;
     }
-    if ((S > 0 && cudaMemcpy(p->d_segs, segs.data(), sizeof(BatchSeg) * S, cudaMemcpyHostToDevice) != cudaSuccess) ||
-        (!items.empty() && cudaMemcpy(p->d_items, items.data(), sizeof(BatchItem) * items.size(),
-                                      cudaMemcpyHostToDevice) != cudaSuccess)) {
+    if ((S > 0 && cudaMemcpy(p->d_segs, hp.segs.data(), sizeof(BatchSeg) * S,
+                             cudaMemcpyHostToDevice) != cudaSuccess) ||
+        (!hp.items.empty() && cudaMemcpy(p->d_items, hp.items.data(), sizeof(BatchItem) * hp.items.size(),
+                                         cudaMemcpyHostToDevice) != cudaSuccess)) {
         cudaFree(p->d_segs);
         cudaFree(p->d_items);
         delete p;

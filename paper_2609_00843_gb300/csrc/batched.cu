@@ -131,7 +131,7 @@ __device__ void do_small(const BatchArgs &a, const BatchSeg &g, uint32_t *sm) {
     // coalesced store per step); a lane's positions grow by 32, so after one
     // binary search its value index only moves forward (next value first,
     // binary search for longer jumps).
-    int32_t *out = a.out + g.off;
+    int32_t *out = a.out + g.out_off;
     const uint32_t lim = min(n, total);
     const uint32_t lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
     const uint32_t per_warp = ((lim + nwarps - 1) / nwarps + 31) & ~31u;
@@ -308,7 +308,7 @@ __device__ void do_fill(const BatchArgs &a, const BatchSeg &g, const BatchItem &
     uint32_t k_cur = a.ws_u32[g.start_run_off + it.aux];
     uint32_t *s_end = sm;
     int32_t *s_val = reinterpret_cast<int32_t *>(sm + nt);
-    int32_t *out = a.out + g.off;
+    int32_t *out = a.out + g.out_off;
     // Positions relative to the segment; vectors aligned to the global `out`.
     const uint32_t head = (uint32_t)(((16 - ((uintptr_t)out & 15)) & 15) / 4);
     int4 *vout = reinterpret_cast<int4 *>(out + head);

@@ -1,6 +1,8 @@
 // Internal declarations of the segmented (batched) RT-CDF launch.
 #pragma once
 
+#include <vector>
+
 #include "rtcdf_internal.h"
 
 namespace rtcdf {
@@ -18,7 +20,8 @@ enum : uint32_t { kItemHist = 0, kItemSmall = 1, kItemScan = 2, kItemFill = 3 };
 
 // One segment (all offsets in 32-bit words of the workspace).
 struct BatchSeg {
-    uint64_t off;          // first element of the segment in `in` / `out`
+    uint64_t off;          // first element of the segment in `in`
+    uint64_t out_off;      // first element of the segment in `out`
     uint32_t n, R;
     int32_t minVal;
     uint32_t T, m;         // tile width and tiles (large segments)
@@ -60,5 +63,22 @@ struct BatchArgs {
 };
 
 cudaError_t launch_batched(const BatchArgs &a, int workers, cudaStream_t s);
+
+// Host planner shared by the plan API and the server: segment s reads
+// n[s] keys at in_off[s] and writes them sorted at out_off[s].
+struct SegSpec {
+    uint64_t in_off, out_off, n;
+    int64_t minVal, maxVal;
+};
+struct HostPlan {
+    std::vector<BatchSeg> segs;
+    std::vector<BatchItem> items;
+    size_t ws_words = 0, ctl_off = 0, segctl_off = 0;
+    uint32_t small_segs = 0, large_segs = 0;
+    uint64_t total_keys = 0;
+};
+// Validates ranges (R in [1, kBatchMaxR], inside int32) and n < 2^32;
+// returns RTCDF-style codes (0 ok, 1 invalid argument, 2 range).
+int build_host_plan(const SegSpec *segs, uint32_t S, HostPlan *plan);
 
 }  // namespace rtcdf

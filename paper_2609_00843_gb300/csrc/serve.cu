@@ -1,0 +1,477 @@
+// Continuous-batching sort server (rtcdf_serve_* in include/rtcdf.h).
+//
+// A request is "sort these n keys from [minVal, maxVal)".  The server keeps
+// one device slab of `budget_bytes`; a request is admitted when its slot (input
+// + output, 8n bytes) fits, in arrival order.  Admitted requests whose input is
+// in place are launched as soon as one of `num_streams` streams is free:
+// requests with at least `single_min_keys` keys alone, through the single-array
+// pipeline (Algorithms 4-7, three kernels); all other pending requests together,
+// as one persistent segmented launch.  New arrivals keep being admitted while
+// earlier launches run, launches on different streams overlap on the device,
+// and a request's slot is released as soon as its launch completes.  Results
+// stay on the device; an optional order-dependent digest of each sorted output
+// lets a caller compare runs.
+#include <chrono>
+#include <cstring>
+#include <deque>
+#include <map>
+#include <thread>
+#include <vector>
+
+#include "../../include/rtcdf.h"
+#include "batched.h"
+
+using namespace rtcdf;
+
+namespace {
+
+using Clock = std::chrono::steady_clock;
+
+// First-fit allocator over [0, cap) in 256-byte units, with coalescing.
+class Slab {
+  public:
+    explicit Slab(size_t cap) { free_[0] = cap / 256 * 256; }
+    bool alloc(size_t bytes, size_t *off) {
+        bytes = (bytes + 255) / 256 * 256;
+        for (auto it = free_.begin(); it != free_.end(); ++it) {
+            if (it->second >= bytes) {
+                *off = it->first;
+                const size_t rest = it->second - bytes, at = it->first + bytes;
+                free_.erase(it);
+                if (rest) free_[at] = rest;
+                used_ += bytes;
+                if (used_ > peak_) peak_ = used_;
+                return true;
+            }
+        }
+        return false;
+    }
+    void release(size_t off, size_t bytes) {
+        bytes = (bytes + 255) / 256 * 256;
+        used_ -= bytes;
+        auto it = free_.emplace(off, bytes).first;
+        auto nx = std::next(it);
+        if (nx != free_.end() && it->first + it->second == nx->first) {
+            it->second += nx->second;
+            free_.erase(nx);
+        }
+        if (it != free_.begin()) {
+            auto pv = std::prev(it);
+            if (pv->first + pv->second == it->first) {
+                pv->second += it->second;
+                free_.erase(it);
+            }
+        }
+    }
+    size_t peak() const { return peak_; }
+    size_t used() const { return used_; }
+
+  private:
+    std::map<size_t, size_t> free_;
+    size_t used_ = 0, peak_ = 0;
+};
+
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// One digest per request: sum over positions i of mix64((i << 32) | out[i]),
+// mod 2^64 -- order-dependent, so two equal digests mean equal arrays with
+// overwhelming probability.  blockIdx.y selects the request.
+struct DigestSeg {
+    uint64_t out_off, n, slot;
+};
+
+__global__ void digest_kernel(const int32_t *base, const DigestSeg *segs, uint64_t *digests) {
+    const DigestSeg d = segs[blockIdx.y];
+    const int32_t *out = base + d.out_off;
+    uint64_t h = 0;
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < d.n;
+         i += (uint64_t)gridDim.x * blockDim.x)
+        h += mix64((i << 32) | (uint32_t)out[i]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) h += __shfl_xor_sync(0xffffffffu, h, o);
+    if ((threadIdx.x & 31) == 0 && h) atomicAdd((unsigned long long *)&digests[d.slot], (unsigned long long)h);
+}
+
+struct Launch {
+    cudaEvent_t done;
+    int stream;
+    std::vector<int64_t> reqs;
+    size_t ws_off = 0, ws_bytes = 0;  // batch workspace + tables in the slab
+    bool batched = false;
+};
+
+double secs(Clock::time_point t0) {
+    return std::chrono::duration<double>(Clock::now() - t0).count();
+}
+
+}  // namespace
+
+extern "C" {
+
+rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_request *reqs,
+                               int64_t count, rtcdf_result *results, rtcdf_serve_stats *stats) {
+    if (!cfg || (count > 0 && (!reqs || !results)) || count < 0) return RTCDF_ERR_INVALID_ARG;
+    if (!cfg->fill || cfg->num_streams < 1 || cfg->num_streams > 16 || cfg->max_batch < 1)
+        return RTCDF_ERR_INVALID_ARG;
+    int64_t maxR = 1;
+    for (int64_t i = 0; i < count; i++) {
+        const int64_t R = reqs[i].maxVal - reqs[i].minVal;
+        if (R <= 0 || R > (int64_t)kBatchMaxR || reqs[i].minVal < INT32_MIN ||
+            reqs[i].maxVal > ((int64_t)1 << 31) || reqs[i].n >= (1ull << 32))
+            return RTCDF_ERR_RANGE;
+        if (R > maxR) maxR = R;
+    }
+    const int K = cfg->num_streams;
+    const bool want_digest = cfg->digests != 0;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RTCDF_ERR_CUDA;
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+
+    // Device slab = admission budget.  Per stream, a single-array workspace
+    // for the widest range is carved out of it first.
+    char *slab = nullptr;
+    if (cudaMalloc(&slab, cfg->budget_bytes) != cudaSuccess) return RTCDF_ERR_NO_MEMORY;
+    Slab alloc(cfg->budget_bytes);
+    size_t ws_bytes = 0;
+    rtcdf_workspace_size(maxR, &ws_bytes);
+    std::vector<size_t> ws_off(K);
+    std::vector<cudaStream_t> streams(K);
+    for (int k = 0; k < K; k++) {
+        if (!alloc.alloc(ws_bytes, &ws_off[k])) { cudaFree(slab); return RTCDF_ERR_NO_MEMORY; }
+        cudaMemset(slab + ws_off[k], 0, ws_bytes);
+        cudaStreamCreateWithFlags(&streams[k], cudaStreamNonBlocking);
+    }
+    // Inputs are written on their own streams (round robin), so writing the
+    // next arrivals overlaps the sorts already running.
+    std::vector<cudaStream_t> fill_streams(K);
+    std::vector<cudaEvent_t> fill_evs(K);
+    for (int k = 0; k < K; k++) {
+        cudaStreamCreateWithFlags(&fill_streams[k], cudaStreamNonBlocking);
+        cudaEventCreateWithFlags(&fill_evs[k], cudaEventDisableTiming);
+    }
+    int fill_rr = 0;
+    uint64_t *d_digest = nullptr;
+    if (want_digest) {
+        cudaMalloc(&d_digest, sizeof(uint64_t) * (size_t)std::max<int64_t>(1, count));
+        cudaMemset(d_digest, 0, sizeof(uint64_t) * (size_t)std::max<int64_t>(1, count));
+    }
+    // Pinned staging for plan uploads, one per stream (reused once that
+    // stream's previous launch has completed).
+    const size_t stage_bytes = 64u << 20;
+    std::vector<char *> stage(K, nullptr);
+    for (int k = 0; k < K; k++) cudaMallocHost(&stage[k], stage_bytes);
+    cudaDeviceSynchronize();
+
+    std::vector<size_t> slot_off(count, 0), slot_bytes(count, 0);
+    for (int64_t i = 0; i < count; i++) {
+        memset(&results[i], 0, sizeof(rtcdf_result));
+        results[i].status = -1;
+    }
+    std::deque<int64_t> pending;            // admitted, input enqueued
+    std::vector<Launch> inflight;
+    std::vector<bool> stream_busy(K, false);
+    int64_t next = 0, done = 0;
+    uint64_t launches_batched = 0, launches_single = 0, batched_requests = 0;
+    int max_inflight = 0;
+    rtcdf_status err = RTCDF_OK;
+    const size_t reserve = std::min<size_t>(cfg->budget_bytes / 8, (size_t)1 << 30);
+    int batch_cap = cfg->max_batch;
+    const Clock::time_point t0 = Clock::now();
+
+    while (done < count && !err) {
+        bool progressed = false;
+        const double now = secs(t0);
+        // 1. Admit arrived requests, in order, while their slots fit.
+        bool admitted = false;
+        while (next < count && reqs[next].arrival_s <= now) {
+            const rtcdf_request &r = reqs[next];
+            size_t off = 0;
+            const size_t bytes = (size_t)r.n * 8 + 512;
+            if ((size_t)r.n * 8 + 512 + reserve > cfg->budget_bytes - (size_t)K * ws_bytes) {
+                results[next].status = RTCDF_ERR_NO_MEMORY;  // can never fit
+                results[next].admit_s = results[next].done_s = secs(t0);
+                next++, done++;
+                continue;
+            }
+            // Keep `reserve` bytes free for launch tables and batch workspaces.
+            if (alloc.used() + (bytes + 255) / 256 * 256 + reserve > cfg->budget_bytes ||
+                !alloc.alloc(bytes, &off))
+                break;  // wait for memory (in order)
+            slot_off[next] = off;
+            slot_bytes[next] = bytes;
+            int32_t *in = reinterpret_cast<int32_t *>(slab + off);
+            const int fs = fill_rr;
+            fill_rr = (fill_rr + 1) % K;
+            if (r.n && cfg->fill(in, r.n, 0, r.minVal, r.maxVal - r.minVal, r.dist, r.seed,
+                                 (rtcdf_stream_t)fill_streams[fs]) != 0) {
+                err = RTCDF_ERR_CUDA;
+                break;
+            }
+            results[next].admit_s = secs(t0);
+            pending.push_back(next);
+            next++;
+            admitted = progressed = true;
+        }
+        if (admitted)
+            for (int k = 0; k < K; k++) cudaEventRecord(fill_evs[k], fill_streams[k]);
+        // 2. Launch pending requests on free streams.
+        while (!pending.empty() && !err) {
+            int k = -1;
+            for (int j = 0; j < K; j++)
+                if (!stream_busy[j]) { k = j; break; }
+            if (k < 0) break;
+            cudaStream_t s = streams[k];
+            for (int f = 0; f < K; f++)  // inputs written before the sort reads them
+                cudaStreamWaitEvent(s, fill_evs[f], 0);
+            Launch L;
+            L.stream = k;
+            // A large request alone, or every small pending request together.
+            const int64_t head = pending.front();
+            if (reqs[head].n >= cfg->single_min_keys) {
+                pending.pop_front();
+                L.reqs.push_back(head);
+            } else {
+                for (auto it = pending.begin(); it != pending.end() && (int)L.reqs.size() < batch_cap;) {
+                    if (reqs[*it].n < cfg->single_min_keys) {
+                        L.reqs.push_back(*it);
+                        it = pending.erase(it);
+                    } else {
+                        ++it;
+                    }
+                }
+            }
+            const double launch_t = secs(t0);
+            const bool single = L.reqs.size() == 1 && reqs[L.reqs[0]].n >= cfg->single_min_keys;
+            // One slab region per launch, released when it completes:
+            // [segment table | work items | digest table | batch workspace].
+            HostPlan hp;
+            std::vector<SegSpec> spec;
+            if (!single) {
+                spec.resize(L.reqs.size());
+                for (size_t j = 0; j < L.reqs.size(); j++) {
+                    const int64_t i = L.reqs[j];
+                    const uint64_t in_off = slot_off[i] / 4;  // input at the slot start, output after it
+                    spec[j] = SegSpec{in_off, in_off + reqs[i].n, reqs[i].n, reqs[i].minVal, reqs[i].maxVal};
+                }
+                if (build_host_plan(spec.data(), (uint32_t)spec.size(), &hp)) { err = RTCDF_ERR_RANGE; break; }
+            }
+            std::vector<DigestSeg> dg;
+            if (want_digest) {
+                dg.resize(L.reqs.size());
+                for (size_t j = 0; j < L.reqs.size(); j++) {
+                    const int64_t i = L.reqs[j];
+                    dg[j] = DigestSeg{slot_off[i] / 4 + reqs[i].n, reqs[i].n, (uint64_t)i};
+                }
+            }
+            const size_t seg_b = hp.segs.size() * sizeof(BatchSeg);
+            const size_t item_b = hp.items.size() * sizeof(BatchItem);
+            const size_t dig_at = (seg_b + item_b + 15) / 16 * 16;
+            const size_t dig_b = dg.size() * sizeof(DigestSeg);
+            const size_t tab_b = (dig_at + dig_b + 255) / 256 * 256;
+            const size_t wsb = hp.ws_words * 4;
+            if (tab_b > stage_bytes) { err = RTCDF_ERR_NO_MEMORY; break; }
+            if (tab_b + wsb > 0 && !alloc.alloc(tab_b + wsb, &L.ws_off)) {
+                if (inflight.empty() && L.reqs.size() > 1) {
+                    // Nothing will free memory: retry with the first request alone.
+                    for (auto it = L.reqs.rbegin(); it != L.reqs.rend(); ++it) pending.push_front(*it);
+                    batch_cap = 1;
+                    continue;
+                }
+                if (inflight.empty()) { err = RTCDF_ERR_NO_MEMORY; break; }
+                for (auto it = L.reqs.rbegin(); it != L.reqs.rend(); ++it) pending.push_front(*it);
+                break;  // wait for a launch to complete
+            }
+            L.ws_bytes = tab_b + wsb;
+            char *tab = slab + L.ws_off;
+            if (seg_b + item_b + dig_b) {
+                memcpy(stage[k], hp.segs.data(), seg_b);
+                memcpy(stage[k] + seg_b, hp.items.data(), item_b);
+                memcpy(stage[k] + dig_at, dg.data(), dig_b);
+                cudaMemcpyAsync(tab, stage[k], dig_at + dig_b, cudaMemcpyHostToDevice, s);
+            }
+            if (single) {
+                const int64_t i = L.reqs[0];
+                int32_t *in = reinterpret_cast<int32_t *>(slab + slot_off[i]);
+                int32_t *out = in + reqs[i].n;
+                const rtcdf_status st = rtcdf_sort_ws(in, out, reqs[i].n, reqs[i].minVal, reqs[i].maxVal,
+                                                      slab + ws_off[k], ws_bytes, (rtcdf_stream_t)s);
+                if (st) { err = st; break; }
+                launches_single++;
+            } else {
+                uint32_t *ws = reinterpret_cast<uint32_t *>(tab + tab_b);
+                cudaMemsetAsync(ws, 0, wsb, s);
+                BatchArgs a;
+                a.in = reinterpret_cast<const int32_t *>(slab);
+                a.out = reinterpret_cast<int32_t *>(slab);
+                a.segs = reinterpret_cast<const BatchSeg *>(tab);
+                a.items = reinterpret_cast<const BatchItem *>(tab + seg_b);
+                a.num_items = (uint32_t)hp.items.size();
+                a.num_segs = (uint32_t)hp.segs.size();
+                a.ws_u32 = ws;
+                a.ctl = reinterpret_cast<BatchCtl *>(ws + hp.ctl_off);
+                a.seg_ctl = reinterpret_cast<BatchSegCtl *>(ws + hp.segctl_off);
+                if (a.num_items && launch_batched(a, sms * kBatchWorkersPerSM, s) != cudaSuccess) {
+                    err = RTCDF_ERR_CUDA;
+                    break;
+                }
+                L.batched = true;
+                launches_batched++;
+                batched_requests += L.reqs.size();
+            }
+            if (want_digest) {
+                uint32_t chunks = 1;
+                for (const DigestSeg &d : dg)
+                    chunks = std::max<uint32_t>(chunks, (uint32_t)std::min<uint64_t>(256, (d.n + 8191) / 8192));
+                for (size_t j0 = 0; j0 < dg.size(); j0 += 65535) {
+                    const uint32_t ny = (uint32_t)std::min<size_t>(65535, dg.size() - j0);
+                    digest_kernel<<<dim3(chunks, ny), 256, 0, s>>>(
+                        reinterpret_cast<const int32_t *>(slab),
+                        reinterpret_cast<const DigestSeg *>(tab + dig_at) + j0, d_digest);
+                }
+            }
+            batch_cap = cfg->max_batch;
+            cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
+            cudaEventRecord(L.done, s);
+            for (int64_t i : L.reqs) results[i].launch_s = launch_t, results[i].batch_id = (int32_t)(launches_batched + launches_single);
+            stream_busy[k] = true;
+            inflight.push_back(std::move(L));
+            if ((int)inflight.size() > max_inflight) max_inflight = (int)inflight.size();
+            progressed = true;
+        }
+        // 3. Retire completed launches, release their memory.
+        for (size_t j = 0; j < inflight.size();) {
+            if (cudaEventQuery(inflight[j].done) == cudaSuccess) {
+                const double t = secs(t0);
+                Launch &L = inflight[j];
+                for (int64_t i : L.reqs) {
+                    results[i].done_s = t;
+                    results[i].status = 0;
+                    alloc.release(slot_off[i], slot_bytes[i]);
+                    done++;
+                }
+                if (L.ws_bytes) alloc.release(L.ws_off, L.ws_bytes);
+                stream_busy[L.stream] = false;
+                cudaEventDestroy(L.done);
+                inflight.erase(inflight.begin() + j);
+                progressed = true;
+            } else {
+                j++;
+            }
+        }
+        if (!progressed) std::this_thread::yield();
+    }
+    cudaDeviceSynchronize();
+    const double makespan = secs(t0);
+    if (want_digest) {
+        std::vector<uint64_t> h((size_t)count);
+        cudaMemcpy(h.data(), d_digest, sizeof(uint64_t) * (size_t)count, cudaMemcpyDeviceToHost);
+        for (int64_t i = 0; i < count; i++) results[i].digest = h[i];
+    }
+    uint64_t keys = 0;
+    for (int64_t i = 0; i < count; i++) keys += reqs[i].n;
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->makespan_s = makespan;
+        stats->total_keys = keys;
+        stats->launches_batched = launches_batched;
+        stats->launches_single = launches_single;
+        stats->batched_requests = batched_requests;
+        stats->max_inflight = max_inflight;
+        stats->peak_bytes = alloc.peak();
+    }
+    for (int k = 0; k < K; k++) {
+        cudaStreamDestroy(streams[k]);
+        cudaFreeHost(stage[k]);
+    }
+    for (int k = 0; k < K; k++) {
+        cudaStreamDestroy(fill_streams[k]);
+        cudaEventDestroy(fill_evs[k]);
+    }
+    cudaFree(d_digest);
+    cudaFree(slab);
+    if (err) return err;
+    return cudaGetLastError() == cudaSuccess ? RTCDF_OK : RTCDF_ERR_CUDA;
+}
+
+rtcdf_status rtcdf_serve_sequential(const rtcdf_server_config *cfg, const rtcdf_request *reqs,
+                                    int64_t count, rtcdf_result *results, rtcdf_serve_stats *stats) {
+    if (!cfg || (count > 0 && (!reqs || !results)) || count < 0 || !cfg->fill)
+        return RTCDF_ERR_INVALID_ARG;
+    uint64_t max_n = 1;
+    int64_t maxR = 1;
+    for (int64_t i = 0; i < count; i++) {
+        const int64_t R = reqs[i].maxVal - reqs[i].minVal;
+        if (R <= 0 || R > RTCDF_MAX_R) return RTCDF_ERR_RANGE;
+        max_n = std::max<uint64_t>(max_n, reqs[i].n);
+        maxR = std::max(maxR, R);
+    }
+    size_t ws_bytes = 0;
+    rtcdf_workspace_size(maxR, &ws_bytes);
+    char *buf = nullptr;
+    if (cudaMalloc(&buf, max_n * 8 + ws_bytes + 512) != cudaSuccess) return RTCDF_ERR_NO_MEMORY;
+    char *ws = buf + (max_n * 8 + 255) / 256 * 256;
+    cudaMemset(ws, 0, ws_bytes);
+    uint64_t *d_digest = nullptr;
+    DigestSeg *d_seg = nullptr;
+    if (cfg->digests) {
+        cudaMalloc(&d_digest, sizeof(uint64_t) * (size_t)std::max<int64_t>(1, count));
+        cudaMemset(d_digest, 0, sizeof(uint64_t) * (size_t)std::max<int64_t>(1, count));
+        cudaMalloc(&d_seg, sizeof(DigestSeg));
+    }
+    cudaStream_t s;
+    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    cudaDeviceSynchronize();
+    rtcdf_status err = RTCDF_OK;
+    const Clock::time_point t0 = Clock::now();
+    for (int64_t i = 0; i < count && !err; i++) {
+        while (secs(t0) < reqs[i].arrival_s) std::this_thread::yield();
+        results[i] = rtcdf_result{};
+        results[i].admit_s = secs(t0);
+        int32_t *in = reinterpret_cast<int32_t *>(buf);
+        int32_t *out = in + reqs[i].n;
+        if (reqs[i].n) {
+            if (cfg->fill(in, reqs[i].n, 0, reqs[i].minVal, reqs[i].maxVal - reqs[i].minVal, reqs[i].dist,
+                          reqs[i].seed, (rtcdf_stream_t)s) != 0) { err = RTCDF_ERR_CUDA; break; }
+            results[i].launch_s = secs(t0);
+            err = rtcdf_sort_ws(in, out, reqs[i].n, reqs[i].minVal, reqs[i].maxVal, ws, ws_bytes,
+                                (rtcdf_stream_t)s);
+            if (cfg->digests && !err) {
+                DigestSeg d{(uint64_t)reqs[i].n, reqs[i].n, (uint64_t)i};
+                cudaMemcpyAsync(d_seg, &d, sizeof(d), cudaMemcpyHostToDevice, s);
+                const uint32_t chunks = (uint32_t)std::min<uint64_t>(256, (reqs[i].n + 8191) / 8192);
+                digest_kernel<<<dim3(chunks, 1), 256, 0, s>>>(reinterpret_cast<const int32_t *>(buf), d_seg, d_digest);
+            }
+        }
+        cudaStreamSynchronize(s);
+        results[i].done_s = secs(t0);
+        results[i].status = err ? (int32_t)err : 0;
+        results[i].batch_id = (int32_t)i;
+    }
+    const double makespan = secs(t0);
+    if (cfg->digests) {
+        std::vector<uint64_t> h((size_t)count);
+        cudaMemcpy(h.data(), d_digest, sizeof(uint64_t) * (size_t)count, cudaMemcpyDeviceToHost);
+        for (int64_t i = 0; i < count; i++) results[i].digest = h[i];
+    }
+    uint64_t keys = 0;
+    for (int64_t i = 0; i < count; i++) keys += reqs[i].n;
+    if (stats) {
+        memset(stats, 0, sizeof(*stats));
+        stats->makespan_s = makespan;
+        stats->total_keys = keys;
+        stats->launches_single = (uint64_t)count;
+        stats->max_inflight = 1;
+        stats->peak_bytes = max_n * 8 + ws_bytes;
+    }
+    cudaStreamDestroy(s);
+    cudaFree(d_seg);
+    cudaFree(d_digest);
+    cudaFree(buf);
+    return err;
+}
+
+}  // extern "C"

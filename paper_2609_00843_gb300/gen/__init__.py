@@ -18,9 +18,11 @@ Distributions (the three input shapes of the paper's evaluation, Section 4)
   output ``16 i`` (multiply-shift range reduction).
 * ``NORMAL``    mean minVal + R/2, standard deviation R/8, rounded half away
   from zero and clipped to [minVal, minVal + R - 1].  The normal variate is the
-  Irwin-Hall sum of twelve 32-bit uniforms (outputs ``16 i .. 16 i + 11``) minus
-  6, which has mean 0 and variance 1; every floating-point step is a single
-  IEEE-754 double operation so that host and device agree exactly.
+  Irwin-Hall sum of twelve 32-bit uniforms (both halves of outputs
+  ``16 i .. 16 i + 5``) minus 6, which has mean 0 and variance 1.  The offset
+  R/2 + (R/8) z is computed in IEEE-754 single precision, one correctly
+  rounded operation at a time (exact integers up to 2^24), so that host and
+  device agree exactly; minVal is added in integer arithmetic.
 * ``ALL_EQUAL`` key = minVal + floor(R / 3).
 """
 from __future__ import annotations
@@ -103,15 +105,17 @@ def keys_host(n: int, minVal: int, R: int, dist: int, seed: int, first: int = 0,
             out[s:e] = (x.astype(np.int64) + minVal).astype(np.int32)
         elif dist == NORMAL:
             S = np.zeros(e - s, dtype=np.uint64)
-            for j in range(12):
-                S += words(seed, base + np.uint64(j)) >> np.uint64(32)
-            z = S.astype(np.float64) * (2.0 ** -32) - 6.0
-            mu = float(minVal) + float(R) / 2.0
-            sigma = float(R) / 8.0
-            xr = mu + sigma * z
-            r = np.where(xr >= 0.0, np.floor(xr + 0.5), -np.floor(-xr + 0.5))
-            r = np.clip(r, float(minVal), float(minVal + R - 1))
-            out[s:e] = r.astype(np.int64).astype(np.int32)
+            for j in range(6):
+                wj = words(seed, base + np.uint64(j))
+                S += (wj >> np.uint64(32)) + (wj & np.uint64(0xFFFFFFFF))
+            f32 = np.float32
+            z = S.astype(f32) * f32(2.0 ** -32) - f32(6.0)
+            half = f32(R) / f32(2.0)
+            sigma = f32(R) / f32(8.0)
+            o = half + sigma * z
+            r = np.where(o >= f32(0), np.floor(o + f32(0.5)), -np.floor(-o + f32(0.5)))
+            r = np.clip(r.astype(np.int64), 0, R - 1)
+            out[s:e] = (r + minVal).astype(np.int32)
         else:
             raise ValueError(f"unknown distribution {dist}")
     return out
@@ -192,3 +196,37 @@ def batched_segments(seed: int, num_segments: int = 4096, n_lo: float = 1e3,
     dist = uniform_ints(seed, num_segments, 0, 2, slot=3)
     seeds = np.array([derive_seed(seed, 7, i) for i in range(num_segments)], dtype=np.uint64)
     return lengths, minv, R, dist, seeds
+
+
+def serving_requests(seed: int, count: int = 20000, n_lo: float = 1e4, n_hi: float = 1e8,
+                     r_lo: float = 2 ** 7, r_hi: float = 2 ** 18):
+    """Request shapes of the serving workload: n log-uniform in [n_lo, n_hi],
+    R log-uniform in [r_lo, r_hi], minVal uniform in [-2^20, 2^20], shape
+    uniform over the three.  Returns (n, minVal, R, dist, seeds)."""
+    n = log_uniform_ints(seed, count, n_lo, n_hi, slot=0)
+    R = log_uniform_ints(seed, count, r_lo, r_hi, slot=1)
+    minv = uniform_ints(seed, count, -(1 << 20), 1 << 20, slot=2)
+    dist = uniform_ints(seed, count, 0, 2, slot=3)
+    seeds = np.array([derive_seed(seed, 9, i) for i in range(count)], dtype=np.uint64)
+    return n, minv, R, dist, seeds
+
+
+def poisson_arrivals(seed: int, count: int, rate_per_s: float) -> np.ndarray:
+    """Arrival times (seconds) of a Poisson process: cumulative exponential gaps."""
+    u = _unit(seed, np.arange(count, dtype=np.uint64) * np.uint64(16) + np.uint64(5))
+    gaps = -np.log1p(-u) / rate_per_s
+    return np.cumsum(gaps)
+
+
+def fill_function_address() -> int:
+    """Address of rtcdf_gen_keys, usable as a server's fill callback."""
+    return ctypes.cast(load_device_lib().rtcdf_gen_keys, ctypes.c_void_p).value
+
+
+def digest(sorted_keys: np.ndarray) -> int:
+    """Order-dependent digest of an array, as the server computes it on the
+    device: sum over positions i of mix64((i << 32) | uint32(key_i)), mod 2^64."""
+    a = np.ascontiguousarray(sorted_keys).view(np.uint32).astype(np.uint64)
+    i = np.arange(a.size, dtype=np.uint64)
+    with np.errstate(over="ignore"):
+        return int(_mix64((i << np.uint64(32)) | a).sum(dtype=np.uint64))

@@ -2,7 +2,8 @@
 // definition).  Holds none of the sort's arithmetic; produces, for the same
 // (seed, index range, minVal, R, distribution), exactly the keys the numpy
 // version produces.  Every floating-point step of the normal shape is a single
-// correctly rounded IEEE-754 double operation (no contraction into FMA).
+// correctly rounded IEEE-754 single-precision operation (no contraction into
+// FMA), matching numpy's float32 arithmetic.
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -23,9 +24,8 @@ __device__ __forceinline__ uint64_t word(uint64_t seed, uint64_t ctr) {
 __global__ void gen_kernel(int32_t *out, uint64_t n, uint64_t first, int64_t minVal, int64_t R,
                            int dist, uint64_t seed) {
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    const double mu = __dadd_rn((double)minVal, (double)R / 2.0);
-    const double sigma = (double)R / 8.0;
-    const double lo = (double)minVal, hi = (double)(minVal + R - 1);
+    const float Rf = __ull2float_rn((unsigned long long)R);
+    const float half = __fdiv_rn(Rf, 2.0f), sigma = __fdiv_rn(Rf, 8.0f);
     for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += stride) {
         const uint64_t idx = first + i;
         int64_t key;
@@ -35,12 +35,16 @@ __global__ void gen_kernel(int32_t *out, uint64_t n, uint64_t first, int64_t min
         } else if (dist == RTCDF_GEN_NORMAL) {
             uint64_t S = 0;
 #pragma unroll
-            for (int j = 0; j < 12; j++) S += word(seed, idx * 16 + j) >> 32;
-            double z = __dadd_rn(__dmul_rn((double)S, 0x1p-32), -6.0);
-            double xr = __dadd_rn(mu, __dmul_rn(sigma, z));
-            double r = (xr >= 0.0) ? floor(__dadd_rn(xr, 0.5)) : -floor(__dadd_rn(-xr, 0.5));
-            r = fmin(fmax(r, lo), hi);
-            key = (int64_t)r;
+            for (int j = 0; j < 6; j++) {
+                const uint64_t w = word(seed, idx * 16 + j);
+                S += (w >> 32) + (w & 0xFFFFFFFFull);
+            }
+            const float z = __fadd_rn(__fmul_rn(__ull2float_rn(S), 0x1p-32f), -6.0f);
+            const float o = __fadd_rn(half, __fmul_rn(sigma, z));
+            const float r = (o >= 0.0f) ? floorf(__fadd_rn(o, 0.5f)) : -floorf(__fadd_rn(-o, 0.5f));
+            int64_t ri = (int64_t)r;
+            ri = ri < 0 ? 0 : (ri > R - 1 ? R - 1 : ri);
+            key = minVal + ri;
         } else {
             key = minVal + R / 3;
         }

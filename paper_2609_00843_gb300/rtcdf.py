@@ -57,6 +57,31 @@ class BatchInfo(ctypes.Structure):
                 ("total_keys", ctypes.c_uint64), ("workspace_bytes", ctypes.c_uint64)]
 
 
+class ServerConfig(ctypes.Structure):
+    _fields_ = [("budget_bytes", ctypes.c_uint64), ("num_streams", ctypes.c_int32),
+                ("max_batch", ctypes.c_int32), ("single_min_keys", ctypes.c_uint64),
+                ("fill", ctypes.c_void_p), ("digests", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_uint64), ("minVal", ctypes.c_int64), ("maxVal", ctypes.c_int64),
+                ("dist", ctypes.c_int32), ("reserved", ctypes.c_int32), ("seed", ctypes.c_uint64),
+                ("arrival_s", ctypes.c_double)]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("admit_s", ctypes.c_double), ("launch_s", ctypes.c_double),
+                ("done_s", ctypes.c_double), ("digest", ctypes.c_uint64),
+                ("status", ctypes.c_int32), ("batch_id", ctypes.c_int32)]
+
+
+class ServeStats(ctypes.Structure):
+    _fields_ = [("makespan_s", ctypes.c_double), ("total_keys", ctypes.c_uint64),
+                ("launches_batched", ctypes.c_uint64), ("launches_single", ctypes.c_uint64),
+                ("batched_requests", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64),
+                ("max_inflight", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 def declared_functions() -> list[str]:
     """Names of the functions declared in include/rtcdf.h."""
     text = open(HEADER).read()
@@ -94,6 +119,10 @@ def lib():
             L.rtcdf_sort_batched_ws.argtypes = [vp, vp, vp, vp, sz, vp]
             L.rtcdf_batch_status_get.argtypes = [vp, vp, ctypes.POINTER(i32)]
             L.rtcdf_sort_batched.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+            for f in ("rtcdf_serve_trace", "rtcdf_serve_sequential"):
+                getattr(L, f).argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(Request),
+                                          i64, ctypes.POINTER(Result), ctypes.POINTER(ServeStats)]
+                getattr(L, f).restype = ctypes.c_int
             for f in ("rtcdf_sort", "rtcdf_sort_ws", "rtcdf_sort_ex", "rtcdf_reserve",
                       "rtcdf_workspace_size", "rtcdf_status_get", "rtcdf_ws_status_get",
                       "rtcdf_plan", "rtcdf_sort_static", "rtcdf_batch_plan_create",
@@ -191,6 +220,35 @@ def rtcdf_sort_batched(in_ptr: int, out_ptr: int, seg_offsets, seg_minVal, seg_m
     mn, mnp = _i64_array(seg_minVal)
     mx, mxp = _i64_array(seg_maxVal)
     return lib().rtcdf_sort_batched(in_ptr, out_ptr, op, mnp, mxp, len(mn), stream)
+
+
+def make_requests(n, minVal, maxVal, dist, seed, arrival_s):
+    """A ctypes array of rtcdf_request from equal-length sequences."""
+    count = len(n)
+    arr = (Request * max(1, count))()
+    for i in range(count):
+        arr[i] = Request(int(n[i]), int(minVal[i]), int(maxVal[i]), int(dist[i]), 0,
+                         int(seed[i]) & ((1 << 64) - 1), float(arrival_s[i]))
+    return arr
+
+
+def _serve(fname, cfg: ServerConfig, reqs, count: int):
+    results = (Result * max(1, count))()
+    stats = ServeStats()
+    rc = getattr(lib(), fname)(ctypes.byref(cfg), reqs, count, results, ctypes.byref(stats))
+    if rc != OK:
+        raise RtcdfError(rc, fname)
+    return results, stats
+
+
+def rtcdf_serve_trace(cfg: ServerConfig, reqs, count: int):
+    """Continuous-batching server over a request trace; returns (results, stats)."""
+    return _serve("rtcdf_serve_trace", cfg, reqs, count)
+
+
+def rtcdf_serve_sequential(cfg: ServerConfig, reqs, count: int):
+    """The same trace served one request at a time; returns (results, stats)."""
+    return _serve("rtcdf_serve_sequential", cfg, reqs, count)
 
 
 def rtcdf_reserve(max_R: int, stream: int = 0) -> int:

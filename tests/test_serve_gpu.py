@@ -1,0 +1,86 @@
+"""Continuous-batching server: every request's result is the same alone (served
+one at a time) and in the mix (admitted while others run, batched with them),
+and matches the CPU oracle -- bit-exact, compared through order-dependent
+digests of the sorted outputs."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2609_00843_gb300 import _build, gen, rtcdf
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    _build.build()
+    torch.cuda.init()
+
+
+def trace(count, seed, n_hi=3e6, rate=20000.0, r_hi=2 ** 18):
+    n, mn, R, dist, seeds = gen.serving_requests(seed, count, n_lo=1e3, n_hi=n_hi, r_hi=r_hi)
+    arr = gen.poisson_arrivals(seed, count, rate)
+    return n, mn, R, dist, seeds, arr
+
+
+def config(budget, digests=True, streams=4, max_batch=64, single_min=1 << 21):
+    return rtcdf.ServerConfig(budget_bytes=budget, num_streams=streams, max_batch=max_batch,
+                              single_min_keys=single_min, fill=gen.fill_function_address(),
+                              digests=1 if digests else 0)
+
+
+def oracle_digest(n, mn, R, dist, seed):
+    a = gen.keys_host(int(n), int(mn), int(R), int(dist), int(seed))
+    return gen.digest(oracle.counting_sort(a, int(mn), int(mn) + int(R)))
+
+
+def test_digest_definition_matches_device():
+    """The device digest of a sorted output equals the numpy digest."""
+    n, mn, R, dist, seeds, arr = trace(8, gen.derive_seed(50), n_hi=2e5)
+    reqs = rtcdf.make_requests(n, mn, mn + R, dist, seeds, np.zeros(8))
+    res, _ = rtcdf.rtcdf_serve_sequential(config(1 << 30), reqs, 8)
+    for i in range(8):
+        assert res[i].status == 0
+        assert res[i].digest == oracle_digest(n[i], mn[i], R[i], dist[i], seeds[i])
+
+
+def test_results_alone_equal_results_in_the_mix():
+    count = 400
+    n, mn, R, dist, seeds, arr = trace(count, gen.derive_seed(51))
+    reqs = rtcdf.make_requests(n, mn, mn + R, dist, seeds, arr)
+    mix, st = rtcdf.rtcdf_serve_trace(config(4 << 30), reqs, count)
+    alone, _ = rtcdf.rtcdf_serve_sequential(config(4 << 30), reqs, count)
+    assert st.launches_batched > 0 and st.batched_requests > 0
+    assert st.max_inflight > 1, "launches should overlap"
+    for i in range(count):
+        assert mix[i].status == 0 and alone[i].status == 0
+        assert mix[i].digest == alone[i].digest, f"request {i} differs alone vs in the mix"
+        assert mix[i].done_s >= mix[i].launch_s >= mix[i].admit_s >= arr[i] - 1e-6
+    # and against the oracle on a sample
+    for i in range(0, count, 23):
+        assert mix[i].digest == oracle_digest(n[i], mn[i], R[i], dist[i], seeds[i]), i
+
+
+def test_small_budget_admission_waits_for_memory():
+    count = 120
+    n, mn, R, dist, seeds, arr = trace(count, gen.derive_seed(52), n_hi=4e6, rate=1e6)
+    reqs = rtcdf.make_requests(n, mn, mn + R, dist, seeds, arr)
+    budget = 256 << 20  # a handful of large requests at a time
+    res, st = rtcdf.rtcdf_serve_trace(config(budget), reqs, count)
+    alone, _ = rtcdf.rtcdf_serve_sequential(config(budget), reqs, count)
+    assert st.peak_bytes <= budget
+    for i in range(count):
+        assert res[i].status == 0 and res[i].digest == alone[i].digest
+
+
+def test_request_larger_than_budget_is_refused_others_served():
+    n = np.array([1000, 50_000_000, 2000])
+    mn = np.array([0, 0, -5])
+    R = np.array([100, 100, 7])
+    reqs = rtcdf.make_requests(n, mn, mn + R, [0, 0, 1], [1, 2, 3], [0.0, 0.0, 0.0])
+    res, _ = rtcdf.rtcdf_serve_trace(config(64 << 20), reqs, 3)
+    assert res[1].status == rtcdf.ERR_NO_MEMORY
+    for i in (0, 2):
+        assert res[i].status == 0
+        assert res[i].digest == oracle_digest(n[i], mn[i], R[i], [0, 0, 1][i], [1, 2, 3][i])
