@@ -1,0 +1,134 @@
+// rtcdf_sort_host: the sort with HOST input and output buffers.
+//
+// Keys cross to the device in chunks on a copy stream; the histogram of each
+// chunk (Algorithm 5) runs on the caller's stream as soon as the chunk has
+// landed, so the transfer and the histogram overlap.  The local-CDF scan and
+// the output generation (Algorithms 6-7) follow, and the sorted keys go back
+// on a second copy stream -- which overlaps the next call's upload, since the
+// two directions of the host link are independent.  Device buffers are owned
+// by the library: two sets per (device, stream), used alternately and guarded
+// by events, so consecutive calls on one stream pipeline without races.
+#include <algorithm>
+#include <map>
+#include <mutex>
+
+#include "../../include/rtcdf.h"
+#include "rtcdf_internal.h"
+
+namespace rtcdf {
+// rtcdf_api.cu
+rtcdf_status host_pipeline_hist(const int32_t *in, uint64_t n, int64_t minVal, uint32_t R, void *ws,
+                                size_t ws_bytes, cudaStream_t s);
+rtcdf_status host_pipeline_finish(int32_t *out, uint64_t n, int64_t minVal, uint32_t R, void *ws,
+                                  size_t ws_bytes, cudaStream_t s);
+}  // namespace rtcdf
+
+using namespace rtcdf;
+
+namespace {
+
+struct BufSet {
+    int32_t *in = nullptr, *out = nullptr;
+    uint64_t cap = 0;
+    cudaEvent_t in_free = nullptr;   // the histogram that last read `in` is done
+    cudaEvent_t out_free = nullptr;  // the download that last read `out` is done
+};
+
+struct HostCtx {
+    BufSet set[2];
+    int next = 0;
+    void *ws = nullptr;
+    size_t ws_bytes = 0;
+    cudaStream_t up = nullptr, down = nullptr;
+    cudaEvent_t ev_done = nullptr;   // sort finished on the compute stream
+};
+
+std::mutex g_host_mu;
+std::map<std::pair<int, cudaStream_t>, HostCtx> g_host;
+
+constexpr uint64_t kChunk = 1ull << 22;  // keys per uploaded chunk (16 MB)
+
+}  // namespace
+
+extern "C" rtcdf_status rtcdf_sort_host(const int32_t *h_in, int32_t *h_out, uint64_t n, int64_t minVal,
+                                        int64_t maxVal, rtcdf_stream_t stream) {
+    if (minVal < INT32_MIN || maxVal > ((int64_t)1 << 31) || maxVal <= minVal ||
+        maxVal - minVal > RTCDF_MAX_R)
+        return RTCDF_ERR_RANGE;
+    if (n == 0) return RTCDF_OK;
+    if (!h_in || !h_out || n >= (1ull << 32)) return RTCDF_ERR_INVALID_ARG;
+    if (((uintptr_t)h_in & 3) || ((uintptr_t)h_out & 3)) return RTCDF_ERR_INVALID_ARG;
+    const uint32_t R = (uint32_t)(maxVal - minVal);
+    cudaStream_t s = (cudaStream_t)stream;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RTCDF_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    HostCtx &c = g_host[std::make_pair(dev, s)];
+    if (!c.up) {
+        if (cudaStreamCreateWithFlags(&c.up, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&c.down, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c.ev_done, cudaEventDisableTiming) != cudaSuccess)
+            return RTCDF_ERR_CUDA;
+        for (BufSet &b : c.set) {
+            if (cudaEventCreateWithFlags(&b.in_free, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&b.out_free, cudaEventDisableTiming) != cudaSuccess)
+                return RTCDF_ERR_CUDA;
+            cudaEventRecord(b.in_free, s);
+            cudaEventRecord(b.out_free, s);
+        }
+    }
+    // Workspace (shared by both sets: the sorts themselves are ordered on `s`).
+    const size_t need_ws = ws_required(R);
+    if (c.ws_bytes < need_ws) {
+        void *p = nullptr;
+        if (cudaMallocAsync(&p, need_ws, s) != cudaSuccess) return RTCDF_ERR_NO_MEMORY;
+        if (cudaMemsetAsync(p, 0, need_ws, s) != cudaSuccess) return RTCDF_ERR_CUDA;
+        if (c.ws) cudaFreeAsync(c.ws, s);
+        c.ws = p;
+        c.ws_bytes = need_ws;
+    }
+    BufSet &b = c.set[c.next];
+    c.next ^= 1;
+    if (b.cap < n) {
+        // Growing: wait until nothing uses the old buffers, then replace them.
+        cudaStreamWaitEvent(s, b.in_free, 0);
+        cudaStreamWaitEvent(s, b.out_free, 0);
+        if (b.in) cudaFreeAsync(b.in, s);
+        if (b.out) cudaFreeAsync(b.out, s);
+        b.in = b.out = nullptr;
+        b.cap = 0;
+        if (cudaMallocAsync((void **)&b.in, n * 4, s) != cudaSuccess ||
+            cudaMallocAsync((void **)&b.out, n * 4, s) != cudaSuccess)
+            return RTCDF_ERR_NO_MEMORY;
+        b.cap = n;
+        cudaEventRecord(b.in_free, s);
+        cudaEventRecord(b.out_free, s);
+    }
+    // Upload in chunks; the histogram of chunk k waits only for chunk k.
+    cudaStreamWaitEvent(c.up, b.in_free, 0);
+    cudaEvent_t ev;
+    for (uint64_t k0 = 0; k0 < n; k0 += kChunk) {
+        const uint64_t k1 = std::min(n, k0 + kChunk);
+        if (cudaMemcpyAsync(b.in + k0, h_in + k0, (k1 - k0) * 4, cudaMemcpyHostToDevice, c.up) != cudaSuccess)
+            return RTCDF_ERR_CUDA;
+        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return RTCDF_ERR_CUDA;
+        cudaEventRecord(ev, c.up);
+        cudaStreamWaitEvent(s, ev, 0);
+        cudaEventDestroy(ev);  // released once recorded work completes
+        rtcdf_status st = host_pipeline_hist(b.in + k0, k1 - k0, minVal, R, c.ws, c.ws_bytes, s);
+        if (st) return st;
+    }
+    cudaEventRecord(b.in_free, s);
+    // Scan and output, once the previous download from this set is done.
+    cudaStreamWaitEvent(s, b.out_free, 0);
+    rtcdf_status st = host_pipeline_finish(b.out, n, minVal, R, c.ws, c.ws_bytes, s);
+    if (st) return st;
+    cudaEventRecord(c.ev_done, s);
+    cudaStreamWaitEvent(c.down, c.ev_done, 0);
+    if (cudaMemcpyAsync(h_out, b.out, n * 4, cudaMemcpyDeviceToHost, c.down) != cudaSuccess)
+        return RTCDF_ERR_CUDA;
+    cudaEventRecord(b.out_free, c.down);
+    // The caller's stream completes only when the download has.
+    cudaStreamWaitEvent(s, b.out_free, 0);
+    return RTCDF_OK;
+}

@@ -157,50 +157,64 @@ rtcdf_status check_args(const int32_t *in, int32_t *out, uint64_t n) {
     return RTCDF_OK;
 }
 
-rtcdf_status run_pipeline(const int32_t *in, int32_t *out, uint64_t n, int64_t minVal,
-                          uint32_t R, const Plan &pl, void *ws, size_t ws_bytes,
-                          const rtcdf_debug *dbg, cudaStream_t s) {
-    const WsLayout L = ws_layout(R, ws_bytes);
-    char *base = (char *)ws;
-    Ctl *ctl = (Ctl *)(base + L.ctl);
-    uint64_t *state = (uint64_t *)(base + L.scan_state);
-    uint32_t *H = (uint32_t *)(base + L.hist);
-    uint32_t *run_end = (uint32_t *)(base + L.run_end);
-    int32_t *run_val = (int32_t *)(base + L.run_val);
-    uint32_t *start_run = (uint32_t *)(base + L.start_run);
-
-    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
-    if (dbg)
-        for (int i = 0; i < 4; i++) ev[i] = (cudaEvent_t)dbg->stage_events[i];
-    if (ev[0] && cudaEventRecord(ev[0], s) != cudaSuccess) return RTCDF_ERR_CUDA;
-
+// Algorithm 5 (all tiles) into the workspace's H.  H accumulates, so several
+// calls over slices of one array add up to the array's histogram.
+rtcdf_status hist_phase(const int32_t *in, uint64_t n, int64_t minVal, uint32_t R, const Plan &pl,
+                        const WsLayout &L, char *base, cudaStream_t s) {
     HistArgs h;
     h.in = in; h.n = n; h.nvec = pl.nvec; h.head = pl.head;
     h.min_u = (uint32_t)(int32_t)minVal; h.R = R; h.T = pl.T; h.m = pl.m; h.g = pl.g;
-    h.H = H; h.ctl = ctl;
+    h.H = (uint32_t *)(base + L.hist);
+    h.ctl = (Ctl *)(base + L.ctl);
     if (launch_hist(h, pl.hist_threads, pl.hist_smem, pl.streaming, s) != cudaSuccess)
         return RTCDF_ERR_CUDA;
-    if (ev[1] && cudaEventRecord(ev[1], s) != cudaSuccess) return RTCDF_ERR_CUDA;
+    return RTCDF_OK;
+}
 
+// Local CDFs + offsets (Algorithm 6) and output generation (Algorithm 7)
+// for an n-key array whose histogram is in H.
+rtcdf_status finish_phase(int32_t *out, uint64_t n, int64_t minVal, uint32_t R, const Plan &pl,
+                          const WsLayout &L, char *base, const rtcdf_debug *dbg,
+                          cudaEvent_t ev_scan, cudaEvent_t ev_fill, cudaStream_t s) {
+    Ctl *ctl = (Ctl *)(base + L.ctl);
+    uint64_t *state = (uint64_t *)(base + L.scan_state);
+    uint32_t *run_end = (uint32_t *)(base + L.run_end);
+    int32_t *run_val = (int32_t *)(base + L.run_val);
+    uint32_t *start_run = (uint32_t *)(base + L.start_run);
     const uint32_t head_out = (uint32_t)(((16 - ((uintptr_t)out & 15)) & 15) / 4);
     ScanArgs sc;
-    sc.H = H; sc.state = state; sc.ctl = ctl; sc.run_end = run_end; sc.run_val = run_val;
-    sc.start_run = start_run; sc.n = n; sc.fill_chunk = pl.fill_chunk; sc.head = head_out;
-    sc.fill_ctas = pl.fill_ctas; sc.R = R; sc.T = pl.T; sc.chunks = L.scan_chunks;
+    sc.H = (uint32_t *)(base + L.hist); sc.state = state; sc.ctl = ctl; sc.run_end = run_end;
+    sc.run_val = run_val; sc.start_run = start_run; sc.n = n; sc.fill_chunk = pl.fill_chunk;
+    sc.head = head_out; sc.fill_ctas = pl.fill_ctas; sc.R = R; sc.T = pl.T; sc.chunks = L.scan_chunks;
     sc.minVal = (int32_t)minVal;
     sc.dbg_hist = dbg ? dbg->tile_hist : nullptr;
     sc.dbg_cdf = dbg ? dbg->cdf : nullptr;
     sc.dbg_offset = dbg ? dbg->tile_offset : nullptr;
     if (launch_scan(sc, s) != cudaSuccess) return RTCDF_ERR_CUDA;
-    if (ev[2] && cudaEventRecord(ev[2], s) != cudaSuccess) return RTCDF_ERR_CUDA;
+    if (ev_scan && cudaEventRecord(ev_scan, s) != cudaSuccess) return RTCDF_ERR_CUDA;
 
     FillArgs f;
     f.out = out; f.n = n; f.fill_chunk = pl.fill_chunk; f.head = head_out;
     f.fill_ctas = pl.fill_ctas; f.run_end = run_end; f.run_val = run_val;
     f.start_run = start_run; f.ctl = ctl; f.scan_state = state; f.scan_chunks = L.scan_chunks;
     if (launch_fill(f, pl.fill_threads, s) != cudaSuccess) return RTCDF_ERR_CUDA;
-    if (ev[3] && cudaEventRecord(ev[3], s) != cudaSuccess) return RTCDF_ERR_CUDA;
+    if (ev_fill && cudaEventRecord(ev_fill, s) != cudaSuccess) return RTCDF_ERR_CUDA;
     return RTCDF_OK;
+}
+
+rtcdf_status run_pipeline(const int32_t *in, int32_t *out, uint64_t n, int64_t minVal,
+                          uint32_t R, const Plan &pl, void *ws, size_t ws_bytes,
+                          const rtcdf_debug *dbg, cudaStream_t s) {
+    const WsLayout L = ws_layout(R, ws_bytes);
+    char *base = (char *)ws;
+    cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+    if (dbg)
+        for (int i = 0; i < 4; i++) ev[i] = (cudaEvent_t)dbg->stage_events[i];
+    if (ev[0] && cudaEventRecord(ev[0], s) != cudaSuccess) return RTCDF_ERR_CUDA;
+    rtcdf_status st = hist_phase(in, n, minVal, R, pl, L, base, s);
+    if (st) return st;
+    if (ev[1] && cudaEventRecord(ev[1], s) != cudaSuccess) return RTCDF_ERR_CUDA;
+    return finish_phase(out, n, minVal, R, pl, L, base, dbg, ev[2], ev[3], s);
 }
 
 // ---------------------------------------------------------------- workspace cache
@@ -266,6 +280,26 @@ rtcdf_status sort_with_workspace(const int32_t *in, int32_t *out, uint64_t n, in
     st = make_plan(n, R, (uintptr_t)in, (uintptr_t)out, nullptr, &pl);
     if (st) return st;
     return run_pipeline(in, out, n, minVal, R, pl, ws, ws_bytes, nullptr, s);
+}
+
+// The two halves of a sort, for rtcdf_sort_host: histogram of a slice (may be
+// called once per uploaded chunk), then scan + output for the whole array.
+rtcdf_status host_pipeline_hist(const int32_t *in, uint64_t n, int64_t minVal, uint32_t R, void *ws,
+                                size_t ws_bytes, cudaStream_t s) {
+    if (n == 0) return RTCDF_OK;
+    Plan pl;
+    rtcdf_status st = make_plan(n, R, (uintptr_t)in, 0, nullptr, &pl);
+    if (st) return st;
+    return hist_phase(in, n, minVal, R, pl, ws_layout(R, ws_bytes), (char *)ws, s);
+}
+
+rtcdf_status host_pipeline_finish(int32_t *out, uint64_t n, int64_t minVal, uint32_t R, void *ws,
+                                  size_t ws_bytes, cudaStream_t s) {
+    Plan pl;
+    rtcdf_status st = make_plan(n, R, 0, (uintptr_t)out, nullptr, &pl);
+    if (st) return st;
+    return finish_phase(out, n, minVal, R, pl, ws_layout(R, ws_bytes), (char *)ws, nullptr,
+                        nullptr, nullptr, s);
 }
 
 }  // namespace rtcdf

@@ -112,6 +112,7 @@ def lib():
             L.rtcdf_ws_status_get.argtypes = [vp, vp, ctypes.POINTER(i32)]
             L.rtcdf_plan.argtypes = [u64, i64, ctypes.POINTER(Params)]
             L.rtcdf_sort_static.argtypes = [vp, vp, u64, i64, i64, vp]
+            L.rtcdf_sort_host.argtypes = [vp, vp, u64, i64, i64, vp]
             L.rtcdf_batch_plan_create.argtypes = [vp, vp, vp, i32, ctypes.POINTER(vp)]
             L.rtcdf_batch_plan_destroy.argtypes = [vp]
             L.rtcdf_batch_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
@@ -125,7 +126,7 @@ def lib():
                 getattr(L, f).restype = ctypes.c_int
             for f in ("rtcdf_sort", "rtcdf_sort_ws", "rtcdf_sort_ex", "rtcdf_reserve",
                       "rtcdf_workspace_size", "rtcdf_status_get", "rtcdf_ws_status_get",
-                      "rtcdf_plan", "rtcdf_sort_static", "rtcdf_batch_plan_create",
+                      "rtcdf_plan", "rtcdf_sort_static", "rtcdf_sort_host", "rtcdf_batch_plan_create",
                       "rtcdf_batch_plan_destroy", "rtcdf_batch_workspace_size",
                       "rtcdf_batch_plan_info", "rtcdf_sort_batched_ws", "rtcdf_batch_status_get",
                       "rtcdf_sort_batched"):
@@ -249,6 +250,12 @@ def rtcdf_serve_trace(cfg: ServerConfig, reqs, count: int):
 def rtcdf_serve_sequential(cfg: ServerConfig, reqs, count: int):
     """The same trace served one request at a time; returns (results, stats)."""
     return _serve("rtcdf_serve_sequential", cfg, reqs, count)
+
+
+def rtcdf_sort_host(in_ptr: int, out_ptr: int, n: int, minVal: int, maxVal: int,
+                    stream: int = 0) -> int:
+    """Sort host buffers (pinned for overlap); returns when enqueued."""
+    return lib().rtcdf_sort_host(in_ptr, out_ptr, n, minVal, maxVal, stream)
 
 
 def rtcdf_reserve(max_R: int, stream: int = 0) -> int:

@@ -222,6 +222,32 @@ def test_cuda_graph_capture_and_replay():
         assert_matches_oracle(x, out, -1000, -1000 + R)
 
 
+@pytest.mark.parametrize("pinned", [True, False])
+def test_host_buffer_entry_point(pinned):
+    """rtcdf_sort_host: host input and output, chunked upload, alternating
+    device buffer sets across consecutive calls, growing sizes."""
+    s = torch.cuda.Stream()
+    cases = [(5, 128, 0), (1_000_003, 4097, 1), (50_000_000, 1 << 14, 1), (3_000_000, 1 << 18, 0),
+             (17, 3, 2), (20_000_000, 1000, 2)]
+    hosts = []
+    for i, (n, R, dist) in enumerate(cases):
+        x = dev_keys(n, -77, R, dist, gen.derive_seed(60, i)).cpu()
+        if pinned:
+            x = x.pin_memory()
+        off = i % 3  # misaligned host views too
+        xin = torch.empty(n + off, dtype=torch.int32, pin_memory=pinned)[off:]
+        xin.copy_(x)
+        xout = torch.full((n + off,), -1, dtype=torch.int32, pin_memory=pinned)[off:]
+        hosts.append((xin, xout, n, R))
+    torch.cuda.synchronize()
+    for xin, xout, n, R in hosts:  # back to back: downloads overlap the next uploads
+        assert rtcdf.rtcdf_sort_host(xin.data_ptr(), xout.data_ptr(), n, -77, -77 + R,
+                                     s.cuda_stream) == rtcdf.OK
+    s.synchronize()
+    for xin, xout, n, R in hosts:
+        np.testing.assert_array_equal(xout.numpy(), oracle.counting_sort(xin.numpy(), -77, -77 + R))
+
+
 def test_sparse_wide_ranges():
     """Few distinct values spread over a wide range: the output walks many
     empty values between runs."""
