@@ -125,15 +125,82 @@ typedef struct {
     int32_t hist_threads;    /* 256, 512 or 1024 */
     int32_t fill_ctas;
     int32_t fill_threads;    /* 256, 512 or 1024 */
-    int32_t reserved[3];
+    int32_t fill_chunk;      /* output positions per output CTA; when > 0 it
+                                replaces fill_ctas (the count then follows n) */
+    int32_t reserved[2];
 } rtcdf_params;
 
-/* The parameters rtcdf_sort would use for (n, R) on the current device. */
+/* The parameters rtcdf_sort would use for (n, R) on the current device
+ * (tuning table first, then the built-in rules). */
 rtcdf_status rtcdf_plan(uint64_t n, int64_t R, rtcdf_params *params);
 
 /*
+ * Tuning table.  rtcdf_sort, rtcdf_sort_ws, rtcdf_sort_host and
+ * rtcdf_sort_static take their launch parameters from a per-process table
+ * keyed by the range class ceil(log2 R) and the input-size class of n; a
+ * range/size pair with no entry, or an entry whose parameters do not fit the
+ * current device, falls back to the built-in rules (zero fields of an entry
+ * also keep the built-in choice).  The table starts as the one compiled into
+ * the library (measured on GB300 with rtcdf_autotune); rtcdf_tune_set replaces
+ * it, rtcdf_tune_reset restores the compiled-in one.  The input distribution
+ * is not a key: the sort cannot know it before its histogram, so the tuner
+ * ranks candidates over several distributions (Section 4.1's rule).
+ */
+#define RTCDF_TUNE_N_SMALL 0   /* n < 2^20 */
+#define RTCDF_TUNE_N_MEDIUM 1  /* 2^20 <= n < 2^26 */
+#define RTCDF_TUNE_N_LARGE 2   /* n >= 2^26 */
+
+typedef struct {
+    int32_t log2_R;        /* ceil(log2 R): 0 for R = 1, up to 24 */
+    int32_t n_class;       /* RTCDF_TUNE_N_* */
+    rtcdf_params params;
+} rtcdf_tune_entry;
+
+/* The size class of n (RTCDF_TUNE_N_*). */
+int32_t rtcdf_tune_n_class(uint64_t n);
+/* Replace the table (count == 0 empties it: built-in rules only).  Entries are
+ * copied; a later entry with the same key wins.  Thread-safe. */
+rtcdf_status rtcdf_tune_set(const rtcdf_tune_entry *entries, int32_t count);
+/* Restore the table compiled into the library. */
+rtcdf_status rtcdf_tune_reset(void);
+/* Copy up to `capacity` entries of the current table; *count = table size. */
+rtcdf_status rtcdf_tune_get(rtcdf_tune_entry *entries, int32_t capacity, int32_t *count);
+
+/*
+ * rtcdf_autotune -- time candidate launch parameters and pick one by the
+ * paper's rule (Section 4.1): for every condition (case) c and candidate k the
+ * median of `reps` sorts t(c, k) is measured with CUDA events on `stream`;
+ * r(c, k) = t(c, k) / min_k' t(c, k') is its time normalised to the fastest
+ * candidate for that condition, and the candidate with the smallest geometric
+ * mean of r over all conditions wins.
+ *
+ * cases[i].in / .out are device arrays of .n keys in [.minVal, .maxVal);
+ * `workspace` (256-byte aligned, zero-filled before first use, left zero-
+ * filled) holds at least rtcdf_workspace_size(max R) bytes.  Host outputs:
+ * times_ms[c * num_candidates + k] (median ms; -1 if candidate k cannot run
+ * case c on this device), geomean[k] (HUGE_VAL for a candidate that cannot
+ * run every case), *best.  Synchronises `stream`; not capturable.  Returns
+ * RTCDF_ERR_INVALID_ARG if no candidate runs every case, and the device
+ * status (e.g. RTCDF_ERR_KEY_OUT_OF_RANGE) if a sort recorded one.
+ */
+typedef struct {
+    const int32_t *in;
+    int32_t *out;
+    uint64_t n;
+    int64_t minVal;
+    int64_t maxVal;
+} rtcdf_tune_case;
+
+rtcdf_status rtcdf_autotune(const rtcdf_tune_case *cases, int32_t num_cases,
+                            const rtcdf_params *candidates, int32_t num_candidates, int32_t reps,
+                            void *workspace, size_t ws_bytes, float *times_ms, double *geomean,
+                            int32_t *best, rtcdf_stream_t stream);
+
+/*
  * rtcdf_sort_ex -- rtcdf_sort_ws with explicit launch parameters (for tuning
- * and tests).  `params` may be NULL.  When `debug` is non-NULL it receives
+ * and tests).  `params` may be NULL (tuning table, then built-in rules); when
+ * given it is used as is (its zero fields take the built-in rules, the tuning
+ * table is not consulted).  When `debug` is non-NULL it receives
  * device copies of the intermediates (device pointers, caller-owned):
  *   debug->tile_hist[0..R-1]  H after the histogram step (Algorithm 5)
  *   debug->cdf[0..R-1]        O[t] + local CDF, i.e. the inclusive CDF

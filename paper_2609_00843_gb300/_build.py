@@ -70,6 +70,7 @@ def build(jobs: int | None = None) -> dict:
     csrc = os.path.join(HERE, "csrc")
     srcs = sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cpp")))
     headers = glob.glob(os.path.join(csrc, "*.h")) + glob.glob(os.path.join(csrc, "*.cuh")) + \
+        glob.glob(os.path.join(csrc, "*.inc")) + \
         glob.glob(os.path.join(ROOT, "include", "*.h"))
     out = {"rtcdf": _build_lib(srcs, headers, lib_path(), jobs)}
     gsrc = [os.path.join(HERE, "gen", "gen.cu")]

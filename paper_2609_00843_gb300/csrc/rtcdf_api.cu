@@ -73,8 +73,8 @@ rtcdf_status check_range(int64_t minVal, int64_t maxVal, uint32_t *R) {
 
 // Choose the launch shape (Section 3.3): tile width T from shared memory, CTAs
 // per tile from occupancy, output CTAs from n.
-rtcdf_status make_plan(uint64_t n, uint32_t R, uintptr_t in_addr, uintptr_t out_addr,
-                       const rtcdf_params *p, Plan *pl) {
+rtcdf_status make_plan_with(uint64_t n, uint32_t R, uintptr_t in_addr, uintptr_t out_addr,
+                            const rtcdf_params *p, Plan *pl) {
     DeviceInfo dev;
     rtcdf_status st = device_info(&dev);
     if (st) return st;
@@ -131,16 +131,36 @@ rtcdf_status make_plan(uint64_t n, uint32_t R, uintptr_t in_addr, uintptr_t out_
     // waves' worth): the block scheduler then balances CTAs whose positions
     // cross many short runs against CTAs inside one long run.
     uint64_t body = n > head_out ? n - head_out : 0;
-    uint64_t want = q.fill_ctas > 0 ? (uint64_t)q.fill_ctas
-                                    : std::max<uint64_t>((uint64_t)dev.sms * 4, body / 32768);
-    want = std::min<uint64_t>(want, kMaxFillCtas);
-    uint64_t chunk = std::max<uint64_t>(4 * (uint64_t)pl->fill_threads, (body + want - 1) / want);
+    uint64_t chunk;
+    if (q.fill_chunk < 0 || q.fill_ctas < 0) return RTCDF_ERR_INVALID_ARG;
+    if (q.fill_chunk > 0) {
+        chunk = std::max<uint64_t>((uint64_t)q.fill_chunk,
+                                   (body + kMaxFillCtas - 1) / kMaxFillCtas);
+        chunk = std::max<uint64_t>(chunk, 4 * (uint64_t)pl->fill_threads);
+    } else {
+        uint64_t want = q.fill_ctas > 0 ? (uint64_t)q.fill_ctas
+                                        : std::max<uint64_t>((uint64_t)dev.sms * 4, body / 32768);
+        want = std::min<uint64_t>(want, kMaxFillCtas);
+        chunk = std::max<uint64_t>(4 * (uint64_t)pl->fill_threads, (body + want - 1) / want);
+    }
     chunk = (chunk + 3) / 4 * 4;
     pl->fill_chunk = chunk;
     pl->fill_ctas = (uint32_t)(1 + (n > head_out ? (n - head_out - 1) / chunk : 0));
     if (pl->fill_ctas > kMaxFillCtas) return RTCDF_ERR_INVALID_ARG;
     pl->head = head_in;
     return RTCDF_OK;
+}
+
+// Explicit parameters are used as given; without them the tuning table is
+// tried first and the built-in rules cover what it lacks (or what does not fit
+// this device).
+rtcdf_status make_plan(uint64_t n, uint32_t R, uintptr_t in_addr, uintptr_t out_addr,
+                       const rtcdf_params *p, Plan *pl) {
+    if (p) return make_plan_with(n, R, in_addr, out_addr, p, pl);
+    rtcdf_params t;
+    if (tune_lookup(n, R, &t) && make_plan_with(n, R, in_addr, out_addr, &t, pl) == RTCDF_OK)
+        return RTCDF_OK;
+    return make_plan_with(n, R, in_addr, out_addr, nullptr, pl);
 }
 
 bool overlaps(const void *a, const void *b, uint64_t n) {
@@ -340,6 +360,7 @@ rtcdf_status rtcdf_plan(uint64_t n, int64_t R, rtcdf_params *params) {
     params->hist_threads = pl.hist_threads;
     params->fill_ctas = (int32_t)pl.fill_ctas;
     params->fill_threads = pl.fill_threads;
+    params->fill_chunk = (int32_t)std::min<uint64_t>(pl.fill_chunk, INT32_MAX);
     return RTCDF_OK;
 }
 

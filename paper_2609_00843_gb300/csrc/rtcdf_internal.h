@@ -6,7 +6,13 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "../../include/rtcdf.h"
+
 namespace rtcdf {
+
+// Launch parameters of the tuning table for (n, R), if it has an entry
+// (tune.cu).
+bool tune_lookup(uint64_t n, uint32_t R, rtcdf_params *out);
 
 // Device status bits (mirror RTCDF_DEV_* in rtcdf.h).
 constexpr uint32_t kDevKeyOutOfRange = 0x1;

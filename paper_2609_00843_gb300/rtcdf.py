@@ -42,7 +42,17 @@ class RtcdfError(RuntimeError):
 class Params(ctypes.Structure):
     _fields_ = [("tile_width", ctypes.c_int32), ("hist_ctas_per_tile", ctypes.c_int32),
                 ("hist_threads", ctypes.c_int32), ("fill_ctas", ctypes.c_int32),
-                ("fill_threads", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
+                ("fill_threads", ctypes.c_int32), ("fill_chunk", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 2)]
+
+
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("log2_R", ctypes.c_int32), ("n_class", ctypes.c_int32), ("params", Params)]
+
+
+class TuneCase(ctypes.Structure):
+    _fields_ = [("in_ptr", ctypes.c_void_p), ("out_ptr", ctypes.c_void_p), ("n", ctypes.c_uint64),
+                ("minVal", ctypes.c_int64), ("maxVal", ctypes.c_int64)]
 
 
 class Debug(ctypes.Structure):
@@ -120,6 +130,16 @@ def lib():
             L.rtcdf_sort_batched_ws.argtypes = [vp, vp, vp, vp, sz, vp]
             L.rtcdf_batch_status_get.argtypes = [vp, vp, ctypes.POINTER(i32)]
             L.rtcdf_sort_batched.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+            L.rtcdf_tune_n_class.argtypes = [u64]
+            L.rtcdf_tune_n_class.restype = i32
+            L.rtcdf_tune_set.argtypes = [ctypes.POINTER(TuneEntry), i32]
+            L.rtcdf_tune_reset.argtypes = []
+            L.rtcdf_tune_get.argtypes = [ctypes.POINTER(TuneEntry), i32, ctypes.POINTER(i32)]
+            L.rtcdf_autotune.argtypes = [ctypes.POINTER(TuneCase), i32, ctypes.POINTER(Params), i32,
+                                         i32, vp, sz, ctypes.POINTER(ctypes.c_float),
+                                         ctypes.POINTER(ctypes.c_double), ctypes.POINTER(i32), vp]
+            for f in ("rtcdf_tune_set", "rtcdf_tune_reset", "rtcdf_tune_get", "rtcdf_autotune"):
+                getattr(L, f).restype = ctypes.c_int
             for f in ("rtcdf_serve_trace", "rtcdf_serve_sequential"):
                 getattr(L, f).argtypes = [ctypes.POINTER(ServerConfig), ctypes.POINTER(Request),
                                           i64, ctypes.POINTER(Result), ctypes.POINTER(ServeStats)]
@@ -288,6 +308,61 @@ def rtcdf_plan(n: int, R: int) -> Params:
     if rc != OK:
         raise RtcdfError(rc, "rtcdf_plan")
     return p
+
+
+def rtcdf_tune_n_class(n: int) -> int:
+    return lib().rtcdf_tune_n_class(n)
+
+
+def rtcdf_tune_set(entries) -> None:
+    """Install a tuning table: an iterable of (log2_R, n_class, Params)."""
+    entries = list(entries)
+    arr = (TuneEntry * max(1, len(entries)))()
+    for i, (lr, nc, p) in enumerate(entries):
+        arr[i].log2_R, arr[i].n_class, arr[i].params = lr, nc, p
+    rc = lib().rtcdf_tune_set(arr, len(entries))
+    if rc != OK:
+        raise RtcdfError(rc, "rtcdf_tune_set")
+
+
+def rtcdf_tune_reset() -> None:
+    rc = lib().rtcdf_tune_reset()
+    if rc != OK:
+        raise RtcdfError(rc, "rtcdf_tune_reset")
+
+
+def rtcdf_tune_get() -> list:
+    """The current tuning table as a list of (log2_R, n_class, Params)."""
+    cnt = ctypes.c_int32(0)
+    rc = lib().rtcdf_tune_get(None, 0, ctypes.byref(cnt))
+    if rc != OK:
+        raise RtcdfError(rc, "rtcdf_tune_get")
+    arr = (TuneEntry * max(1, cnt.value))()
+    rc = lib().rtcdf_tune_get(arr, cnt.value, ctypes.byref(cnt))
+    if rc != OK:
+        raise RtcdfError(rc, "rtcdf_tune_get")
+    return [(arr[i].log2_R, arr[i].n_class, arr[i].params) for i in range(cnt.value)]
+
+
+def rtcdf_autotune(cases, candidates, reps: int, ws_ptr: int, ws_bytes: int, stream: int = 0):
+    """cases: iterable of (in_ptr, out_ptr, n, minVal, maxVal); candidates: Params list.
+    Returns (times_ms [cases x candidates] as nested lists, geomeans, best index)."""
+    cases = list(cases)
+    candidates = list(candidates)
+    carr = (TuneCase * len(cases))()
+    for i, (ip, op, n, a, b) in enumerate(cases):
+        carr[i].in_ptr, carr[i].out_ptr, carr[i].n, carr[i].minVal, carr[i].maxVal = ip, op, n, a, b
+    parr = (Params * len(candidates))(*candidates)
+    times = (ctypes.c_float * (len(cases) * len(candidates)))()
+    gm = (ctypes.c_double * len(candidates))()
+    best = ctypes.c_int32(-1)
+    rc = lib().rtcdf_autotune(carr, len(cases), parr, len(candidates), reps, ws_ptr, ws_bytes,
+                              times, gm, ctypes.byref(best), stream)
+    if rc != OK:
+        raise RtcdfError(rc, "rtcdf_autotune")
+    k = len(candidates)
+    t = [[times[c * k + j] for j in range(k)] for c in range(len(cases))]
+    return t, [gm[j] for j in range(k)], best.value
 
 
 def rtcdf_status_str(code: int) -> str:
