@@ -34,6 +34,33 @@ WORKLOAD = ("sweep: n=1e8 int32 keys per array, minVal=-1000, R in {2^7,2^10,2^1
             "{uniform, normal(mean minVal+R/2, sd R/8), all-equal(minVal+R/3)}; 12 arrays per step")
 
 
+SPEC_HBM_GBS = 7900.0  # GB300 HBM3e nominal bandwidth: the second (spec) roofline column
+
+
+def paper_protocol_ms(sort_once, stream, runs=3, reps=30, warm=10, between=None):
+    """The paper's timing protocol (Section 4): `warm` untimed sorts, then
+    `runs` runs of `reps` sorts, each sort bracketed by CUDA events on the
+    launching stream; the median of the per-run medians.  `between` (e.g. an
+    L2 flush) runs after each timed sort, outside its events."""
+    import torch
+    for _ in range(warm):
+        sort_once()
+    meds = []
+    for _ in range(runs):
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(reps)]
+        for a, b in ev:
+            a.record(stream)
+            sort_once()
+            b.record(stream)
+            if between is not None:
+                between()
+        stream.synchronize()
+        ts = sorted(a.elapsed_time(b) for a, b in ev)
+        meds.append(ts[len(ts) // 2])
+    return statistics.median(meds)
+
+
 def peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
@@ -164,13 +191,32 @@ def run_reference(args, rank, world):
         "impl": "reference",
         "config": {"workload": WORKLOAD, "n_per_array": n_sample, "arrays": len(cases)},
         "cpu_baseline": {"value": value, "unit": "GKeys/s", "cores": 1, "kind": "oracle",
-                         "sample": f"12 sweep arrays at n={n_sample} keys each per step"},
+                         "sample": f"12 sweep arrays at n={n_sample} keys each per step",
+                         **cpu_info()},
         "e2e": {"value": value, "unit": "GKeys/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
         "gpu_launches": 0,
     }
     print(json.dumps(line), flush=True)
     return 0
+
+
+def cpu_info() -> dict:
+    """Host CPU model and core count, for the CPU baseline's record."""
+    model = ""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                k = ln.split(":")[0].strip().lower()
+                if k in ("model name", "cpu model", "hardware") and ":" in ln:
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    if not model:
+        import platform
+        model = platform.processor() or platform.machine()
+    return {"cpu_model": model, "nproc": os.cpu_count()}
 
 
 def cpu_baseline_sweep(host_inputs, cases):
@@ -182,9 +228,91 @@ def cpu_baseline_sweep(host_inputs, cases):
         oracle.counting_sort(a, MIN_SWEEP, MIN_SWEEP + c["R"], lib)
     dt = time.perf_counter() - t0
     keys = sum(a.size for a in host_inputs)
+    ci = cpu_info()
     return {"value": keys / dt / 1e9, "unit": "GKeys/s", "cores": 1, "kind": "oracle",
             "sample": f"one pass over the 12 sweep arrays (n=1e8 each, {keys} keys), "
-                      f"{dt:.1f} s single-threaded"}
+                      f"{dt:.1f} s single-threaded (1 of {ci['nproc']} cores)", **ci}
+
+
+def single_config(stream):
+    """The small workload: n = 1e6 int32 keys, minVal = 0, R = 2^7, uniform,
+    seed 0.  Its 8 MB working set sits in L2, so it is timed warm (back-to-back
+    sorts of the same array) and with L2 flushed between sorts (a 256 MB buffer
+    written after each timed sort, outside its events)."""
+    import torch
+    from paper_2609_00843_gb300 import gen, rtcdf
+    n, R = 1_000_000, 1 << 7
+    sh = stream.cuda_stream
+    with torch.cuda.stream(stream):
+        x = torch.empty(n, dtype=torch.int32, device="cuda")
+        gen.keys_device(x.data_ptr(), n, 0, R, gen.UNIFORM, 0, stream=sh)
+        out = torch.empty_like(x)
+        flush = torch.empty(64 << 20, dtype=torch.int32, device="cuda")
+    wsb = rtcdf.rtcdf_workspace_size(R)
+    ws = torch.zeros(wsb // 4 + 64, dtype=torch.int32, device="cuda")
+    stream.synchronize()
+
+    def once():
+        rc = rtcdf.rtcdf_sort_ws(x.data_ptr(), out.data_ptr(), n, 0, R, ws.data_ptr(), wsb, sh)
+        if rc != rtcdf.OK:
+            raise rtcdf.RtcdfError(rc, "rtcdf_sort_ws")
+
+    def do_flush():
+        with torch.cuda.stream(stream):
+            flush.fill_(1)
+    warm = paper_protocol_ms(once, stream)
+    cold = paper_protocol_ms(once, stream, between=do_flush)
+    # host wall-clock of one call + synchronisation (what a blocking caller sees)
+    walls = []
+    for _ in range(30):
+        t0 = time.perf_counter()
+        once()
+        stream.synchronize()
+        walls.append((time.perf_counter() - t0) * 1e3)
+    res = {"workload": "n=1e6 int32, minVal=0, R=2^7, uniform, seed 0",
+           "warm_ms": round(warm, 5), "l2_flushed_ms": round(cold, 5),
+           "warm_GKeys_s": round(n / (warm * 1e-3) / 1e9, 2),
+           "l2_flushed_GKeys_s": round(n / (cold * 1e-3) / 1e9, 2),
+           "host_wall_ms_median": round(statistics.median(walls), 4),
+           "note": "launch-latency bound: 8n bytes at the copy bandwidth take ~1.2 us"}
+    del x, out, flush, ws
+    return res
+
+
+def large_config(stream):
+    """The large workload: n = 1e9 int32 keys (4 GB in, 4 GB out), minVal = 0,
+    R in {2^12, 2^16, 2^18}, uniform and normal; one array at a time."""
+    import torch
+    from paper_2609_00843_gb300 import gen, rtcdf
+    n = 1_000_000_000
+    sh = stream.cuda_stream
+    hbm, _ = peaks()
+    with torch.cuda.stream(stream):
+        x = torch.empty(n, dtype=torch.int32, device="cuda")
+        out = torch.empty_like(x)
+    wsb = rtcdf.rtcdf_workspace_size(1 << 18)
+    ws = torch.zeros(wsb // 4 + 64, dtype=torch.int32, device="cuda")
+    rows = []
+    for R in (1 << 12, 1 << 16, 1 << 18):
+        for d, name in ((gen.UNIFORM, "uniform"), (gen.NORMAL, "normal")):
+            gen.keys_device(x.data_ptr(), n, 0, R, d, gen.derive_seed(3, d, R.bit_length() - 1),
+                            stream=sh)
+
+            def once(R=R):
+                rc = rtcdf.rtcdf_sort_ws(x.data_ptr(), out.data_ptr(), n, 0, R, ws.data_ptr(), wsb, sh)
+                if rc != rtcdf.OK:
+                    raise rtcdf.RtcdfError(rc, "rtcdf_sort_ws")
+            ms = paper_protocol_ms(once, stream, runs=3, reps=5, warm=2)
+            rc, bits = rtcdf.rtcdf_ws_status_get(ws.data_ptr(), sh)
+            if rc != rtcdf.OK:
+                raise rtcdf.RtcdfError(rc, "device status (large)")
+            rows.append({"R": R, "dist": name, "ms": round(ms, 4),
+                         "GKeys_s": round(n / (ms * 1e-3) / 1e9, 1),
+                         "frac_8n_roofline": round(8 * n / (ms * 1e-3) / 1e9 / hbm, 4)})
+    del x, out, ws
+    torch.cuda.empty_cache()
+    return {"workload": "n=1e9 int32, minVal=0, R in {2^12,2^16,2^18}, uniform/normal",
+            "rows": rows}
 
 
 def cub_comparison(cases, ins, outs, n, stream, nsteps, ours_ms):
@@ -331,10 +459,10 @@ def batched_comparison(args, stream, num_segments=4096):
 def serving_comparison(count: int, budget_gb: float = 32.0):
     """Serving workload: a Poisson stream of sort requests, n log-uniform in
     [1e4, 1e8], R log-uniform in [2^7, 2^18], mixed shapes, 32 GB admission
-    budget.  The arrival rate is 0.9 x the throughput of sequential
-    per-request calls (measured first with every request present at t=0);
-    the same trace is then served sequentially and by the continuous-batching
-    server.  Latency = completion - arrival; a request's keys are written into
+    budget.  The arrival rate is rho x the throughput of sequential
+    per-request calls (measured first with every request present at t=0),
+    rho in {0.5, 0.9, 1.5}; each trace is served sequentially and by the
+    continuous-batching server.  Latency = completion - arrival; a request's keys are written into
     its device slot by the generator at admission (data arrival)."""
     import numpy as np
     from paper_2609_00843_gb300 import gen, rtcdf
@@ -350,32 +478,42 @@ def serving_comparison(count: int, budget_gb: float = 32.0):
     r0 = rtcdf.make_requests(n, mn, mx, dist, seeds, zero)
     _, st0 = rtcdf.rtcdf_serve_sequential(cfg(), r0, count)
     _, st1 = rtcdf.rtcdf_serve_trace(cfg(), r0, count)
-    rate = 0.9 * count / st0.makespan_s
-    arr = gen.poisson_arrivals(seed, count, rate)
-    reqs = rtcdf.make_requests(n, mn, mx, dist, seeds, arr)
-    out = {"workload": f"{count} requests, Poisson arrivals at 0.9 x sequential throughput "
-                       f"({rate:.0f}/s), n log-uniform [1e4,1e8], R log-uniform [2^7,2^18], "
-                       f"mixed shapes, {budget_gb:g} GB admission budget",
-           "total_keys": int(n.sum()), "arrival_rate_per_s": round(rate, 1),
+    seq_rate = count / st0.makespan_s
+    out = {"workload": f"{count} requests, Poisson arrivals at rho x sequential throughput "
+                       f"(rho in {{0.5, 0.9, 1.5}}), n log-uniform [1e4,1e8], R log-uniform "
+                       f"[2^7,2^18], mixed shapes, {budget_gb:g} GB admission budget",
+           "total_keys": int(n.sum()), "sequential_rate_per_s": round(seq_rate, 1),
            "saturated": {"note": "every request present at t=0: capacity in keys/s",
                          "sequential_GKeys_s": round(st0.total_keys / st0.makespan_s / 1e9, 2),
                          "server_GKeys_s": round(st1.total_keys / st1.makespan_s / 1e9, 2),
-                         "server_vs_sequential": round(st0.makespan_s / st1.makespan_s, 3)}}
-    for name, fn in (("sequential", rtcdf.rtcdf_serve_sequential), ("server", rtcdf.rtcdf_serve_trace)):
-        res, st = fn(cfg(), reqs, count)
-        lat = np.array([res[i].done_s - arr[i] for i in range(count)])
-        ok = all(res[i].status == 0 for i in range(count))
-        out[name] = {"GKeys_s": round(st.total_keys / st.makespan_s / 1e9, 2),
-                     "makespan_s": round(st.makespan_s, 4),
-                     "p50_latency_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
-                     "p99_latency_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
-                     "all_ok": ok, "launches_batched": int(st.launches_batched),
-                     "launches_single": int(st.launches_single),
-                     "max_inflight": int(st.max_inflight), "peak_GB": round(st.peak_bytes / 1e9, 2)}
+                         "server_vs_sequential": round(st0.makespan_s / st1.makespan_s, 3)},
+           "load": {}}
+    for rho in (0.5, 0.9, 1.5):
+        rate = rho * seq_rate
+        arr = gen.poisson_arrivals(seed, count, rate)
+        reqs = rtcdf.make_requests(n, mn, mx, dist, seeds, arr)
+        row = {"arrival_rate_per_s": round(rate, 1)}
+        for name, fn in (("sequential", rtcdf.rtcdf_serve_sequential),
+                         ("server", rtcdf.rtcdf_serve_trace)):
+            res, st = fn(cfg(), reqs, count)
+            lat = np.array([res[i].done_s - arr[i] for i in range(count)])
+            ok = all(res[i].status == 0 for i in range(count))
+            row[name] = {"GKeys_s": round(st.total_keys / st.makespan_s / 1e9, 2),
+                         "makespan_s": round(st.makespan_s, 4),
+                         "p50_latency_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                         "p99_latency_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
+                         "all_ok": ok, "launches_batched": int(st.launches_batched),
+                         "launches_single": int(st.launches_single),
+                         "max_inflight": int(st.max_inflight),
+                         "peak_GB": round(st.peak_bytes / 1e9, 2)}
+        row["p99_ratio_sequential_vs_server"] = round(
+            row["sequential"]["p99_latency_ms"] / max(1e-9, row["server"]["p99_latency_ms"]), 3)
+        out["load"][str(rho)] = row
+    main = out["load"]["0.9"]
+    out["sequential"], out["server"] = main["sequential"], main["server"]
     out["throughput_ratio_server_vs_sequential"] = round(
         out["server"]["GKeys_s"] / max(1e-9, out["sequential"]["GKeys_s"]), 3)
-    out["p99_ratio_sequential_vs_server"] = round(
-        out["sequential"]["p99_latency_ms"] / max(1e-9, out["server"]["p99_latency_ms"]), 3)
+    out["p99_ratio_sequential_vs_server"] = main["p99_ratio_sequential_vs_server"]
     return out
 
 
@@ -393,6 +531,8 @@ def main():
     ap.add_argument("--no-serve", action="store_true", help="skip the serving comparison")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-single", action="store_true", help="skip the n=1e6 single-array config")
+    ap.add_argument("--no-large", action="store_true", help="skip the n=1e9 configs")
     ap.add_argument("--preheat-s", type=float, default=0.5,
                     help="seconds of untimed load after warm-up so clocks settle")
     ap.add_argument("--only", default="",
@@ -503,20 +643,25 @@ def main():
     torch.cuda.synchronize()
     barrier()
     total_ms = t0.elapsed_time(t1)
-    # Per array: K back-to-back sorts of the same array, uninstrumented.
-    solo_ms = []
+    # Per array: K back-to-back sorts of the same array, uninstrumented, and
+    # the paper's protocol (3 runs x 30 event-timed sorts after 10 warm-ups,
+    # median of medians).
+    solo_ms, proto_ms = [], []
     for i, c in enumerate(cases):
-        a0 = torch.cuda.Event(enable_timing=True)
-        a1 = torch.cuda.Event(enable_timing=True)
-        a0.record(stream)
-        for k in range(nsteps):
+        def sort_once(i=i, c=c):
             rc = rtcdf.rtcdf_sort_ex(ins[i].data_ptr(), outs[i].data_ptr(), n, MIN_SWEEP,
                                      MIN_SWEEP + c["R"], None, ws.data_ptr(), ws_bytes, None, sh)
             if rc != rtcdf.OK:
                 raise rtcdf.RtcdfError(rc, "rtcdf_sort_ex")
+        a0 = torch.cuda.Event(enable_timing=True)
+        a1 = torch.cuda.Event(enable_timing=True)
+        a0.record(stream)
+        for k in range(nsteps):
+            sort_once()
         a1.record(stream)
         stream.synchronize()
         solo_ms.append(a0.elapsed_time(a1) / nsteps)
+        proto_ms.append(paper_protocol_ms(sort_once, stream))
     # Instrumented region: the same K steps with CUDA events on the launching
     # stream before and after every kernel, for the per-kernel durations.
     for k in range(nsteps):
@@ -548,9 +693,16 @@ def main():
     per_config = []
     for i, c in enumerate(cases):
         ms = solo_ms[i]
+        pp = rtcdf.rtcdf_plan(n, c["R"])
         per_config.append({"R": c["R"], "dist": c["dist_name"], "ms": round(ms, 5),
                            "GKeys_s": round(n / (ms * 1e-3) / 1e9, 2),
                            "frac_8n_roofline": round(8 * n / (ms * 1e-3) / 1e9 / hbm, 4),
+                           "frac_8n_spec": round(8 * n / (ms * 1e-3) / 1e9 / SPEC_HBM_GBS, 4),
+                           "ms_paper_protocol": round(proto_ms[i], 5),
+                           "launch": {"T": pp.tile_width, "m": -(-c["R"] // pp.tile_width),
+                                      "hist_ctas": pp.hist_ctas_per_tile * -(-c["R"] // pp.tile_width),
+                                      "hist_threads": pp.hist_threads, "fill_ctas": pp.fill_ctas,
+                                      "fill_threads": pp.fill_threads},
                            "ms_instrumented": round(per_case_ms[i] / nsteps, 5),
                            "hist_ms": round(stage_ms[i][0] / nsteps, 5),
                            "scan_ms": round(stage_ms[i][1] / nsteps, 5),
@@ -573,6 +725,8 @@ def main():
                 "algorithmic_bytes_per_launch": 4 * n}
     whole = {"achieved_8n_GBs": round(8 * n * len(cases) / (sort_ms * 1e-3) / 1e9, 1)}
     whole["frac_8n_roofline"] = round(whole["achieved_8n_GBs"] / hbm, 4)
+    whole["frac_8n_spec"] = round(whole["achieved_8n_GBs"] / SPEC_HBM_GBS, 4)
+    whole["spec_GBs"] = SPEC_HBM_GBS
 
     line = {
         "metric": "sort throughput (GKeys/s) on the RT-CDF sweep; fraction of 8n-byte HBM roofline per R",
@@ -595,11 +749,15 @@ def main():
     if not args.no_cub and rank == 0:
         line["cub_comparison"] = cub_comparison(cases, ins, outs, n, stream, nsteps, solo_ms)
 
+    if not args.no_single and rank == 0:
+        line["single"] = single_config(stream)
+
     if not args.no_batched and rank == 0:
         line["batched"] = batched_comparison(args, stream, args.batched_segments)
 
     if not args.no_serve and rank == 0:
         line["serve"] = serving_comparison(args.serve_requests)
+
 
     # End to end through the C ABI with host buffers (rtcdf_sort_host): pinned
     # host input -> chunked upload overlapped with the histogram -> scan and
@@ -635,6 +793,12 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         host = [x.cpu().numpy() for x in ins]
         line["cpu_baseline"] = cpu_baseline_sweep(host, cases)
+
+    if not args.no_large and rank == 0:
+        # the sweep arrays are no longer needed: make room for 8 GB
+        del ins[:], outs[:]
+        torch.cuda.empty_cache()
+        line["large"] = large_config(stream)
 
     if rank == 0:
         print(json.dumps(line), flush=True)
