@@ -272,6 +272,19 @@ typedef struct {
 rtcdf_status rtcdf_batch_plan_create(const int64_t *seg_offsets, const int64_t *seg_minVal,
                                      const int64_t *seg_maxVal, int32_t num_segments,
                                      rtcdf_batch_plan **plan);
+/* Work-item sizes of a segmented sort (zero = built-in choice). */
+typedef struct {
+    int32_t hist_chunk;   /* keys per histogram item of a large segment (>= 4096; default 131072) */
+    int32_t fill_chunk;   /* output positions per output item (>= 4096; default 65536) */
+    int32_t small_max_n;  /* longest segment sorted inside one CTA (<= 65535; default 65535) */
+    int32_t reserved[5];
+} rtcdf_batch_params;
+
+/* rtcdf_batch_plan_create with explicit work-item sizes (`params` may be NULL). */
+rtcdf_status rtcdf_batch_plan_create_ex(const int64_t *seg_offsets, const int64_t *seg_minVal,
+                                        const int64_t *seg_maxVal, int32_t num_segments,
+                                        const rtcdf_batch_params *params,
+                                        rtcdf_batch_plan **plan);
 rtcdf_status rtcdf_batch_plan_destroy(rtcdf_batch_plan *plan);
 rtcdf_status rtcdf_batch_workspace_size(const rtcdf_batch_plan *plan, size_t *bytes);
 rtcdf_status rtcdf_batch_plan_info(const rtcdf_batch_plan *plan, rtcdf_batch_info *info);

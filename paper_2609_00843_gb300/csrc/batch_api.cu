@@ -28,16 +28,15 @@ struct rtcdf_batch_plan {
 
 namespace {
 
-constexpr uint64_t kHistChunk = 1ull << 17;   // keys per HIST item
-constexpr uint32_t kFillChunk = 1u << 16;     // positions per FILL item
-
 size_t words_align(size_t words) { return (words + 63) / 64 * 64; }  // 256-byte units
 
 }  // namespace
 
 namespace rtcdf {
 
-int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P) {
+int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P, const BatchTuning &tun) {
+    const uint64_t kHistChunk = tun.hist_chunk;
+    const uint32_t kFillChunk = tun.fill_chunk;
     for (uint32_t s = 0; s < S; s++) {
         if (spec[s].n >= (1ull << 32)) return 1;
         if (spec[s].minVal < INT32_MIN || spec[s].maxVal > ((int64_t)1 << 31)) return 2;
@@ -64,7 +63,7 @@ int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P) {
         g.minVal = (int32_t)spec[s].minVal;
         P->total_keys += g.n;
         if (g.n == 0) continue;
-        if (g.n <= kBatchSmallMaxN && g.R <= kBatchSmallMaxR) {
+        if (g.n <= tun.small_max_n && g.R <= kBatchSmallMaxR) {
             small.push_back(BatchItem{kItemSmall, s, 0, 0, 0, 0});
             P->small_segs++;
             continue;
@@ -117,7 +116,25 @@ extern "C" {
 rtcdf_status rtcdf_batch_plan_create(const int64_t *seg_offsets, const int64_t *seg_minVal,
                                      const int64_t *seg_maxVal, int32_t num_segments,
                                      rtcdf_batch_plan **plan_out) {
+    return rtcdf_batch_plan_create_ex(seg_offsets, seg_minVal, seg_maxVal, num_segments, nullptr,
+                                      plan_out);
+}
+
+rtcdf_status rtcdf_batch_plan_create_ex(const int64_t *seg_offsets, const int64_t *seg_minVal,
+                                        const int64_t *seg_maxVal, int32_t num_segments,
+                                        const rtcdf_batch_params *params,
+                                        rtcdf_batch_plan **plan_out) {
     if (!plan_out || num_segments < 0) return RTCDF_ERR_INVALID_ARG;
+    BatchTuning tun;
+    if (params) {
+        if (params->hist_chunk < 0 || (params->hist_chunk > 0 && params->hist_chunk < 4096) ||
+            params->fill_chunk < 0 || (params->fill_chunk > 0 && params->fill_chunk < 4096) ||
+            params->small_max_n < 0 || params->small_max_n > (int32_t)kBatchSmallMaxN)
+            return RTCDF_ERR_INVALID_ARG;
+        if (params->hist_chunk) tun.hist_chunk = (uint64_t)params->hist_chunk;
+        if (params->fill_chunk) tun.fill_chunk = (uint32_t)params->fill_chunk;
+        if (params->small_max_n) tun.small_max_n = (uint32_t)params->small_max_n;
+    }
     *plan_out = nullptr;
     if (num_segments > 0 && (!seg_offsets || !seg_minVal || !seg_maxVal)) return RTCDF_ERR_INVALID_ARG;
     const uint32_t S = (uint32_t)num_segments;
@@ -129,7 +146,7 @@ rtcdf_status rtcdf_batch_plan_create(const int64_t *seg_offsets, const int64_t *
                           (uint64_t)(seg_offsets[s + 1] - seg_offsets[s]), seg_minVal[s], seg_maxVal[s]};
     }
     HostPlan hp;
-    const int rc = build_host_plan(spec.data(), S, &hp);
+    const int rc = build_host_plan(spec.data(), S, &hp, tun);
     if (rc) return (rtcdf_status)rc;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RTCDF_ERR_CUDA;

@@ -79,6 +79,14 @@ struct HostPlan {
 };
 // Validates ranges (R in [1, kBatchMaxR], inside int32) and n < 2^32;
 // returns RTCDF-style codes (0 ok, 1 invalid argument, 2 range).
-int build_host_plan(const SegSpec *segs, uint32_t S, HostPlan *plan);
+// Work-item sizes of a plan (rtcdf_batch_params with the defaults filled in).
+struct BatchTuning {
+    uint64_t hist_chunk = 1ull << 17;   // keys per HIST item
+    uint32_t fill_chunk = 1u << 16;     // positions per FILL item
+    uint32_t small_max_n = kBatchSmallMaxN;
+};
+
+int build_host_plan(const SegSpec *segs, uint32_t S, HostPlan *plan,
+                    const BatchTuning &tuning = BatchTuning());
 
 }  // namespace rtcdf

@@ -29,10 +29,18 @@ __device__ __forceinline__ int first_run_after(const uint32_t *s_end, int lo, in
     return lo;
 }
 
+// Runs per shared-memory window: four per thread, so that a CTA whose
+// positions cross thousands of short runs (the tails of a peaked distribution
+// over a wide range) needs few window rounds -- each round costs a global
+// round trip and two barriers.
+template <int WIN>
+constexpr int kRunWindow = 4 * WIN;
+
 template <int WIN>
 __global__ void __launch_bounds__(WIN) fill_kernel(FillArgs a) {
-    __shared__ uint32_t s_end[WIN];
-    __shared__ int32_t s_val[WIN];
+    constexpr int RW = kRunWindow<WIN>;
+    __shared__ uint32_t s_end[RW];
+    __shared__ int32_t s_val[RW];
     const int tid = threadIdx.x;
     const uint32_t c = blockIdx.x;
 
@@ -46,15 +54,17 @@ __global__ void __launch_bounds__(WIN) fill_kernel(FillArgs a) {
     const uint32_t P1 = (c + 1 == a.fill_ctas) ? n : head + (c + 1) * fc;
     const uint32_t D = a.ctl->num_runs;
     uint32_t k_cur = a.start_run[c];
+    // Last run this CTA can need: the one holding the next CTA's first position.
+    const uint32_t k_last = (c + 1 < a.fill_ctas) ? min(a.start_run[c + 1], D - 1) : D - 1;
     int4 *vout = reinterpret_cast<int4 *>(a.out + head);  // 16-byte aligned frame
     uint32_t pos = P0;
 
     while (pos < P1 && k_cur < D) {
-        const int nw = (int)min((uint32_t)WIN, D - k_cur);
+        const int nw = (int)min((uint32_t)RW, (k_last >= k_cur ? k_last - k_cur : 0u) + 1u);
         __syncthreads();  // previous window no longer in use
-        if (tid < nw) {
-            s_end[tid] = a.run_end[k_cur + tid];
-            s_val[tid] = a.run_val[k_cur + tid];
+        for (int i = tid; i < nw; i += WIN) {
+            s_end[i] = a.run_end[k_cur + i];
+            s_val[i] = a.run_val[k_cur + i];
         }
         __syncthreads();
         const uint32_t hi = min(P1, s_end[nw - 1]);

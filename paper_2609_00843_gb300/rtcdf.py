@@ -46,6 +46,11 @@ class Params(ctypes.Structure):
                 ("reserved", ctypes.c_int32 * 2)]
 
 
+class BatchParams(ctypes.Structure):
+    _fields_ = [("hist_chunk", ctypes.c_int32), ("fill_chunk", ctypes.c_int32),
+                ("small_max_n", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+
+
 class TuneEntry(ctypes.Structure):
     _fields_ = [("log2_R", ctypes.c_int32), ("n_class", ctypes.c_int32), ("params", Params)]
 
@@ -124,6 +129,9 @@ def lib():
             L.rtcdf_sort_static.argtypes = [vp, vp, u64, i64, i64, vp]
             L.rtcdf_sort_host.argtypes = [vp, vp, u64, i64, i64, vp]
             L.rtcdf_batch_plan_create.argtypes = [vp, vp, vp, i32, ctypes.POINTER(vp)]
+            L.rtcdf_batch_plan_create_ex.argtypes = [vp, vp, vp, i32, ctypes.POINTER(BatchParams),
+                                                     ctypes.POINTER(vp)]
+            L.rtcdf_batch_plan_create_ex.restype = ctypes.c_int
             L.rtcdf_batch_plan_destroy.argtypes = [vp]
             L.rtcdf_batch_workspace_size.argtypes = [vp, ctypes.POINTER(sz)]
             L.rtcdf_batch_plan_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
@@ -188,14 +196,15 @@ def _i64_array(xs):
 class BatchPlan:
     """A segmented-sort plan (rtcdf_batch_plan_create / _destroy)."""
 
-    def __init__(self, seg_offsets, seg_minVal, seg_maxVal):
+    def __init__(self, seg_offsets, seg_minVal, seg_maxVal, params: BatchParams | None = None):
         self._keep = [_i64_array(seg_offsets), _i64_array(seg_minVal), _i64_array(seg_maxVal)]
         S = len(self._keep[1][0])
         if len(self._keep[0][0]) != S + 1 or len(self._keep[2][0]) != S:
             raise ValueError("seg_offsets needs S+1 entries, seg_minVal/seg_maxVal S entries")
         h = ctypes.c_void_p(0)
-        rc = lib().rtcdf_batch_plan_create(self._keep[0][1], self._keep[1][1], self._keep[2][1], S,
-                                           ctypes.byref(h))
+        rc = lib().rtcdf_batch_plan_create_ex(self._keep[0][1], self._keep[1][1], self._keep[2][1], S,
+                                              ctypes.byref(params) if params is not None else None,
+                                              ctypes.byref(h))
         if rc != OK:
             raise RtcdfError(rc, "rtcdf_batch_plan_create")
         self.handle = h

@@ -1,4 +1,5 @@
-"""Autotuner for the single-array sort's launch parameters.
+"""Autotuner for the launch parameters of the single-array sort and the
+work-item sizes of the segmented sort.
 
 The paper fixes one tile width per range size by measuring every candidate
 width on 20 conditions (10 input sizes x 2 input distributions), normalising
@@ -26,7 +27,10 @@ generator's shapes).  Run on the target GPU::
 
 which writes DIR/tune_table.json (every measured time and geometric mean) and
 DIR/tune_table.inc (the table in the form csrc/tune_table.inc takes; copy it
-there and rebuild to make it the library's built-in table).
+there and rebuild to make it the library's built-in table).  With
+``--batched`` it ranks the segmented sort's work-item sizes (histogram keys
+per item, output positions per item, longest in-CTA segment) over several
+segment-shape mixes by the same rule and writes DIR/tune_batched.json.
 """
 from __future__ import annotations
 
@@ -177,6 +181,78 @@ def tune(classes, n_classes=(0, 1, 2), reps: int = 5, margin: float = 0.01, log=
     return record
 
 
+BATCH_WORKLOADS = (
+    # (segments, n_lo, n_hi, r_lo, r_hi, seed)
+    (4096, 1e3, 1e6, 2 ** 7, 2 ** 16, 1),
+    (4096, 1e3, 1e6, 2 ** 7, 2 ** 16, 2),
+    (16384, 1e2, 1e4, 2 ** 4, 2 ** 12, 3),
+    (512, 1e4, 1e7, 2 ** 10, 2 ** 18, 4),
+)
+BATCH_HIST_CHUNKS = (65536, 131072, 262144, 524288)
+BATCH_FILL_CHUNKS = (16384, 32768, 65536, 131072)
+BATCH_SMALL_MAX = (16384, 65535)
+
+
+def tune_batched(reps: int = 5, margin: float = 0.01, log=print) -> dict:
+    """Work-item sizes of the segmented sort, by the same geometric-mean rule
+    over several segment-shape mixes (candidate 0 is the built-in choice)."""
+    import numpy as np
+    import torch
+
+    from . import _build, gen, rtcdf
+    _build.build()
+    stream = torch.cuda.Stream()
+    sh = stream.cuda_stream
+    cands = [rtcdf.BatchParams()]
+    for hc in BATCH_HIST_CHUNKS:
+        for fc in BATCH_FILL_CHUNKS:
+            for sm in BATCH_SMALL_MAX:
+                cands.append(rtcdf.BatchParams(hist_chunk=hc, fill_chunk=fc, small_max_n=sm))
+    times = []
+    for (S, n_lo, n_hi, r_lo, r_hi, sd) in BATCH_WORKLOADS:
+        L, mn, R, dist, seeds = gen.batched_segments(gen.derive_seed(12, sd), S, n_lo=n_lo,
+                                                     n_hi=n_hi, r_lo=r_lo, r_hi=r_hi)
+        offs = np.zeros(S + 1, dtype=np.int64)
+        offs[1:] = np.cumsum(L)
+        x = torch.empty(int(offs[-1]), dtype=torch.int32, device="cuda")
+        out = torch.empty_like(x)
+        for i in range(S):
+            gen.keys_device(x.data_ptr() + 4 * int(offs[i]), int(L[i]), int(mn[i]), int(R[i]),
+                            int(dist[i]), int(seeds[i]), stream=sh)
+        row = []
+        for p in cands:
+            plan = rtcdf.BatchPlan(offs, mn, mn + R, p)
+            wsb = max(256, plan.workspace_size())
+            ws = torch.zeros(wsb // 4 + 64, dtype=torch.int32, device="cuda")
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+            plan.run(x.data_ptr(), out.data_ptr(), ws.data_ptr(), wsb, sh)
+            ev[0].record(stream)
+            for r in range(reps):
+                rc = plan.run(x.data_ptr(), out.data_ptr(), ws.data_ptr(), wsb, sh)
+                if rc != rtcdf.OK:
+                    raise rtcdf.RtcdfError(rc, "rtcdf_sort_batched_ws")
+                ev[r + 1].record(stream)
+            stream.synchronize()
+            rc, bits = rtcdf.rtcdf_batch_status_get(ws.data_ptr(), sh)
+            if rc != rtcdf.OK:
+                raise rtcdf.RtcdfError(rc, "batched device status")
+            ts = sorted(ev[r].elapsed_time(ev[r + 1]) for r in range(reps))
+            row.append(ts[reps // 2])
+            plan.close()
+            del ws
+        times.append(row)
+        log(f"workload {S} segs n[{n_lo:g},{n_hi:g}] R[{r_lo},{r_hi}]: rule {row[0]:.3f} ms, "
+            f"best {min(row):.3f} ms")
+        del x, out
+    gm = _geomean(times)
+    k = _pick(gm, margin)
+    fields = ("hist_chunk", "fill_chunk", "small_max_n")
+    return {"workloads": [list(w) for w in BATCH_WORKLOADS],
+            "candidates": [{f: getattr(p, f) for f in fields} for p in cands],
+            "times_ms": times, "geomean": gm, "chosen": k,
+            "chosen_params": {f: getattr(cands[k], f) for f in fields}}
+
+
 def _geomean(times):
     """Section 4.1's rule over a [condition][candidate] table (-1 = cannot run)."""
     import math
@@ -213,14 +289,23 @@ def main():
     ap.add_argument("--log2r", default="1-24", help="range classes, e.g. 1-24 or 7,10,14,18")
     ap.add_argument("--n-classes", default="0,1,2")
     ap.add_argument("--reps", type=int, default=5)
+    ap.add_argument("--batched", action="store_true",
+                    help="tune the segmented sort's work-item sizes instead")
     args = ap.parse_args()
+    os.makedirs(args.out, exist_ok=True)
+    if args.batched:
+        rec = tune_batched(args.reps)
+        with open(os.path.join(args.out, "tune_batched.json"), "w") as f:
+            json.dump(rec, f, indent=1)
+        print("chosen:", rec["chosen_params"], "geomean", rec["geomean"][rec["chosen"]],
+              "rule geomean", rec["geomean"][0])
+        return
     if "-" in args.log2r:
         a, b = args.log2r.split("-")
         classes = list(range(int(a), int(b) + 1))
     else:
         classes = [int(x) for x in args.log2r.split(",")]
     ncl = [int(x) for x in args.n_classes.split(",")]
-    os.makedirs(args.out, exist_ok=True)
     rec = tune(classes, ncl, args.reps)
     with open(os.path.join(args.out, "tune_table.json"), "w") as f:
         json.dump(rec, f, indent=1)

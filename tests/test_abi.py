@@ -107,3 +107,18 @@ def test_batched_plan_rejects_bad_metadata_on_host():
     assert create([0, 10], [0], [(1 << 20) + 1]) == rtcdf.ERR_RANGE          # R too wide
     assert create([0, 10], [-(1 << 31) - 1], [0]) == rtcdf.ERR_RANGE         # outside int32
     assert lib.rtcdf_batch_plan_create(None, None, None, -1, ctypes.byref(h)) == rtcdf.ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("field,value", [("hist_chunk", 100), ("hist_chunk", -1), ("fill_chunk", 4095),
+                                         ("small_max_n", 65536), ("small_max_n", -2)])
+def test_batched_plan_rejects_bad_work_item_sizes_on_host(field, value):
+    import ctypes
+    import numpy as np
+    o = np.asarray([0, 10], np.int64); a = np.asarray([0], np.int64); b = np.asarray([4], np.int64)
+    p = rtcdf.BatchParams(**{field: value})
+    h = ctypes.c_void_p(0)
+    rc = rtcdf.lib().rtcdf_batch_plan_create_ex(o.ctypes.data_as(ctypes.c_void_p),
+                                                a.ctypes.data_as(ctypes.c_void_p),
+                                                b.ctypes.data_as(ctypes.c_void_p), 1, ctypes.byref(p),
+                                                ctypes.byref(h))
+    assert rc == rtcdf.ERR_INVALID_ARG and not h.value

@@ -44,8 +44,8 @@ def check_segments(x, out, offs, mins, maxs):
                                  f"positions differ, first {bad[:5].tolist()}")
 
 
-def run_plan(x, out, offs, mins, maxs):
-    plan = rtcdf.BatchPlan(offs, mins, maxs)
+def run_plan(x, out, offs, mins, maxs, params=None):
+    plan = rtcdf.BatchPlan(offs, mins, maxs, params)
     wsb = max(256, plan.workspace_size())
     ws = torch.zeros(wsb // 4 + 64, dtype=torch.int32, device="cuda")
     s = stream_handle()
@@ -133,3 +133,22 @@ def test_out_of_range_key_in_one_segment_reports_status():
         out = torch.empty_like(x)
         _, _, _, rc, bits = run_plan(x, out, offs, mn, mx)
         assert rc == rtcdf.ERR_KEY_OUT_OF_RANGE and bits & rtcdf.DEV_KEY_OUT_OF_RANGE
+
+
+@pytest.mark.parametrize("hist_chunk,fill_chunk,small_max_n", [
+    (4096, 4096, 1),            # every segment large, many tiny items
+    (4100, 65536, 20000),       # chunk boundaries off the 16-byte grid
+    (1 << 20, 1 << 18, 65535),  # few large items
+])
+def test_work_item_sizes_change_nothing_but_the_schedule(hist_chunk, fill_chunk, small_max_n):
+    L, mn, R, dist, seeds = gen.batched_segments(gen.derive_seed(70), 48, n_lo=1, n_hi=3e5,
+                                                 r_hi=2 ** 17)
+    x, offs, mins, maxs = make_segments(L, R, mn, dist, seeds, pad_front=3)
+    out = torch.full_like(x, 12345)
+    p = rtcdf.BatchParams(hist_chunk=hist_chunk, fill_chunk=fill_chunk, small_max_n=small_max_n)
+    plan, ws, wsb, rc, bits = run_plan(x, out, offs, mins, maxs, p)
+    assert rc == rtcdf.OK and bits == 0
+    info = plan.info()
+    if small_max_n == 1:
+        assert info["small_segments"] <= sum(1 for n in L if n <= 1)
+    check_segments(x, out, offs, mins, maxs)
