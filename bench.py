@@ -540,9 +540,8 @@ def main():
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2609_00843_gb300 import dist as rdist
+    rank, world, local_rank = rdist.rank_env()
 
     if args.impl == "reference":
         return run_reference(args, rank, world)
@@ -551,12 +550,8 @@ def main():
     torch.cuda.set_device(local_rank)
     dist_on = world > 1
     if dist_on:
-        import torch.distributed as tdist
-        tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-
-    def barrier():
-        if dist_on:
-            torch.distributed.barrier()
+        rdist.init("nccl", torch.device("cuda", local_rank))
+    barrier = rdist.barrier
 
     from paper_2609_00843_gb300 import _build
     if rank == 0 or not dist_on:
@@ -577,7 +572,7 @@ def main():
     with torch.cuda.stream(stream):
         for c in cases:
             x = torch.empty(n, dtype=torch.int32, device="cuda")
-            seed = gen.derive_seed(c["seed"], rank) if rank else c["seed"]
+            seed = rdist.rank_seed(c["seed"], rank)
             gen.keys_device(x.data_ptr(), n, MIN_SWEEP, c["R"], c["dist"], seed, stream=sh)
             ins.append(x)
             outs.append(torch.empty(n, dtype=torch.int32, device="cuda"))
@@ -669,10 +664,7 @@ def main():
     torch.cuda.synchronize()
     time.sleep(0.1)
     clocks = sampler.stop()
-    if dist_on:
-        tt = torch.tensor([total_ms], device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        total_ms = float(tt.item())
+    total_ms = rdist.max_over_ranks(total_ms, device="cuda")
     rc, bits = rtcdf.rtcdf_ws_status_get(ws.data_ptr(), sh)
     if rc != rtcdf.OK:
         raise rtcdf.RtcdfError(rc, "device status after timed region")
@@ -686,8 +678,7 @@ def main():
                 stage_ms[i][j] += e[j].elapsed_time(e[j + 1])
             per_case_ms[i] += e[0].elapsed_time(e[3])
     sort_ms = total_ms / nsteps  # whole step, max over ranks
-    keys_per_step = n * len(cases) * world
-    value = keys_per_step / (sort_ms * 1e-3) / 1e9
+    value = rdist.job_throughput(n * len(cases), world, sort_ms) / 1e9
 
     hbm, peak_kind = peaks()
     per_config = []
@@ -784,7 +775,7 @@ def main():
             e2e_step()
         a1.record(stream)
         stream.synchronize()
-        e_ms = a0.elapsed_time(a1) / args.e2e_steps
+        e_ms = rdist.max_over_ranks(a0.elapsed_time(a1) / args.e2e_steps, device="cuda")
         line["e2e"] = {"value": round(n * len(cases) * world / (e_ms * 1e-3) / 1e9, 3),
                        "unit": "GKeys/s", "h2d_bytes_per_step": 4 * n * len(cases),
                        "d2h_bytes_per_step": 4 * n * len(cases), "ms_per_step": round(e_ms, 3)}
@@ -802,8 +793,7 @@ def main():
 
     if rank == 0:
         print(json.dumps(line), flush=True)
-    if dist_on:
-        torch.distributed.destroy_process_group()
+    rdist.finish()
     return 0
 
 

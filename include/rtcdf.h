@@ -305,7 +305,7 @@ rtcdf_status rtcdf_sort_batched(const int32_t *in, int32_t *out, const int64_t *
  * are launched as soon as one of `num_streams` streams is free -- a request of
  * at least `single_min_keys` keys alone through the single-array pipeline, all
  * other pending requests together in one segmented launch (at most
- * `max_batch`).  Arrivals keep being admitted while launches run, and a
+ * `max_batch`; a lone pending request takes the single-array pipeline).  Arrivals keep being admitted while launches run, and a
  * request's memory is released when its launch completes.  With `digests`
  * set, each result carries an order-dependent 64-bit digest of its sorted
  * output (sum over positions i of SplitMix64's finaliser applied to
