@@ -456,7 +456,7 @@ def batched_comparison(args, stream, num_segments=4096):
     return res
 
 
-def serving_comparison(count: int, budget_gb: float = 32.0):
+def serving_comparison(count: int, budget_gb: float = 32.0, max_large: int = 0):
     """Serving workload: a Poisson stream of sort requests, n log-uniform in
     [1e4, 1e8], R log-uniform in [2^7, 2^18], mixed shapes, 32 GB admission
     budget.  The arrival rate is rho x the throughput of sequential
@@ -473,7 +473,8 @@ def serving_comparison(count: int, budget_gb: float = 32.0):
 
     def cfg():
         return rtcdf.ServerConfig(budget_bytes=int(budget_gb * (1 << 30)), num_streams=4,
-                                  max_batch=256, single_min_keys=1 << 22, fill=fill, digests=0)
+                                  max_batch=256, single_min_keys=1 << 22, fill=fill, digests=0,
+                                  max_large_inflight=max_large)
     zero = np.zeros(count)
     r0 = rtcdf.make_requests(n, mn, mx, dist, seeds, zero)
     _, st0 = rtcdf.rtcdf_serve_sequential(cfg(), r0, count)

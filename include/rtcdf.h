@@ -274,7 +274,7 @@ rtcdf_status rtcdf_batch_plan_create(const int64_t *seg_offsets, const int64_t *
                                      rtcdf_batch_plan **plan);
 /* Work-item sizes of a segmented sort (zero = built-in choice). */
 typedef struct {
-    int32_t hist_chunk;   /* keys per histogram item of a large segment (>= 4096; default 131072) */
+    int32_t hist_chunk;   /* keys per histogram item of a large segment (>= 4096; default 524288) */
     int32_t fill_chunk;   /* output positions per output item (>= 4096; default 65536) */
     int32_t small_max_n;  /* longest segment sorted inside one CTA (<= 65535; default 65535) */
     int32_t reserved[5];
@@ -324,7 +324,11 @@ typedef struct {
     uint64_t single_min_keys;   /* requests this large run alone */
     rtcdf_fill_fn fill;
     int32_t digests;            /* nonzero: compute result digests */
-    int32_t reserved;
+    int32_t max_large_inflight; /* launches of requests with at least single_min_keys
+                                   keys in flight at once (0 = num_streams): large
+                                   sorts are bandwidth-bound, so running them one
+                                   after another keeps their latency while small
+                                   batches still overlap them */
 } rtcdf_server_config;
 
 typedef struct {

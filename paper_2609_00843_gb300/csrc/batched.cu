@@ -156,6 +156,16 @@ __device__ void do_small(const BatchArgs &a, const BatchSeg &g, uint32_t *sm) {
 }
 
 // ---------------------------------------------------------------- HIST
+// S[y] += 1 when y < w: a predicated shared-memory reduction (as in the
+// single-array histogram kernel).
+__device__ __forceinline__ void count_key_pred(uint32_t s_base, uint32_t y, uint32_t w) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "setp.lt.u32 p, %0, %1;\n\t"
+        "@p red.shared.add.u32 [%2], 1;\n\t}"
+        ::"r"(y), "r"(w), "r"(s_base + 4u * y));
+}
+
 __device__ void do_hist(const BatchArgs &a, const BatchSeg &g, const BatchItem &it, uint32_t *S) {
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
     const uint32_t b = it.tile * g.T;
@@ -170,12 +180,12 @@ __device__ void do_hist(const BatchArgs &a, const BatchSeg &g, const BatchItem &
     const uint64_t lead = lead_a < k1 - k0 ? lead_a : k1 - k0;
     const uint64_t nv = (k1 - k0 - lead) / 4;
     const int4 *vin = reinterpret_cast<const int4 *>(in + k0 + lead);
+    const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(S);
     auto count4 = [&](const int4 k) {
-        uint32_t y;
-        y = (uint32_t)k.x - base; if (y < w) atomicAdd(&S[y], 1u);
-        y = (uint32_t)k.y - base; if (y < w) atomicAdd(&S[y], 1u);
-        y = (uint32_t)k.z - base; if (y < w) atomicAdd(&S[y], 1u);
-        y = (uint32_t)k.w - base; if (y < w) atomicAdd(&S[y], 1u);
+        count_key_pred(s_base, (uint32_t)k.x - base, w);
+        count_key_pred(s_base, (uint32_t)k.y - base, w);
+        count_key_pred(s_base, (uint32_t)k.z - base, w);
+        count_key_pred(s_base, (uint32_t)k.w - base, w);
     };
     uint64_t v = tid;
     for (; v + 7 * nt < nv; v += 8 * nt) {
@@ -306,8 +316,13 @@ __device__ void do_fill(const BatchArgs &a, const BatchSeg &g, const BatchItem &
     const uint32_t *run_end = a.ws_u32 + g.run_end_off;
     const int32_t *run_val = reinterpret_cast<const int32_t *>(a.ws_u32 + g.run_val_off);
     uint32_t k_cur = a.ws_u32[g.start_run_off + it.aux];
+    // Last run this item can need: the one holding the next item's first position.
+    const uint32_t k_last = (it.aux + 1 < g.fill_items)
+                                ? min(a.ws_u32[g.start_run_off + it.aux + 1], D - 1) : D - 1;
+    // A window of up to four runs per thread (few rounds where runs are short).
+    const uint32_t RW = 4 * nt;
     uint32_t *s_end = sm;
-    int32_t *s_val = reinterpret_cast<int32_t *>(sm + nt);
+    int32_t *s_val = reinterpret_cast<int32_t *>(sm + RW);
     int32_t *out = a.out + g.out_off;
     // Positions relative to the segment; vectors aligned to the global `out`.
     const uint32_t head = (uint32_t)(((16 - ((uintptr_t)out & 15)) & 15) / 4);
@@ -315,11 +330,11 @@ __device__ void do_fill(const BatchArgs &a, const BatchSeg &g, const BatchItem &
     uint32_t pos = (uint32_t)it.a;
     const uint32_t P1 = (uint32_t)it.b;
     while (pos < P1 && k_cur < D) {
-        const uint32_t nw = min(nt, D - k_cur);
+        const uint32_t nw = min(RW, (k_last >= k_cur ? k_last - k_cur : 0u) + 1u);
         __syncthreads();
-        if (tid < nw) {
-            s_end[tid] = run_end[k_cur + tid];
-            s_val[tid] = run_val[k_cur + tid];
+        for (uint32_t i = tid; i < nw; i += nt) {
+            s_end[i] = run_end[k_cur + i];
+            s_val[i] = run_val[k_cur + i];
         }
         __syncthreads();
         const uint32_t hi = min(P1, s_end[nw - 1]);
@@ -367,15 +382,21 @@ __device__ void do_fill(const BatchArgs &a, const BatchSeg &g, const BatchItem &
 
 }  // namespace
 
+// Each worker holds its current item and, taken while the current one runs,
+// the index of its next (so the queue's atomic round trip is off the critical
+// path).  Holding one item ahead cannot deadlock: the unfinished item with the
+// lowest queue index is always some worker's current item (a held-ahead item
+// has a lower-index current item in front of it), and everything it waits on
+// has a lower index, hence has finished.
 __global__ void __launch_bounds__(kBatchThreads, kBatchWorkersPerSM) batched_kernel(BatchArgs a) {
     extern __shared__ uint32_t sm[];
     __shared__ uint32_t s_item;
-    for (;;) {
-        __syncthreads();
-        if (threadIdx.x == 0) s_item = atomicAdd(&a.ctl->queue_head, 1u);
-        __syncthreads();
-        const uint32_t i = s_item;
-        if (i >= a.num_items) break;
+    if (threadIdx.x == 0) s_item = atomicAdd(&a.ctl->queue_head, 1u);
+    __syncthreads();
+    uint32_t i = s_item;
+    while (i < a.num_items) {
+        uint32_t next = 0;
+        if (threadIdx.x == 0) next = atomicAdd(&a.ctl->queue_head, 1u);
         const BatchItem it = a.items[i];
         const BatchSeg g = a.segs[it.seg];
         switch (it.kind) {
@@ -384,6 +405,10 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchWorkersPerSM) batched_ker
             case kItemScan: do_scan(a, g, it, sm); break;
             default: do_fill(a, g, it, sm); break;
         }
+        __syncthreads();  // every thread is done with this item and with s_item
+        if (threadIdx.x == 0) s_item = next;
+        __syncthreads();
+        i = s_item;
     }
     // The last worker out resets the queue and the per-segment counters.
     __syncthreads();

@@ -81,7 +81,7 @@ struct HostPlan {
 // returns RTCDF-style codes (0 ok, 1 invalid argument, 2 range).
 // Work-item sizes of a plan (rtcdf_batch_params with the defaults filled in).
 struct BatchTuning {
-    uint64_t hist_chunk = 1ull << 17;   // keys per HIST item
+    uint64_t hist_chunk = 1ull << 19;   // keys per HIST item (tuned on GB300)
     uint32_t fill_chunk = 1u << 16;     // positions per FILL item
     uint32_t small_max_n = kBatchSmallMaxN;
 };

@@ -103,6 +103,7 @@ struct Launch {
     std::vector<int64_t> reqs;
     size_t ws_off = 0, ws_bytes = 0;  // batch workspace + tables in the slab
     bool batched = false;
+    bool large = false;   // a request of at least single_min_keys keys
 };
 
 double secs(Clock::time_point t0) {
@@ -181,6 +182,8 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
     rtcdf_status err = RTCDF_OK;
     const size_t reserve = std::min<size_t>(cfg->budget_bytes / 8, (size_t)1 << 30);
     int batch_cap = cfg->max_batch;
+    const int max_large = cfg->max_large_inflight > 0 ? cfg->max_large_inflight : K;
+    int large_inflight = 0;
     const Clock::time_point t0 = Clock::now();
 
     while (done < count && !err) {
@@ -230,11 +233,13 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
                 cudaStreamWaitEvent(s, fill_evs[f], 0);
             Launch L;
             L.stream = k;
-            // A large request alone, or every small pending request together.
+            // A large request alone (while fewer than max_large of them run),
+            // or every small pending request together.
             const int64_t head = pending.front();
-            if (reqs[head].n >= cfg->single_min_keys) {
+            if (reqs[head].n >= cfg->single_min_keys && large_inflight < max_large) {
                 pending.pop_front();
                 L.reqs.push_back(head);
+                L.large = true;
             } else {
                 for (auto it = pending.begin(); it != pending.end() && (int)L.reqs.size() < batch_cap;) {
                     if (reqs[*it].n < cfg->single_min_keys) {
@@ -244,6 +249,7 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
                         ++it;
                     }
                 }
+                if (L.reqs.empty()) break;  // only large requests wait: a large launch must finish
             }
             const double launch_t = secs(t0);
             // A lone request (large, or small with nothing to batch it with --
@@ -343,6 +349,7 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
             cudaEventRecord(L.done, s);
             for (int64_t i : L.reqs) results[i].launch_s = launch_t, results[i].batch_id = (int32_t)(launches_batched + launches_single);
             stream_busy[k] = true;
+            if (L.large) large_inflight++;
             inflight.push_back(std::move(L));
             if ((int)inflight.size() > max_inflight) max_inflight = (int)inflight.size();
             progressed = true;
@@ -359,6 +366,7 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
                     done++;
                 }
                 if (L.ws_bytes) alloc.release(L.ws_off, L.ws_bytes);
+                if (L.large) large_inflight--;
                 stream_busy[L.stream] = false;
                 cudaEventDestroy(L.done);
                 inflight.erase(inflight.begin() + j);

@@ -24,10 +24,10 @@ def trace(count, seed, n_hi=3e6, rate=20000.0, r_hi=2 ** 18):
     return n, mn, R, dist, seeds, arr
 
 
-def config(budget, digests=True, streams=4, max_batch=64, single_min=1 << 21):
+def config(budget, digests=True, streams=4, max_batch=64, single_min=1 << 21, max_large=0):
     return rtcdf.ServerConfig(budget_bytes=budget, num_streams=streams, max_batch=max_batch,
                               single_min_keys=single_min, fill=gen.fill_function_address(),
-                              digests=1 if digests else 0)
+                              digests=1 if digests else 0, max_large_inflight=max_large)
 
 
 def oracle_digest(n, mn, R, dist, seed):
@@ -84,3 +84,14 @@ def test_request_larger_than_budget_is_refused_others_served():
     for i in (0, 2):
         assert res[i].status == 0
         assert res[i].digest == oracle_digest(n[i], mn[i], R[i], [0, 0, 1][i], [1, 2, 3][i])
+
+
+def test_one_large_launch_at_a_time_still_matches():
+    count = 200
+    n, mn, R, dist, seeds, arr = trace(count, gen.derive_seed(53), n_hi=8e6, rate=5e4)
+    reqs = rtcdf.make_requests(n, mn, mn + R, dist, seeds, arr)
+    res, st = rtcdf.rtcdf_serve_trace(config(2 << 30, max_large=1), reqs, count)
+    alone, _ = rtcdf.rtcdf_serve_sequential(config(2 << 30), reqs, count)
+    assert st.launches_single > 0
+    for i in range(count):
+        assert res[i].status == 0 and res[i].digest == alone[i].digest, i
