@@ -435,7 +435,18 @@ def batched_comparison(args, stream, num_segments=4096):
         looped()
     ms_looped_graph = timed(g2.replay, steps)
     same = same and bool(torch.equal(out, ref))
+    # One instrumented launch: where the persistent kernel spends its time.
+    import torch as _t
+    prof = _t.zeros(rtcdf.BATCH_PROFILE_WORDS, dtype=_t.int64, device="cuda")
+    prof[8:12] = -1  # UINT64_MAX: earliest-start slots
+    with _t.cuda.stream(stream):
+        rc = plan.run_profiled(x.data_ptr(), out.data_ptr(), ws.data_ptr(), wsb, prof.data_ptr(), sh)
+    stream.synchronize()
+    if rc != rtcdf.OK:
+        raise rtcdf.RtcdfError(rc, "rtcdf_sort_batched_profiled")
+    words = [int(v) & ((1 << 64) - 1) for v in prof.cpu().tolist()]
     info = plan.info()
+    phases = rtcdf.batch_profile_summary(words, info["workers"])
     plan.close()
     res = {
         "workload": f"{num_segments} segments: n log-uniform [1e3,1e6], R log-uniform [2^7,2^16], "
@@ -449,7 +460,7 @@ def batched_comparison(args, stream, num_segments=4096):
         "looped_ms": round(ms_looped, 4), "looped_graph_ms": round(ms_looped_graph, 4),
         "speedup_vs_looped_graph": round(ms_looped_graph / ms_batched_graph, 2),
         "frac_8n_roofline": round(8 * total / (ms_batched_graph * 1e-3) / 1e9 / peaks()[0], 4),
-        "outputs_equal": same, "plan": info,
+        "outputs_equal": same, "plan": info, "phases": phases,
     }
     del x, out, ws, ref
     torch.cuda.empty_cache()

@@ -292,6 +292,25 @@ rtcdf_status rtcdf_sort_batched_ws(const rtcdf_batch_plan *plan, const int32_t *
                                    void *workspace, size_t ws_bytes, rtcdf_stream_t stream);
 rtcdf_status rtcdf_batch_status_get(void *workspace, rtcdf_stream_t stream,
                                     int32_t *device_status);
+
+/*
+ * rtcdf_sort_batched_profiled -- rtcdf_sort_batched_ws that also records where
+ * the persistent launch spends its time, per work-item kind k (0 histogram,
+ * 1 in-CTA segment, 2 segment scan, 3 output): `profile` is a device array of
+ * RTCDF_BATCH_PROFILE_WORDS uint64, initialised by the caller to zero except
+ * words 8..11, initialised to UINT64_MAX; afterwards
+ *   profile[k]      sum over items of their duration (ns, all workers)
+ *   profile[4 + k]  items processed
+ *   profile[8 + k]  earliest item start   (device global timer, ns)
+ *   profile[12 + k] latest item end       (device global timer, ns)
+ *   profile[16 + k] ns spent waiting for other items (scan: histograms,
+ *                   output: the segment's scan), included in profile[k].
+ * The instrumentation adds a few timer reads and atomics per item.
+ */
+#define RTCDF_BATCH_PROFILE_WORDS 20
+rtcdf_status rtcdf_sort_batched_profiled(const rtcdf_batch_plan *plan, const int32_t *in,
+                                         int32_t *out, void *workspace, size_t ws_bytes,
+                                         uint64_t *profile, rtcdf_stream_t stream);
 rtcdf_status rtcdf_sort_batched(const int32_t *in, int32_t *out, const int64_t *seg_offsets,
                                 const int64_t *seg_minVal, const int64_t *seg_maxVal,
                                 int32_t num_segments, rtcdf_stream_t stream);

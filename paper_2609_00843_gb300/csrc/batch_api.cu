@@ -215,6 +215,13 @@ rtcdf_status rtcdf_batch_plan_info(const rtcdf_batch_plan *plan, rtcdf_batch_inf
 
 rtcdf_status rtcdf_sort_batched_ws(const rtcdf_batch_plan *plan, const int32_t *in, int32_t *out,
                                    void *workspace, size_t ws_bytes, rtcdf_stream_t stream) {
+    return rtcdf_sort_batched_profiled(plan, in, out, workspace, ws_bytes, nullptr, stream);
+}
+
+rtcdf_status rtcdf_sort_batched_profiled(const rtcdf_batch_plan *plan, const int32_t *in,
+                                         int32_t *out, void *workspace, size_t ws_bytes,
+                                         uint64_t *profile, rtcdf_stream_t stream) {
+    if (profile && ((uintptr_t)profile & 7)) return RTCDF_ERR_INVALID_ARG;
     if (!plan) return RTCDF_ERR_INVALID_ARG;
     if (plan->num_items == 0) return RTCDF_OK;
     if (!in || !out || !workspace) return RTCDF_ERR_INVALID_ARG;
@@ -239,6 +246,7 @@ rtcdf_status rtcdf_sort_batched_ws(const rtcdf_batch_plan *plan, const int32_t *
     a.ws_u32 = ws;
     a.ctl = (BatchCtl *)(ws + plan->ctl_off);
     a.seg_ctl = (BatchSegCtl *)(ws + plan->segctl_off);
+    a.prof = reinterpret_cast<unsigned long long *>(profile);
     if (launch_batched(a, plan->workers, (cudaStream_t)stream) != cudaSuccess) return RTCDF_ERR_CUDA;
     return RTCDF_OK;
 }

@@ -33,9 +33,18 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
     return v;
 }
 
-// Wait (bounded) until *p >= target; thread 0 waits, the CTA follows.
-__device__ void wait_at_least(const uint32_t *p, uint32_t target, uint32_t *status) {
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Wait (bounded) until *p >= target; thread 0 waits, the CTA follows.  With a
+// profile buffer, the time spent waiting is added to wait_ns.
+__device__ void wait_at_least(const uint32_t *p, uint32_t target, uint32_t *status,
+                              unsigned long long *wait_ns) {
     if (threadIdx.x == 0) {
+        const unsigned long long t0 = wait_ns ? global_ns() : 0ull;
         uint32_t spins = 0;
         int ok = 1;
         while (ld_acquire_u32(p) < target) {
@@ -43,6 +52,7 @@ __device__ void wait_at_least(const uint32_t *p, uint32_t target, uint32_t *stat
             __nanosleep(128);
         }
         if (!ok) atomicOr(status, kDevTimeout);
+        if (wait_ns) atomicAdd(wait_ns, global_ns() - t0);
     }
     __syncthreads();
 }
@@ -219,7 +229,8 @@ __device__ void do_hist(const BatchArgs &a, const BatchSeg &g, const BatchItem &
 __device__ void do_scan(const BatchArgs &a, const BatchSeg &g, const BatchItem &it, uint32_t *sm) {
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
     BatchSegCtl &sc = a.seg_ctl[it.seg];
-    wait_at_least(&sc.hist_done, g.hist_items, &a.ctl->status);
+    wait_at_least(&sc.hist_done, g.hist_items, &a.ctl->status,
+                  a.prof ? a.prof + 16 + kItemScan : nullptr);
     uint32_t *H = a.ws_u32 + g.hist_off;
     uint32_t *run_end = a.ws_u32 + g.run_end_off;
     int32_t *run_val = reinterpret_cast<int32_t *>(a.ws_u32 + g.run_val_off);
@@ -311,7 +322,7 @@ __device__ __forceinline__ uint32_t first_after(const uint32_t *e, uint32_t lo, 
 __device__ void do_fill(const BatchArgs &a, const BatchSeg &g, const BatchItem &it, uint32_t *sm) {
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
     BatchSegCtl &sc = a.seg_ctl[it.seg];
-    wait_at_least(&sc.scan_done, 1u, &a.ctl->status);
+    wait_at_least(&sc.scan_done, 1u, &a.ctl->status, a.prof ? a.prof + 16 + kItemFill : nullptr);
     const uint32_t D = *(volatile uint32_t *)&sc.num_runs;
     const uint32_t *run_end = a.ws_u32 + g.run_end_off;
     const int32_t *run_val = reinterpret_cast<const int32_t *>(a.ws_u32 + g.run_val_off);
@@ -399,6 +410,7 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchWorkersPerSM) batched_ker
         if (threadIdx.x == 0) next = atomicAdd(&a.ctl->queue_head, 1u);
         const BatchItem it = a.items[i];
         const BatchSeg g = a.segs[it.seg];
+        const unsigned long long t_start = (a.prof && threadIdx.x == 0) ? global_ns() : 0ull;
         switch (it.kind) {
             case kItemSmall: do_small(a, g, sm); break;
             case kItemHist: do_hist(a, g, it, sm); break;
@@ -406,6 +418,14 @@ __global__ void __launch_bounds__(kBatchThreads, kBatchWorkersPerSM) batched_ker
             default: do_fill(a, g, it, sm); break;
         }
         __syncthreads();  // every thread is done with this item and with s_item
+        if (a.prof && threadIdx.x == 0) {
+            const unsigned long long t_end = global_ns();
+            const uint32_t k = it.kind & 3u;
+            atomicAdd(a.prof + k, t_end - t_start);
+            atomicAdd(a.prof + 4 + k, 1ull);
+            atomicMin(a.prof + 8 + k, t_start);
+            atomicMax(a.prof + 12 + k, t_end);
+        }
         if (threadIdx.x == 0) s_item = next;
         __syncthreads();
         i = s_item;

@@ -60,6 +60,9 @@ struct BatchArgs {
     uint32_t *ws_u32;       // workspace base
     BatchCtl *ctl;
     BatchSegCtl *seg_ctl;
+    // Optional phase profile (device, RTCDF_BATCH_PROFILE_WORDS u64), or null:
+    // per item kind busy ns, items, first start, last end, dependency-wait ns.
+    unsigned long long *prof = nullptr;
 };
 
 cudaError_t launch_batched(const BatchArgs &a, int workers, cudaStream_t s);

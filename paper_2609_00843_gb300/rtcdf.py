@@ -138,6 +138,8 @@ def lib():
             L.rtcdf_batch_plan_info.argtypes = [vp, ctypes.POINTER(BatchInfo)]
             L.rtcdf_sort_batched_ws.argtypes = [vp, vp, vp, vp, sz, vp]
             L.rtcdf_batch_status_get.argtypes = [vp, vp, ctypes.POINTER(i32)]
+            L.rtcdf_sort_batched_profiled.argtypes = [vp, vp, vp, vp, sz, vp, vp]
+            L.rtcdf_sort_batched_profiled.restype = ctypes.c_int
             L.rtcdf_sort_batched.argtypes = [vp, vp, vp, vp, vp, i32, vp]
             L.rtcdf_tune_n_class.argtypes = [u64]
             L.rtcdf_tune_n_class.restype = i32
@@ -194,6 +196,26 @@ def _i64_array(xs):
     return a, a.ctypes.data_as(ctypes.c_void_p)
 
 
+BATCH_PROFILE_WORDS = 20
+BATCH_ITEM_KINDS = ("hist", "small", "scan", "fill")
+
+
+def batch_profile_summary(words, workers: int) -> dict:
+    """Turn the profile words of rtcdf_sort_batched_profiled into per-kind
+    figures: average busy ms per worker, items, span ms, wait share."""
+    t0 = min(words[8 + k] for k in range(4) if words[4 + k])
+    out = {}
+    for k, name in enumerate(BATCH_ITEM_KINDS):
+        if not words[4 + k]:
+            continue
+        out[name] = {"items": int(words[4 + k]),
+                     "busy_ms_per_worker": round(words[k] / workers / 1e6, 4),
+                     "start_ms": round((words[8 + k] - t0) / 1e6, 4),
+                     "end_ms": round((words[12 + k] - t0) / 1e6, 4),
+                     "wait_share": round(words[16 + k] / words[k], 4) if words[k] else 0.0}
+    return out
+
+
 class BatchPlan:
     """A segmented-sort plan (rtcdf_batch_plan_create / _destroy)."""
 
@@ -226,6 +248,12 @@ class BatchPlan:
 
     def run(self, in_ptr: int, out_ptr: int, ws_ptr: int, ws_bytes: int, stream: int = 0) -> int:
         return lib().rtcdf_sort_batched_ws(self.handle, in_ptr, out_ptr, ws_ptr, ws_bytes, stream)
+
+    def run_profiled(self, in_ptr: int, out_ptr: int, ws_ptr: int, ws_bytes: int,
+                     prof_ptr: int, stream: int = 0) -> int:
+        """rtcdf_sort_batched_profiled; prof_ptr: device array of PROFILE_WORDS uint64."""
+        return lib().rtcdf_sort_batched_profiled(self.handle, in_ptr, out_ptr, ws_ptr, ws_bytes,
+                                                 prof_ptr, stream)
 
     def close(self):
         if getattr(self, "handle", None):

@@ -152,3 +152,33 @@ def test_work_item_sizes_change_nothing_but_the_schedule(hist_chunk, fill_chunk,
     if small_max_n == 1:
         assert info["small_segments"] <= sum(1 for n in L if n <= 1)
     check_segments(x, out, offs, mins, maxs)
+
+
+def test_profiled_launch_counts_every_item_and_sorts_the_same():
+    L, mn, R, dist, seeds = gen.batched_segments(gen.derive_seed(71), 300, n_lo=10, n_hi=4e5)
+    x, offs, mins, maxs = make_segments(L, R, mn, dist, seeds)
+    out = torch.empty_like(x)
+    plan = rtcdf.BatchPlan(offs, mins, maxs)
+    wsb = max(256, plan.workspace_size())
+    ws = torch.zeros(wsb // 4 + 64, dtype=torch.int32, device="cuda")
+    prof = torch.zeros(rtcdf.BATCH_PROFILE_WORDS, dtype=torch.int64, device="cuda")
+    prof[8:12] = -1
+    s = stream_handle()
+    assert plan.run_profiled(x.data_ptr(), out.data_ptr(), ws.data_ptr(), wsb, prof.data_ptr(), s) == rtcdf.OK
+    rc, bits = rtcdf.rtcdf_batch_status_get(ws.data_ptr(), s)
+    assert rc == rtcdf.OK and bits == 0
+    w = [int(v) & ((1 << 64) - 1) for v in prof.cpu().tolist()]
+    info = plan.info()
+    assert sum(w[4:8]) == info["work_items"]
+    assert w[5] == info["small_segments"]
+    for k in range(4):
+        if w[4 + k]:
+            assert w[k] > 0 and w[8 + k] <= w[12 + k] and w[16 + k] <= w[k]
+    summ = rtcdf.batch_profile_summary(w, info["workers"])
+    assert set(summ) <= set(rtcdf.BATCH_ITEM_KINDS)
+    check_segments(x, out, offs, mins, maxs)
+    # and the same plan, unprofiled, replays with the counters reset
+    out2 = torch.empty_like(x)
+    assert plan.run(x.data_ptr(), out2.data_ptr(), ws.data_ptr(), wsb, s) == rtcdf.OK
+    torch.cuda.synchronize()
+    assert torch.equal(out, out2)
