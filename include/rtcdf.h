@@ -277,7 +277,10 @@ typedef struct {
     int32_t hist_chunk;   /* keys per histogram item of a large segment (>= 4096; default 524288) */
     int32_t fill_chunk;   /* output positions per output item (>= 4096; default 65536) */
     int32_t small_max_n;  /* longest segment sorted inside one CTA (<= 65535; default 65535) */
-    int32_t reserved[5];
+    int32_t schedule_lag; /* queue distance (work items) from a segment's last histogram
+                             item to its scan and from its scan to its outputs;
+                             0 = twice the workers, -1 = one phase after another */
+    int32_t reserved[4];
 } rtcdf_batch_params;
 
 /* rtcdf_batch_plan_create with explicit work-item sizes (`params` may be NULL). */

@@ -7,6 +7,8 @@
 // CUDA graph and replayed for new keys with the same segment shapes.
 #include <algorithm>
 #include <cstring>
+#include <deque>
+#include <utility>
 #include <vector>
 
 #include "../../include/rtcdf.h"
@@ -34,15 +36,21 @@ size_t words_align(size_t words) { return (words + 63) / 64 * 64; }  // 256-byte
 
 namespace rtcdf {
 
-int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P, const BatchTuning &tun) {
-    const uint64_t kHistChunk = tun.hist_chunk;
-    const uint32_t kFillChunk = tun.fill_chunk;
+// 0, or the rtcdf_status for the first segment with a bad length or range.
+int check_specs(const SegSpec *spec, uint32_t S) {
     for (uint32_t s = 0; s < S; s++) {
         if (spec[s].n >= (1ull << 32)) return 1;
         if (spec[s].minVal < INT32_MIN || spec[s].maxVal > ((int64_t)1 << 31)) return 2;
         if (spec[s].maxVal <= spec[s].minVal || spec[s].maxVal - spec[s].minVal > (int64_t)kBatchMaxR)
             return 2;
     }
+    return 0;
+}
+
+int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P, const BatchTuning &tun) {
+    const uint64_t kHistChunk = tun.hist_chunk;
+    const uint32_t kFillChunk = tun.fill_chunk;
+    if (const int rc = check_specs(spec, S)) return rc;
     P->segs.assign(S, BatchSeg{});
     P->items.clear();
     P->small_segs = P->large_segs = 0;
@@ -89,23 +97,80 @@ int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P, const BatchTun
         g.start_run_off = w; w += words_align(g.fill_items);
     }
     P->ws_words = w;
-    // Queue order: HIST (largest segments first), SMALL (largest first), SCAN,
-    // FILL -- every item a worker can wait on precedes it in the queue.
     const std::vector<BatchSeg> &segs = P->segs;
-    auto by_size = [&](const BatchItem &x, const BatchItem &y) {
-        const uint64_t cx = (uint64_t)segs[x.seg].n + segs[x.seg].R;
-        const uint64_t cy = (uint64_t)segs[y.seg].n + segs[y.seg].R;
-        return cx != cy ? cx > cy : x.seg < y.seg;
+    auto by_size = [&](uint32_t x, uint32_t y) {
+        const uint64_t cx = (uint64_t)segs[x].n + segs[x].R;
+        const uint64_t cy = (uint64_t)segs[y].n + segs[y].R;
+        return cx != cy ? cx > cy : x < y;
     };
-    std::stable_sort(hist.begin(), hist.end(), [&](const BatchItem &x, const BatchItem &y) {
-        return x.seg != y.seg ? by_size(x, y) : false;
-    });
-    std::stable_sort(small.begin(), small.end(), by_size);
-    P->items.reserve(hist.size() + small.size() + scan.size() + fill.size());
-    P->items.insert(P->items.end(), hist.begin(), hist.end());
-    P->items.insert(P->items.end(), small.begin(), small.end());
-    P->items.insert(P->items.end(), scan.begin(), scan.end());
-    P->items.insert(P->items.end(), fill.begin(), fill.end());
+    std::vector<uint32_t> large_ids, small_ids;
+    for (uint32_t s = 0; s < S; s++) {
+        if (segs[s].n == 0) continue;
+        (segs[s].m ? large_ids : small_ids).push_back(s);
+    }
+    std::stable_sort(large_ids.begin(), large_ids.end(), by_size);
+    std::stable_sort(small_ids.begin(), small_ids.end(), by_size);
+    // Items of each large segment, contiguous in the per-kind lists above.
+    std::vector<size_t> hist_at(S, 0), fill_at(S, 0);
+    for (size_t i = hist.size(); i-- > 0;) hist_at[hist[i].seg] = i;
+    for (size_t i = fill.size(); i-- > 0;) fill_at[fill[i].seg] = i;
+    std::vector<size_t> scan_at(S, 0);
+    for (size_t i = 0; i < scan.size(); i++) scan_at[scan[i].seg] = i;
+    std::vector<BatchItem> &Q = P->items;
+    Q.reserve(hist.size() + small.size() + scan.size() + fill.size());
+    auto emit_hist = [&](uint32_t s) {
+        for (uint32_t k = 0; k < segs[s].hist_items; k++) Q.push_back(hist[hist_at[s] + k]);
+    };
+    auto emit_fill = [&](uint32_t s) {
+        for (uint32_t k = 0; k < segs[s].fill_items; k++) Q.push_back(fill[fill_at[s] + k]);
+    };
+    if (tun.lag_items < 0) {
+        // Phase order: every HIST, every SMALL, every SCAN, every FILL.
+        for (uint32_t s : large_ids) emit_hist(s);
+        for (uint32_t s : small_ids) Q.push_back(BatchItem{kItemSmall, s, 0, 0, 0, 0});
+        for (uint32_t s : large_ids) Q.push_back(scan[scan_at[s]]);
+        for (uint32_t s : large_ids) emit_fill(s);
+        return 0;
+    }
+    // Pipelined order (largest segments first): a segment's SCAN is queued
+    // `lag` items after its last HIST item and its FILL items `lag` items
+    // after its SCAN, so that by the time a worker takes them the items they
+    // wait for have most likely finished; SMALL items are spread in
+    // proportion to their keys, so reads and writes stay mixed throughout.
+    // Every item still comes after all the items it waits for.
+    const size_t lag = (size_t)tun.lag_items;
+    uint64_t large_keys = 0, small_keys = 0;
+    for (uint32_t s : large_ids) large_keys += segs[s].n;
+    for (uint32_t s : small_ids) small_keys += segs[s].n;
+    std::deque<std::pair<uint32_t, size_t>> ps, pf;  // (segment, queue position)
+    size_t si = 0;
+    uint64_t large_done = 0, small_done = 0;
+    auto drain = [&](bool all) {
+        while (!ps.empty() && (all || ps.front().second + lag <= Q.size())) {
+            Q.push_back(scan[scan_at[ps.front().first]]);
+            pf.emplace_back(ps.front().first, Q.size());
+            ps.pop_front();
+        }
+        while (!pf.empty() && (all || pf.front().second + lag <= Q.size())) {
+            emit_fill(pf.front().first);
+            pf.pop_front();
+        }
+    };
+    for (uint32_t s : large_ids) {
+        emit_hist(s);
+        ps.emplace_back(s, Q.size());
+        large_done += segs[s].n;
+        // small_done / small_keys keeps up with large_done / large_keys
+        while (si < small_ids.size() &&
+               (unsigned __int128)small_done * large_keys < (unsigned __int128)large_done * small_keys) {
+            Q.push_back(BatchItem{kItemSmall, small_ids[si], 0, 0, 0, 0});
+            small_done += segs[small_ids[si]].n;
+            si++;
+        }
+        drain(false);
+    }
+    for (; si < small_ids.size(); si++) Q.push_back(BatchItem{kItemSmall, small_ids[si], 0, 0, 0, 0});
+    drain(true);
     return 0;
 }
 
@@ -134,6 +199,7 @@ rtcdf_status rtcdf_batch_plan_create_ex(const int64_t *seg_offsets, const int64_
         if (params->hist_chunk) tun.hist_chunk = (uint64_t)params->hist_chunk;
         if (params->fill_chunk) tun.fill_chunk = (uint32_t)params->fill_chunk;
         if (params->small_max_n) tun.small_max_n = (uint32_t)params->small_max_n;
+        if (params->schedule_lag < -1) return RTCDF_ERR_INVALID_ARG;
     }
     *plan_out = nullptr;
     if (num_segments > 0 && (!seg_offsets || !seg_minVal || !seg_maxVal)) return RTCDF_ERR_INVALID_ARG;
@@ -145,13 +211,16 @@ rtcdf_status rtcdf_batch_plan_create_ex(const int64_t *seg_offsets, const int64_
         spec[s] = SegSpec{(uint64_t)seg_offsets[s], (uint64_t)seg_offsets[s],
                           (uint64_t)(seg_offsets[s + 1] - seg_offsets[s]), seg_minVal[s], seg_maxVal[s]};
     }
-    HostPlan hp;
-    const int rc = build_host_plan(spec.data(), S, &hp, tun);
-    if (rc) return (rtcdf_status)rc;
+    if (const int rc = check_specs(spec.data(), S)) return (rtcdf_status)rc;
     int dev = 0, sms = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RTCDF_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return RTCDF_ERR_CUDA;
+    const int32_t lag = params ? params->schedule_lag : 0;
+    tun.lag_items = lag == 0 ? 2 * (int64_t)sms * kBatchWorkersPerSM : (int64_t)lag;
+    HostPlan hp;
+    const int rc = build_host_plan(spec.data(), S, &hp, tun);
+    if (rc) return (rtcdf_status)rc;
 
     rtcdf_batch_plan *p = new rtcdf_batch_plan();
     p->device = dev;

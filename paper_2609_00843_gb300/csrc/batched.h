@@ -87,6 +87,7 @@ struct BatchTuning {
     uint64_t hist_chunk = 1ull << 19;   // keys per HIST item (tuned on GB300)
     uint32_t fill_chunk = 1u << 16;     // positions per FILL item
     uint32_t small_max_n = kBatchSmallMaxN;
+    int64_t lag_items = -1;             // queue distance HIST -> SCAN -> FILL; < 0: phase order
 };
 
 int build_host_plan(const SegSpec *segs, uint32_t S, HostPlan *plan,

@@ -268,7 +268,9 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
                     const uint64_t in_off = slot_off[i] / 4;  // input at the slot start, output after it
                     spec[j] = SegSpec{in_off, in_off + reqs[i].n, reqs[i].n, reqs[i].minVal, reqs[i].maxVal};
                 }
-                if (build_host_plan(spec.data(), (uint32_t)spec.size(), &hp)) { err = RTCDF_ERR_RANGE; break; }
+                BatchTuning tun;
+                tun.lag_items = 2 * (int64_t)sms * kBatchWorkersPerSM;
+                if (build_host_plan(spec.data(), (uint32_t)spec.size(), &hp, tun)) { err = RTCDF_ERR_RANGE; break; }
             }
             std::vector<DigestSeg> dg;
             if (want_digest) {

@@ -1,0 +1,129 @@
+// Host-side check of the segmented-sort planner (rtcdf::build_host_plan):
+// for random segment shapes and every schedule, each work item comes after
+// the items it waits for, the items of every segment cover its keys and
+// positions exactly once, and the per-segment workspace regions are disjoint.
+// Usage: planner_check <seed> <segments>; prints "OK" or the first violation.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <random>
+#include <vector>
+
+#include "batched.h"
+
+using namespace rtcdf;
+
+static int fail(const char *what, long a, long b) {
+    std::printf("FAIL %s (%ld, %ld)\n", what, a, b);
+    return 1;
+}
+
+static int check(const std::vector<SegSpec> &spec, const BatchTuning &tun) {
+    HostPlan P;
+    if (build_host_plan(spec.data(), (uint32_t)spec.size(), &P, tun)) return fail("plan rejected", 0, 0);
+    const uint32_t S = (uint32_t)spec.size();
+    std::vector<long> last_hist(S, -1), scan_pos(S, -1), first_fill(S, 1L << 60);
+    std::vector<uint32_t> small_seen(S, 0), scans(S, 0);
+    std::vector<std::vector<std::pair<uint64_t, uint64_t>>> hist_rng(S), fill_rng(S);
+    for (size_t q = 0; q < P.items.size(); q++) {
+        const BatchItem &it = P.items[q];
+        if (it.seg >= S) return fail("segment index", (long)q, it.seg);
+        const BatchSeg &g = P.segs[it.seg];
+        switch (it.kind) {
+            case kItemHist:
+                if (scan_pos[it.seg] >= 0) return fail("hist after its scan", (long)q, it.seg);
+                last_hist[it.seg] = (long)q;
+                if (it.tile >= g.m) return fail("tile index", (long)q, it.tile);
+                hist_rng[it.seg].push_back({it.a * 1024 + it.tile, it.b});
+                break;
+            case kItemSmall: small_seen[it.seg]++; break;
+            case kItemScan:
+                scans[it.seg]++;
+                if (last_hist[it.seg] < 0) return fail("scan before any hist", (long)q, it.seg);
+                scan_pos[it.seg] = (long)q;
+                break;
+            case kItemFill:
+                if (scan_pos[it.seg] < 0) return fail("fill before its scan", (long)q, it.seg);
+                fill_rng[it.seg].push_back({it.a, it.b});
+                if (it.aux >= g.fill_items) return fail("fill index", (long)q, it.aux);
+                break;
+            default: return fail("item kind", (long)q, it.kind);
+        }
+    }
+    size_t ws_prev_end = 0;
+    for (uint32_t s = 0; s < S; s++) {
+        const BatchSeg &g = P.segs[s];
+        if (spec[s].n == 0) {
+            if (small_seen[s] || scans[s]) return fail("empty segment has items", s, 0);
+            continue;
+        }
+        const bool large = g.m > 0;
+        if (!large) {
+            if (small_seen[s] != 1) return fail("small segment not exactly once", s, small_seen[s]);
+            continue;
+        }
+        if (small_seen[s] || scans[s] != 1) return fail("large segment scans", s, scans[s]);
+        // histogram items: for each tile, key ranges tile [0, n) without overlap
+        std::vector<std::vector<std::pair<uint64_t, uint64_t>>> per_tile(g.m);
+        for (auto &r : hist_rng[s]) per_tile[r.first % 1024].push_back({r.first / 1024, r.second});
+        uint32_t nh = 0;
+        for (uint32_t t = 0; t < g.m; t++) {
+            auto &v = per_tile[t];
+            std::sort(v.begin(), v.end());
+            uint64_t at = 0;
+            for (auto &r : v) {
+                if (r.first != at || r.second <= r.first) return fail("hist key ranges", s, t);
+                at = r.second;
+            }
+            if (at != g.n) return fail("hist keys not covered", s, t);
+            nh += (uint32_t)v.size();
+        }
+        if (nh != g.hist_items) return fail("hist item count", s, nh);
+        auto &f = fill_rng[s];
+        std::sort(f.begin(), f.end());
+        uint64_t at = 0;
+        for (auto &r : f) {
+            if (r.first != at || r.second <= r.first) return fail("fill positions", s, (long)r.first);
+            at = r.second;
+        }
+        if (at != g.n || f.size() != g.fill_items) return fail("fill coverage", s, (long)at);
+        if ((uint64_t)g.T * g.m < g.R || g.T > kBatchTileMax) return fail("tiles", s, g.T);
+        // workspace regions in order, disjoint, inside ws_words
+        const size_t regs[4][2] = {{g.hist_off, (g.R + kBatchScanChunk - 1) / kBatchScanChunk * kBatchScanChunk},
+                                   {g.run_end_off, g.R}, {g.run_val_off, g.R}, {g.start_run_off, g.fill_items}};
+        for (auto &r : regs) {
+            if (r[0] < ws_prev_end) return fail("workspace overlap", s, (long)r[0]);
+            ws_prev_end = r[0] + r[1];
+        }
+        if (ws_prev_end > P.ws_words) return fail("workspace size", s, (long)ws_prev_end);
+    }
+    return 0;
+}
+
+int main(int argc, char **argv) {
+    const unsigned seed = argc > 1 ? (unsigned)atoi(argv[1]) : 1;
+    const int S = argc > 2 ? atoi(argv[2]) : 500;
+    std::mt19937_64 rng(seed);
+    std::vector<SegSpec> spec(S);
+    uint64_t off = 0;
+    for (int s = 0; s < S; s++) {
+        const double u = std::uniform_real_distribution<double>(0, 1)(rng);
+        const uint64_t n = (rng() % 7 == 0) ? 0 : (uint64_t)std::exp(u * std::log(3e6));
+        const int64_t R = 1 + (int64_t)(rng() % ((rng() % 3 == 0) ? (1u << 20) : 60000u));
+        const int64_t mn = (int64_t)(rng() % 2000000) - 1000000;
+        spec[s] = SegSpec{off, off, n, mn, mn + R};
+        off += n;
+    }
+    BatchTuning tunings[5];
+    tunings[0].lag_items = -1;
+    tunings[1].lag_items = 0;
+    tunings[2].lag_items = 608;
+    tunings[3].lag_items = 1000000;
+    tunings[4].lag_items = 7; tunings[4].hist_chunk = 4096; tunings[4].fill_chunk = 4096;
+    tunings[4].small_max_n = 100;
+    for (auto &t : tunings)
+        if (check(spec, t)) return 1;
+    std::printf("OK\n");
+    return 0;
+}
