@@ -788,9 +788,32 @@ def main():
         a1.record(stream)
         stream.synchronize()
         e_ms = rdist.max_over_ranks(a0.elapsed_time(a1) / args.e2e_steps, device="cuda")
-        line["e2e"] = {"value": round(n * len(cases) * world / (e_ms * 1e-3) / 1e9, 3),
+        e_val = n * len(cases) * world / (e_ms * 1e-3) / 1e9
+        line["e2e"] = {"value": round(e_val, 3),
                        "unit": "GKeys/s", "h2d_bytes_per_step": 4 * n * len(cases),
                        "d2h_bytes_per_step": 4 * n * len(cases), "ms_per_step": round(e_ms, 3)}
+        # The host link's bound: one array's upload and download at the same
+        # time (plain copies of the same 400 MB buffers, both directions).
+        d_tmp = torch.empty(n, dtype=torch.int32, device="cuda")
+        s_up, s_dn = torch.cuda.Stream(), torch.cuda.Stream()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        for rep in range(3):
+            torch.cuda.synchronize()
+            ev[0].record(s_up)
+            s_dn.wait_event(ev[0])
+            with torch.cuda.stream(s_up):
+                d_tmp.copy_(pin_in[0], non_blocking=True)
+            with torch.cuda.stream(s_dn):
+                pin_out[0].copy_(outs[0], non_blocking=True)
+            s_up.wait_stream(s_dn)
+            ev[1].record(s_up)
+            torch.cuda.synchronize()
+        link_ms = ev[0].elapsed_time(ev[1])
+        bound = n / (link_ms * 1e-3) / 1e9
+        line["e2e"]["link_bound_GKeys_s"] = round(bound, 2)
+        line["e2e"]["link_bidir_GBs"] = round(8 * n / (link_ms * 1e-3) / 1e9, 1)
+        line["e2e"]["frac_of_link_bound"] = round(e_val / world / bound, 4)
+        del d_tmp
         del pin_in, pin_out
 
     if rank == 0 and not args.no_cpu_baseline:

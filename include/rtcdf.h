@@ -226,13 +226,16 @@ rtcdf_status rtcdf_sort_ex(const int32_t *in, int32_t *out, uint64_t n, int64_t 
  * rtcdf_sort_host -- rtcdf_sort with HOST buffers: `in` and `out` point to
  * host memory (page-locked for the transfers to overlap anything; pageable
  * works but copies synchronously).  The keys are uploaded in 16 MB chunks on
- * a library-owned copy stream, the histogram of each chunk runs on `stream`
- * as soon as it has landed, the scan and output follow, and the result is
- * downloaded on a second copy stream, which overlaps the next call's upload.
- * Device buffers are library-owned (two sets per device and stream, used in
- * turn).  When `stream` completes, `out` holds the result; `in` must not be
- * modified before then.  Device status: rtcdf_status_get does not cover these
- * calls; keys outside [minVal, maxVal) leave `out` unspecified.
+ * a library-owned copy stream, the histogram of each chunk runs on a
+ * library-owned compute stream as soon as it has landed, the scan and output
+ * follow, and the result is downloaded on a second copy stream, which
+ * overlaps the next call's upload and histogram.  Device buffers are
+ * library-owned (two sets per device and stream, used in turn).  `in` is read
+ * as of the call (the host must have finished writing it; the upload is not
+ * ordered after earlier work on `stream`).  When `stream` completes, `out`
+ * holds the result; `in` must not be modified before then.  Device status:
+ * rtcdf_status_get does not cover these calls; keys outside [minVal, maxVal)
+ * leave `out` unspecified.
  */
 rtcdf_status rtcdf_sort_host(const int32_t *in, int32_t *out, uint64_t n, int64_t minVal,
                              int64_t maxVal, rtcdf_stream_t stream);

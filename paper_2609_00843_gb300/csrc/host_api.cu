@@ -1,13 +1,15 @@
 // rtcdf_sort_host: the sort with HOST input and output buffers.
 //
 // Keys cross to the device in chunks on a copy stream; the histogram of each
-// chunk (Algorithm 5) runs on the caller's stream as soon as the chunk has
-// landed, so the transfer and the histogram overlap.  The local-CDF scan and
-// the output generation (Algorithms 6-7) follow, and the sorted keys go back
-// on a second copy stream -- which overlaps the next call's upload, since the
-// two directions of the host link are independent.  Device buffers are owned
-// by the library: two sets per (device, stream), used alternately and guarded
-// by events, so consecutive calls on one stream pipeline without races.
+// chunk (Algorithm 5) runs on a library-owned compute stream as soon as the
+// chunk has landed, so the transfer and the histogram overlap.  The local-CDF
+// scan and the output generation (Algorithms 6-7) follow, and the sorted keys
+// go back on a second copy stream.  The caller's stream only waits for that
+// download: the next call's upload and histogram do not wait for it, so a
+// sequence of calls keeps both directions of the host link busy at once
+// (uploads of call i + 1 under the download of call i).  Device buffers are
+// owned by the library: two sets per (device, stream), used alternately and
+// guarded by events.
 #include <algorithm>
 #include <map>
 #include <mutex>
@@ -39,8 +41,9 @@ struct HostCtx {
     int next = 0;
     void *ws = nullptr;
     size_t ws_bytes = 0;
-    cudaStream_t up = nullptr, down = nullptr;
+    cudaStream_t up = nullptr, down = nullptr, comp = nullptr;
     cudaEvent_t ev_done = nullptr;   // sort finished on the compute stream
+    cudaEvent_t ev_chunk = nullptr;  // a chunk has landed (re-recorded per chunk)
 };
 
 std::mutex g_host_mu;
@@ -67,23 +70,27 @@ extern "C" rtcdf_status rtcdf_sort_host(const int32_t *h_in, int32_t *h_out, uin
     if (!c.up) {
         if (cudaStreamCreateWithFlags(&c.up, cudaStreamNonBlocking) != cudaSuccess ||
             cudaStreamCreateWithFlags(&c.down, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c.ev_done, cudaEventDisableTiming) != cudaSuccess)
+            cudaStreamCreateWithFlags(&c.comp, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c.ev_done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c.ev_chunk, cudaEventDisableTiming) != cudaSuccess)
             return RTCDF_ERR_CUDA;
         for (BufSet &b : c.set) {
             if (cudaEventCreateWithFlags(&b.in_free, cudaEventDisableTiming) != cudaSuccess ||
                 cudaEventCreateWithFlags(&b.out_free, cudaEventDisableTiming) != cudaSuccess)
                 return RTCDF_ERR_CUDA;
-            cudaEventRecord(b.in_free, s);
-            cudaEventRecord(b.out_free, s);
+            cudaEventRecord(b.in_free, c.comp);
+            cudaEventRecord(b.out_free, c.comp);
         }
     }
-    // Workspace (shared by both sets: the sorts themselves are ordered on `s`).
+    cudaStream_t cs = c.comp;
+    // Workspace (shared by both sets: the sorts themselves are ordered on the
+    // compute stream).
     const size_t need_ws = ws_required(R);
     if (c.ws_bytes < need_ws) {
         void *p = nullptr;
-        if (cudaMallocAsync(&p, need_ws, s) != cudaSuccess) return RTCDF_ERR_NO_MEMORY;
-        if (cudaMemsetAsync(p, 0, need_ws, s) != cudaSuccess) return RTCDF_ERR_CUDA;
-        if (c.ws) cudaFreeAsync(c.ws, s);
+        if (cudaMallocAsync(&p, need_ws, cs) != cudaSuccess) return RTCDF_ERR_NO_MEMORY;
+        if (cudaMemsetAsync(p, 0, need_ws, cs) != cudaSuccess) return RTCDF_ERR_CUDA;
+        if (c.ws) cudaFreeAsync(c.ws, cs);
         c.ws = p;
         c.ws_bytes = need_ws;
     }
@@ -91,39 +98,38 @@ extern "C" rtcdf_status rtcdf_sort_host(const int32_t *h_in, int32_t *h_out, uin
     c.next ^= 1;
     if (b.cap < n) {
         // Growing: wait until nothing uses the old buffers, then replace them.
-        cudaStreamWaitEvent(s, b.in_free, 0);
-        cudaStreamWaitEvent(s, b.out_free, 0);
-        if (b.in) cudaFreeAsync(b.in, s);
-        if (b.out) cudaFreeAsync(b.out, s);
+        cudaStreamWaitEvent(cs, b.in_free, 0);
+        cudaStreamWaitEvent(cs, b.out_free, 0);
+        if (b.in) cudaFreeAsync(b.in, cs);
+        if (b.out) cudaFreeAsync(b.out, cs);
         b.in = b.out = nullptr;
         b.cap = 0;
-        if (cudaMallocAsync((void **)&b.in, n * 4, s) != cudaSuccess ||
-            cudaMallocAsync((void **)&b.out, n * 4, s) != cudaSuccess)
+        if (cudaMallocAsync((void **)&b.in, n * 4, cs) != cudaSuccess ||
+            cudaMallocAsync((void **)&b.out, n * 4, cs) != cudaSuccess)
             return RTCDF_ERR_NO_MEMORY;
         b.cap = n;
-        cudaEventRecord(b.in_free, s);
-        cudaEventRecord(b.out_free, s);
+        cudaEventRecord(b.in_free, cs);
+        cudaEventRecord(b.out_free, cs);
     }
-    // Upload in chunks; the histogram of chunk k waits only for chunk k.
+    // Upload in chunks; the histogram of chunk k waits only for chunk k (the
+    // wait takes the event as last recorded, so one event serves every chunk).
     cudaStreamWaitEvent(c.up, b.in_free, 0);
-    cudaEvent_t ev;
     for (uint64_t k0 = 0; k0 < n; k0 += kChunk) {
         const uint64_t k1 = std::min(n, k0 + kChunk);
         if (cudaMemcpyAsync(b.in + k0, h_in + k0, (k1 - k0) * 4, cudaMemcpyHostToDevice, c.up) != cudaSuccess)
             return RTCDF_ERR_CUDA;
-        if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) return RTCDF_ERR_CUDA;
-        cudaEventRecord(ev, c.up);
-        cudaStreamWaitEvent(s, ev, 0);
-        cudaEventDestroy(ev);  // released once recorded work completes
-        rtcdf_status st = host_pipeline_hist(b.in + k0, k1 - k0, minVal, R, c.ws, c.ws_bytes, s);
+        if (cudaEventRecord(c.ev_chunk, c.up) != cudaSuccess ||
+            cudaStreamWaitEvent(cs, c.ev_chunk, 0) != cudaSuccess)
+            return RTCDF_ERR_CUDA;
+        rtcdf_status st = host_pipeline_hist(b.in + k0, k1 - k0, minVal, R, c.ws, c.ws_bytes, cs);
         if (st) return st;
     }
-    cudaEventRecord(b.in_free, s);
+    cudaEventRecord(b.in_free, cs);
     // Scan and output, once the previous download from this set is done.
-    cudaStreamWaitEvent(s, b.out_free, 0);
-    rtcdf_status st = host_pipeline_finish(b.out, n, minVal, R, c.ws, c.ws_bytes, s);
+    cudaStreamWaitEvent(cs, b.out_free, 0);
+    rtcdf_status st = host_pipeline_finish(b.out, n, minVal, R, c.ws, c.ws_bytes, cs);
     if (st) return st;
-    cudaEventRecord(c.ev_done, s);
+    cudaEventRecord(c.ev_done, cs);
     cudaStreamWaitEvent(c.down, c.ev_done, 0);
     if (cudaMemcpyAsync(h_out, b.out, n * 4, cudaMemcpyDeviceToHost, c.down) != cudaSuccess)
         return RTCDF_ERR_CUDA;
