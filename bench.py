@@ -366,7 +366,7 @@ def cub_comparison(cases, ins, outs, n, stream, nsteps, ours_ms):
 def batched_comparison(args, stream, num_segments=4096):
     """Batched workload: 4096 segments, lengths log-uniform in [1e3, 1e6],
     R log-uniform in [2^7, 2^16], minVal uniform in [-2^20, 2^20], mixed
-    shapes.  One persistent launch (graph-captured) against looped
+    shapes.  One plan (three launches, graph-captured) against looped
     rtcdf_sort calls (plain and graph-captured), keys/s of each."""
     import numpy as np
     import torch
@@ -435,7 +435,7 @@ def batched_comparison(args, stream, num_segments=4096):
         looped()
     ms_looped_graph = timed(g2.replay, steps)
     same = same and bool(torch.equal(out, ref))
-    # One instrumented launch: where the persistent kernel spends its time.
+    # One instrumented run: where the three launches spend their time.
     import torch as _t
     prof = _t.zeros(rtcdf.BATCH_PROFILE_WORDS, dtype=_t.int64, device="cuda")
     prof[8:12] = -1  # UINT64_MAX: earliest-start slots

@@ -241,13 +241,15 @@ rtcdf_status rtcdf_sort_host(const int32_t *in, int32_t *out, uint64_t n, int64_
                              int64_t maxVal, rtcdf_stream_t stream);
 
 /*
- * Segmented sort: many independent arrays ("segments") sorted by one
- * persistent launch.  Segment s is in[seg_offsets[s] .. seg_offsets[s+1]),
- * its keys lie in [seg_minVal[s], seg_maxVal[s]) (R_s <= 2^20), and it is
- * written sorted to the same positions of `out`.  The method per segment is
- * Algorithms 4-7 unchanged; segments with fewer than 65536 keys (and R_s <=
- * 55296) are sorted entirely inside one CTA, larger ones are split into
- * histogram, scan and output work items with per-segment dependencies.
+ * Segmented sort: many independent arrays ("segments") sorted by three
+ * launches whatever their number.  Segment s is
+ * in[seg_offsets[s] .. seg_offsets[s+1]), its keys lie in
+ * [seg_minVal[s], seg_maxVal[s]) (R_s <= 2^20), and it is written sorted to
+ * the same positions of `out`.  The method per segment is Algorithms 4-7
+ * unchanged; segments with fewer than 65536 keys (and R_s <= 55296) are
+ * sorted entirely inside one CTA of the first launch, larger ones are split
+ * into histogram items (first launch), 4096-bin scan chunks (second launch)
+ * and output items (third launch).
  *
  * rtcdf_batch_plan_create builds the work list from HOST arrays
  * (seg_offsets: S+1 entries, nondecreasing; seg_minVal / seg_maxVal: S) and
@@ -265,8 +267,8 @@ typedef struct {
     uint32_t num_segments;
     uint32_t small_segments;   /* sorted inside one CTA */
     uint32_t large_segments;   /* split into work items */
-    uint32_t work_items;
-    uint32_t workers;          /* persistent CTAs (two per SM) */
+    uint32_t work_items;       /* CTAs over the three launches */
+    uint32_t workers;          /* CTAs resident at once per launch (two per SM) */
     uint32_t reserved;
     uint64_t total_keys;
     uint64_t workspace_bytes;
@@ -280,10 +282,7 @@ typedef struct {
     int32_t hist_chunk;   /* keys per histogram item of a large segment (>= 4096; default 524288) */
     int32_t fill_chunk;   /* output positions per output item (>= 4096; default 65536) */
     int32_t small_max_n;  /* longest segment sorted inside one CTA (<= 65535; default 65535) */
-    int32_t schedule_lag; /* queue distance (work items) from a segment's last histogram
-                             item to its scan and from its scan to its outputs;
-                             0 = twice the workers, -1 = one phase after another */
-    int32_t reserved[4];
+    int32_t reserved[5];
 } rtcdf_batch_params;
 
 /* rtcdf_batch_plan_create with explicit work-item sizes (`params` may be NULL). */
@@ -301,16 +300,16 @@ rtcdf_status rtcdf_batch_status_get(void *workspace, rtcdf_stream_t stream,
 
 /*
  * rtcdf_sort_batched_profiled -- rtcdf_sort_batched_ws that also records where
- * the persistent launch spends its time, per work-item kind k (0 histogram,
- * 1 in-CTA segment, 2 segment scan, 3 output): `profile` is a device array of
+ * the launches spend their time, per work-item kind k (0 histogram, 1 in-CTA
+ * segment, 2 scan chunk, 3 output): `profile` is a device array of
  * RTCDF_BATCH_PROFILE_WORDS uint64, initialised by the caller to zero except
  * words 8..11, initialised to UINT64_MAX; afterwards
- *   profile[k]      sum over items of their duration (ns, all workers)
+ *   profile[k]      sum over items (CTAs) of their duration (ns)
  *   profile[4 + k]  items processed
  *   profile[8 + k]  earliest item start   (device global timer, ns)
  *   profile[12 + k] latest item end       (device global timer, ns)
- *   profile[16 + k] ns spent waiting for other items (scan: histograms,
- *                   output: the segment's scan), included in profile[k].
+ *   profile[16 + k] ns spent waiting for other items (scan chunks: the
+ *                   lookback over earlier chunks), included in profile[k].
  * The instrumentation adds a few timer reads and atomics per item.
  */
 #define RTCDF_BATCH_PROFILE_WORDS 20

@@ -1,5 +1,5 @@
 // Host side of the segmented sort: the planner that turns per-segment shapes
-// into the persistent launch's work list, and the C entry points
+// into the work lists of its three launches, and the C entry points
 // (rtcdf_batch_* in include/rtcdf.h).
 //
 // The plan is built once from host-side segment metadata (offsets and ranges)
@@ -7,8 +7,6 @@
 // CUDA graph and replayed for new keys with the same segment shapes.
 #include <algorithm>
 #include <cstring>
-#include <deque>
-#include <utility>
 #include <vector>
 
 #include "../../include/rtcdf.h"
@@ -20,6 +18,7 @@ struct rtcdf_batch_plan {
     int device = 0;
     int workers = 0;
     uint32_t num_segs = 0, num_items = 0;
+    uint32_t n_first = 0, n_scan = 0, n_fill = 0;
     uint64_t total_keys = 0;
     size_t ws_bytes = 0;          // caller workspace needed
     size_t ctl_off = 0, segctl_off = 0;
@@ -48,19 +47,18 @@ int check_specs(const SegSpec *spec, uint32_t S) {
 }
 
 int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P, const BatchTuning &tun) {
-    const uint64_t kHistChunk = tun.hist_chunk;
-    const uint32_t kFillChunk = tun.fill_chunk;
     if (const int rc = check_specs(spec, S)) return rc;
     P->segs.assign(S, BatchSeg{});
     P->items.clear();
     P->small_segs = P->large_segs = 0;
     P->total_keys = 0;
-    std::vector<BatchItem> hist, small, scan, fill;
     // Workspace (in 32-bit words): control block, per-segment control, then
-    // per large segment its histogram (zero between runs) and run tables.
+    // per large segment its histogram (zero between runs), run tables,
+    // output-item start runs and lookback state (zero between runs).
     size_t w = 0;
     P->ctl_off = w;     w += words_align(sizeof(BatchCtl) / 4);
     P->segctl_off = w;  w += words_align((size_t)S * sizeof(BatchSegCtl) / 4);
+    std::vector<uint32_t> large_ids, small_ids;
     for (uint32_t s = 0; s < S; s++) {
         BatchSeg &g = P->segs[s];
         memset(&g, 0, sizeof(g));
@@ -72,29 +70,25 @@ int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P, const BatchTun
         P->total_keys += g.n;
         if (g.n == 0) continue;
         if (g.n <= tun.small_max_n && g.R <= kBatchSmallMaxR) {
-            small.push_back(BatchItem{kItemSmall, s, 0, 0, 0, 0});
+            small_ids.push_back(s);
             P->small_segs++;
             continue;
         }
+        large_ids.push_back(s);
         P->large_segs++;
         g.m = (g.R + kBatchTileMax - 1) / kBatchTileMax;
         g.T = (g.R + g.m - 1) / g.m;
-        const uint64_t chunks = (g.n + kHistChunk - 1) / kHistChunk;
+        const uint64_t chunks = (g.n + tun.hist_chunk - 1) / tun.hist_chunk;
         g.hist_items = (uint32_t)(chunks * g.m);
-        for (uint64_t c = 0; c < chunks; c++)
-            for (uint32_t t = 0; t < g.m; t++)
-                hist.push_back(BatchItem{kItemHist, s, c * kHistChunk,
-                                         std::min<uint64_t>(g.n, (c + 1) * kHistChunk), t, 0});
-        scan.push_back(BatchItem{kItemScan, s, 0, 0, 0, 0});
-        g.fill_chunk = kFillChunk;
-        g.fill_items = (g.n + kFillChunk - 1) / kFillChunk;
-        for (uint32_t f = 0; f < g.fill_items; f++)
-            fill.push_back(BatchItem{kItemFill, s, (uint64_t)f * kFillChunk,
-                                     std::min<uint64_t>(g.n, (uint64_t)(f + 1) * kFillChunk), 0, f});
-        g.hist_off = w;      w += words_align((g.R + kBatchScanChunk - 1) / kBatchScanChunk * kBatchScanChunk);
+        g.single_hist = chunks == 1 ? 1u : 0u;
+        g.scan_chunks = (g.R + kBatchScanChunk - 1) / kBatchScanChunk;
+        g.fill_chunk = tun.fill_chunk;
+        g.fill_items = (uint32_t)((g.n + tun.fill_chunk - 1) / tun.fill_chunk);
+        g.hist_off = w;      w += words_align((size_t)g.scan_chunks * kBatchScanChunk);
         g.run_end_off = w;   w += words_align(g.R);
         g.run_val_off = w;   w += words_align(g.R);
         g.start_run_off = w; w += words_align(g.fill_items);
+        g.state_off = w;     w += words_align((size_t)g.scan_chunks * 2);
     }
     P->ws_words = w;
     const std::vector<BatchSeg> &segs = P->segs;
@@ -103,74 +97,39 @@ int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P, const BatchTun
         const uint64_t cy = (uint64_t)segs[y].n + segs[y].R;
         return cx != cy ? cx > cy : x < y;
     };
-    std::vector<uint32_t> large_ids, small_ids;
-    for (uint32_t s = 0; s < S; s++) {
-        if (segs[s].n == 0) continue;
-        (segs[s].m ? large_ids : small_ids).push_back(s);
-    }
     std::stable_sort(large_ids.begin(), large_ids.end(), by_size);
     std::stable_sort(small_ids.begin(), small_ids.end(), by_size);
-    // Items of each large segment, contiguous in the per-kind lists above.
-    std::vector<size_t> hist_at(S, 0), fill_at(S, 0);
-    for (size_t i = hist.size(); i-- > 0;) hist_at[hist[i].seg] = i;
-    for (size_t i = fill.size(); i-- > 0;) fill_at[fill[i].seg] = i;
-    std::vector<size_t> scan_at(S, 0);
-    for (size_t i = 0; i < scan.size(); i++) scan_at[scan[i].seg] = i;
     std::vector<BatchItem> &Q = P->items;
-    Q.reserve(hist.size() + small.size() + scan.size() + fill.size());
-    auto emit_hist = [&](uint32_t s) {
-        for (uint32_t k = 0; k < segs[s].hist_items; k++) Q.push_back(hist[hist_at[s] + k]);
-    };
-    auto emit_fill = [&](uint32_t s) {
-        for (uint32_t k = 0; k < segs[s].fill_items; k++) Q.push_back(fill[fill_at[s] + k]);
-    };
-    if (tun.lag_items < 0) {
-        // Phase order: every HIST, every SMALL, every SCAN, every FILL.
-        for (uint32_t s : large_ids) emit_hist(s);
-        for (uint32_t s : small_ids) Q.push_back(BatchItem{kItemSmall, s, 0, 0, 0, 0});
-        for (uint32_t s : large_ids) Q.push_back(scan[scan_at[s]]);
-        for (uint32_t s : large_ids) emit_fill(s);
-        return 0;
-    }
-    // Pipelined order (largest segments first): a segment's SCAN is queued
-    // `lag` items after its last HIST item and its FILL items `lag` items
-    // after its SCAN, so that by the time a worker takes them the items they
-    // wait for have most likely finished; SMALL items are spread in
-    // proportion to their keys, so reads and writes stay mixed throughout.
-    // Every item still comes after all the items it waits for.
-    const size_t lag = (size_t)tun.lag_items;
-    uint64_t large_keys = 0, small_keys = 0;
-    for (uint32_t s : large_ids) large_keys += segs[s].n;
-    for (uint32_t s : small_ids) small_keys += segs[s].n;
-    std::deque<std::pair<uint32_t, size_t>> ps, pf;  // (segment, queue position)
-    size_t si = 0;
-    uint64_t large_done = 0, small_done = 0;
-    auto drain = [&](bool all) {
-        while (!ps.empty() && (all || ps.front().second + lag <= Q.size())) {
-            Q.push_back(scan[scan_at[ps.front().first]]);
-            pf.emplace_back(ps.front().first, Q.size());
-            ps.pop_front();
-        }
-        while (!pf.empty() && (all || pf.front().second + lag <= Q.size())) {
-            emit_fill(pf.front().first);
-            pf.pop_front();
-        }
-    };
+    // First launch: histogram items (largest segments first), then the
+    // in-CTA segments (largest first) -- long items start early.
     for (uint32_t s : large_ids) {
-        emit_hist(s);
-        ps.emplace_back(s, Q.size());
-        large_done += segs[s].n;
-        // small_done / small_keys keeps up with large_done / large_keys
-        while (si < small_ids.size() &&
-               (unsigned __int128)small_done * large_keys < (unsigned __int128)large_done * small_keys) {
-            Q.push_back(BatchItem{kItemSmall, small_ids[si], 0, 0, 0, 0});
-            small_done += segs[small_ids[si]].n;
-            si++;
-        }
-        drain(false);
+        const BatchSeg &g = segs[s];
+        const uint64_t chunks = g.hist_items / g.m;
+        for (uint64_t c = 0; c < chunks; c++)
+            for (uint32_t t = 0; t < g.m; t++)
+                Q.push_back(BatchItem{kItemHist, s, c * tun.hist_chunk,
+                                      std::min<uint64_t>(g.n, (c + 1) * tun.hist_chunk), t, 0});
     }
-    for (; si < small_ids.size(); si++) Q.push_back(BatchItem{kItemSmall, small_ids[si], 0, 0, 0, 0});
-    drain(true);
+    for (uint32_t s : small_ids) Q.push_back(BatchItem{kItemSmall, s, 0, 0, 0, 0});
+    P->n_first = (uint32_t)Q.size();
+    // Scan launch, in ticket order: each segment's chunks in ascending order
+    // (a chunk's lookback only reaches earlier chunks of its segment), the
+    // longest chains first.
+    std::vector<uint32_t> by_chunks = large_ids;
+    std::stable_sort(by_chunks.begin(), by_chunks.end(), [&](uint32_t x, uint32_t y) {
+        return segs[x].scan_chunks > segs[y].scan_chunks;
+    });
+    for (uint32_t s : by_chunks)
+        for (uint32_t c = 0; c < segs[s].scan_chunks; c++) Q.push_back(BatchItem{kItemScan, s, c, 0, 0, 0});
+    P->n_scan = (uint32_t)Q.size() - P->n_first;
+    // Output launch.
+    for (uint32_t s : large_ids) {
+        const BatchSeg &g = segs[s];
+        for (uint32_t f = 0; f < g.fill_items; f++)
+            Q.push_back(BatchItem{kItemFill, s, (uint64_t)f * g.fill_chunk,
+                                  std::min<uint64_t>(g.n, (uint64_t)(f + 1) * g.fill_chunk), 0, f});
+    }
+    P->n_fill = (uint32_t)Q.size() - P->n_first - P->n_scan;
     return 0;
 }
 
@@ -199,7 +158,6 @@ rtcdf_status rtcdf_batch_plan_create_ex(const int64_t *seg_offsets, const int64_
         if (params->hist_chunk) tun.hist_chunk = (uint64_t)params->hist_chunk;
         if (params->fill_chunk) tun.fill_chunk = (uint32_t)params->fill_chunk;
         if (params->small_max_n) tun.small_max_n = (uint32_t)params->small_max_n;
-        if (params->schedule_lag < -1) return RTCDF_ERR_INVALID_ARG;
     }
     *plan_out = nullptr;
     if (num_segments > 0 && (!seg_offsets || !seg_minVal || !seg_maxVal)) return RTCDF_ERR_INVALID_ARG;
@@ -216,17 +174,18 @@ rtcdf_status rtcdf_batch_plan_create_ex(const int64_t *seg_offsets, const int64_
     if (cudaGetDevice(&dev) != cudaSuccess) return RTCDF_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return RTCDF_ERR_CUDA;
-    const int32_t lag = params ? params->schedule_lag : 0;
-    tun.lag_items = lag == 0 ? 2 * (int64_t)sms * kBatchWorkersPerSM : (int64_t)lag;
     HostPlan hp;
     const int rc = build_host_plan(spec.data(), S, &hp, tun);
     if (rc) return (rtcdf_status)rc;
 
     rtcdf_batch_plan *p = new rtcdf_batch_plan();
     p->device = dev;
-    p->workers = sms * kBatchWorkersPerSM;
+    p->workers = sms * 2;  // resident 1024-thread CTAs per launch
     p->num_segs = S;
     p->num_items = (uint32_t)hp.items.size();
+    p->n_first = hp.n_first;
+    p->n_scan = hp.n_scan;
+    p->n_fill = hp.n_fill;
     p->total_keys = hp.total_keys;
     p->ws_bytes = hp.ws_words * 4;
     p->ctl_off = hp.ctl_off;
@@ -310,13 +269,15 @@ rtcdf_status rtcdf_sort_batched_profiled(const rtcdf_batch_plan *plan, const int
     a.out = out;
     a.segs = plan->d_segs;
     a.items = plan->d_items;
-    a.num_items = plan->num_items;
+    a.n_first = plan->n_first;
+    a.n_scan = plan->n_scan;
+    a.n_fill = plan->n_fill;
     a.num_segs = plan->num_segs;
     a.ws_u32 = ws;
     a.ctl = (BatchCtl *)(ws + plan->ctl_off);
     a.seg_ctl = (BatchSegCtl *)(ws + plan->segctl_off);
     a.prof = reinterpret_cast<unsigned long long *>(profile);
-    if (launch_batched(a, plan->workers, (cudaStream_t)stream) != cudaSuccess) return RTCDF_ERR_CUDA;
+    if (launch_batched(a, (cudaStream_t)stream) != cudaSuccess) return RTCDF_ERR_CUDA;
     return RTCDF_OK;
 }
 

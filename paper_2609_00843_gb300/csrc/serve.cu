@@ -268,9 +268,7 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
                     const uint64_t in_off = slot_off[i] / 4;  // input at the slot start, output after it
                     spec[j] = SegSpec{in_off, in_off + reqs[i].n, reqs[i].n, reqs[i].minVal, reqs[i].maxVal};
                 }
-                BatchTuning tun;
-                tun.lag_items = 2 * (int64_t)sms * kBatchWorkersPerSM;
-                if (build_host_plan(spec.data(), (uint32_t)spec.size(), &hp, tun)) { err = RTCDF_ERR_RANGE; break; }
+                if (build_host_plan(spec.data(), (uint32_t)spec.size(), &hp)) { err = RTCDF_ERR_RANGE; break; }
             }
             std::vector<DigestSeg> dg;
             if (want_digest) {
@@ -322,12 +320,14 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
                 a.out = reinterpret_cast<int32_t *>(slab);
                 a.segs = reinterpret_cast<const BatchSeg *>(tab);
                 a.items = reinterpret_cast<const BatchItem *>(tab + seg_b);
-                a.num_items = (uint32_t)hp.items.size();
+                a.n_first = hp.n_first;
+                a.n_scan = hp.n_scan;
+                a.n_fill = hp.n_fill;
                 a.num_segs = (uint32_t)hp.segs.size();
                 a.ws_u32 = ws;
                 a.ctl = reinterpret_cast<BatchCtl *>(ws + hp.ctl_off);
                 a.seg_ctl = reinterpret_cast<BatchSegCtl *>(ws + hp.segctl_off);
-                if (a.num_items && launch_batched(a, sms * kBatchWorkersPerSM, s) != cudaSuccess) {
+                if (launch_batched(a, s) != cudaSuccess) {
                     err = RTCDF_ERR_CUDA;
                     break;
                 }

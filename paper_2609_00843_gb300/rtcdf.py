@@ -48,8 +48,7 @@ class Params(ctypes.Structure):
 
 class BatchParams(ctypes.Structure):
     _fields_ = [("hist_chunk", ctypes.c_int32), ("fill_chunk", ctypes.c_int32),
-                ("small_max_n", ctypes.c_int32), ("schedule_lag", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("small_max_n", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
 
 
 class TuneEntry(ctypes.Structure):
@@ -203,7 +202,8 @@ BATCH_ITEM_KINDS = ("hist", "small", "scan", "fill")
 
 def batch_profile_summary(words, workers: int) -> dict:
     """Turn the profile words of rtcdf_sort_batched_profiled into per-kind
-    figures: average busy ms per worker, items, span ms, wait share."""
+    figures: busy ms per resident CTA slot (sum of item durations / workers),
+    items, start and end of the phase (ms from the first item), wait share."""
     t0 = min(words[8 + k] for k in range(4) if words[4 + k])
     out = {}
     for k, name in enumerate(BATCH_ITEM_KINDS):

@@ -208,9 +208,6 @@ def tune_batched(reps: int = 5, margin: float = 0.01, log=print) -> dict:
         for fc in BATCH_FILL_CHUNKS:
             for sm in BATCH_SMALL_MAX:
                 cands.append(rtcdf.BatchParams(hist_chunk=hc, fill_chunk=fc, small_max_n=sm))
-    workers = 2 * torch.cuda.get_device_properties(0).multi_processor_count
-    for lag in (-1, workers // 2, workers, 4 * workers, 8 * workers):
-        cands.append(rtcdf.BatchParams(schedule_lag=lag))
     times = []
     for (S, n_lo, n_hi, r_lo, r_hi, sd) in BATCH_WORKLOADS:
         L, mn, R, dist, seeds = gen.batched_segments(gen.derive_seed(12, sd), S, n_lo=n_lo,
@@ -249,7 +246,7 @@ def tune_batched(reps: int = 5, margin: float = 0.01, log=print) -> dict:
         del x, out
     gm = _geomean(times)
     k = _pick(gm, margin)
-    fields = ("hist_chunk", "fill_chunk", "small_max_n", "schedule_lag")
+    fields = ("hist_chunk", "fill_chunk", "small_max_n")
     return {"workloads": [list(w) for w in BATCH_WORKLOADS],
             "candidates": [{f: getattr(p, f) for f in fields} for p in cands],
             "times_ms": times, "geomean": gm, "chosen": k,

@@ -1,8 +1,11 @@
 // Host-side check of the segmented-sort planner (rtcdf::build_host_plan):
-// for random segment shapes and every schedule, each work item comes after
-// the items it waits for, the items of every segment cover its keys and
-// positions exactly once, and the per-segment workspace regions are disjoint.
-// Usage: planner_check <seed> <segments>; prints "OK" or the first violation.
+// for random segment shapes and several work-item sizes, the work list splits
+// into the three launches with the right kinds, every segment's scan chunks
+// come in ascending order (a chunk's lookback only reaches earlier chunks of
+// its segment, handed out before it), the items of every segment cover its
+// keys and positions exactly once, and the per-segment workspace regions are
+// disjoint.  Usage: planner_check <seed> <segments>; prints "OK" or the first
+// violation.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -23,47 +26,55 @@ static int check(const std::vector<SegSpec> &spec, const BatchTuning &tun) {
     HostPlan P;
     if (build_host_plan(spec.data(), (uint32_t)spec.size(), &P, tun)) return fail("plan rejected", 0, 0);
     const uint32_t S = (uint32_t)spec.size();
-    std::vector<long> last_hist(S, -1), scan_pos(S, -1), first_fill(S, 1L << 60);
-    std::vector<uint32_t> small_seen(S, 0), scans(S, 0);
+    if ((size_t)P.n_first + P.n_scan + P.n_fill != P.items.size()) return fail("launch sizes", 0, 0);
+    std::vector<uint32_t> small_seen(S, 0), next_chunk(S, 0);
     std::vector<std::vector<std::pair<uint64_t, uint64_t>>> hist_rng(S), fill_rng(S);
     for (size_t q = 0; q < P.items.size(); q++) {
         const BatchItem &it = P.items[q];
         if (it.seg >= S) return fail("segment index", (long)q, it.seg);
         const BatchSeg &g = P.segs[it.seg];
+        const int launch = q < P.n_first ? 0 : (q < (size_t)P.n_first + P.n_scan ? 1 : 2);
         switch (it.kind) {
             case kItemHist:
-                if (scan_pos[it.seg] >= 0) return fail("hist after its scan", (long)q, it.seg);
-                last_hist[it.seg] = (long)q;
+                if (launch != 0) return fail("hist outside the first launch", (long)q, launch);
                 if (it.tile >= g.m) return fail("tile index", (long)q, it.tile);
                 hist_rng[it.seg].push_back({it.a * 1024 + it.tile, it.b});
                 break;
-            case kItemSmall: small_seen[it.seg]++; break;
+            case kItemSmall:
+                if (launch != 0) return fail("small outside the first launch", (long)q, launch);
+                small_seen[it.seg]++;
+                break;
             case kItemScan:
-                scans[it.seg]++;
-                if (last_hist[it.seg] < 0) return fail("scan before any hist", (long)q, it.seg);
-                scan_pos[it.seg] = (long)q;
+                if (launch != 1) return fail("scan outside the scan launch", (long)q, launch);
+                if (it.a != next_chunk[it.seg]) return fail("scan chunk order", (long)q, (long)it.a);
+                next_chunk[it.seg]++;
                 break;
             case kItemFill:
-                if (scan_pos[it.seg] < 0) return fail("fill before its scan", (long)q, it.seg);
+                if (launch != 2) return fail("fill outside the output launch", (long)q, launch);
                 fill_rng[it.seg].push_back({it.a, it.b});
-                if (it.aux >= g.fill_items) return fail("fill index", (long)q, it.aux);
+                if (it.aux >= g.fill_items || it.a != (uint64_t)it.aux * g.fill_chunk)
+                    return fail("fill index", (long)q, it.aux);
                 break;
             default: return fail("item kind", (long)q, it.kind);
         }
     }
-    size_t ws_prev_end = 0;
+    size_t ws_prev_end = P.segctl_off + S * sizeof(BatchSegCtl) / 4;
+    if (P.segctl_off < P.ctl_off + sizeof(BatchCtl) / 4) return fail("control blocks overlap", 0, 0);
     for (uint32_t s = 0; s < S; s++) {
         const BatchSeg &g = P.segs[s];
         if (spec[s].n == 0) {
-            if (small_seen[s] || scans[s]) return fail("empty segment has items", s, 0);
+            if (small_seen[s] || next_chunk[s] || !hist_rng[s].empty()) return fail("empty segment has items", s, 0);
             continue;
         }
         const bool large = g.m > 0;
         if (!large) {
             if (small_seen[s] != 1) return fail("small segment not exactly once", s, small_seen[s]);
+            if (g.n > tun.small_max_n || g.R > kBatchSmallMaxR) return fail("small limits", s, g.R);
             continue;
         }
-        if (small_seen[s] || scans[s] != 1) return fail("large segment scans", s, scans[s]);
+        if (small_seen[s]) return fail("large segment sorted in one CTA", s, 0);
+        if (next_chunk[s] != g.scan_chunks || (uint64_t)g.scan_chunks * kBatchScanChunk < g.R)
+            return fail("scan chunks", s, next_chunk[s]);
         // histogram items: for each tile, key ranges tile [0, n) without overlap
         std::vector<std::vector<std::pair<uint64_t, uint64_t>>> per_tile(g.m);
         for (auto &r : hist_rng[s]) per_tile[r.first % 1024].push_back({r.first / 1024, r.second});
@@ -77,6 +88,7 @@ static int check(const std::vector<SegSpec> &spec, const BatchTuning &tun) {
                 at = r.second;
             }
             if (at != g.n) return fail("hist keys not covered", s, t);
+            if (g.single_hist != (v.size() == 1 ? 1u : 0u)) return fail("single_hist flag", s, t);
             nh += (uint32_t)v.size();
         }
         if (nh != g.hist_items) return fail("hist item count", s, nh);
@@ -89,13 +101,17 @@ static int check(const std::vector<SegSpec> &spec, const BatchTuning &tun) {
         }
         if (at != g.n || f.size() != g.fill_items) return fail("fill coverage", s, (long)at);
         if ((uint64_t)g.T * g.m < g.R || g.T > kBatchTileMax) return fail("tiles", s, g.T);
-        // workspace regions in order, disjoint, inside ws_words
-        const size_t regs[4][2] = {{g.hist_off, (g.R + kBatchScanChunk - 1) / kBatchScanChunk * kBatchScanChunk},
-                                   {g.run_end_off, g.R}, {g.run_val_off, g.R}, {g.start_run_off, g.fill_items}};
+        // workspace regions in order, disjoint, inside ws_words; the lookback
+        // state is 8-byte aligned
+        const size_t regs[5][2] = {{g.hist_off, (size_t)g.scan_chunks * kBatchScanChunk},
+                                   {g.run_end_off, g.R}, {g.run_val_off, g.R},
+                                   {g.start_run_off, g.fill_items}, {g.state_off, 2 * (size_t)g.scan_chunks}};
         for (auto &r : regs) {
             if (r[0] < ws_prev_end) return fail("workspace overlap", s, (long)r[0]);
             ws_prev_end = r[0] + r[1];
         }
+        if (g.state_off % 2) return fail("state alignment", s, (long)g.state_off);
+        if (g.hist_off % 4) return fail("histogram alignment", s, (long)g.hist_off);
         if (ws_prev_end > P.ws_words) return fail("workspace size", s, (long)ws_prev_end);
     }
     return 0;
@@ -115,13 +131,10 @@ int main(int argc, char **argv) {
         spec[s] = SegSpec{off, off, n, mn, mn + R};
         off += n;
     }
-    BatchTuning tunings[5];
-    tunings[0].lag_items = -1;
-    tunings[1].lag_items = 0;
-    tunings[2].lag_items = 608;
-    tunings[3].lag_items = 1000000;
-    tunings[4].lag_items = 7; tunings[4].hist_chunk = 4096; tunings[4].fill_chunk = 4096;
-    tunings[4].small_max_n = 100;
+    BatchTuning tunings[4];
+    tunings[1].hist_chunk = 4096; tunings[1].fill_chunk = 4096; tunings[1].small_max_n = 100;
+    tunings[2].hist_chunk = 1ull << 22; tunings[2].fill_chunk = 1u << 20; tunings[2].small_max_n = 1;
+    tunings[3].hist_chunk = 5000; tunings[3].fill_chunk = 6000;
     for (auto &t : tunings)
         if (check(spec, t)) return 1;
     std::printf("OK\n");

@@ -1,8 +1,8 @@
 """The segmented-sort planner, on the host: a small C++ program links the
 library, builds plans for random segment shapes under every schedule and
-checks the invariants the persistent launch relies on (each item after the
-items it waits for, exact coverage of keys and positions, disjoint workspace
-regions)."""
+checks the invariants the three launches rely on (kinds in the right launch,
+scan chunks of a segment in ascending ticket order, exact coverage of keys
+and positions, disjoint workspace regions)."""
 import os
 import shutil
 import subprocess
