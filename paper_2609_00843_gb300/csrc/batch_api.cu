@@ -100,17 +100,32 @@ int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P, const BatchTun
     std::stable_sort(large_ids.begin(), large_ids.end(), by_size);
     std::stable_sort(small_ids.begin(), small_ids.end(), by_size);
     std::vector<BatchItem> &Q = P->items;
-    // First launch: histogram items (largest segments first), then the
-    // in-CTA segments (largest first) -- long items start early.
+    // First launch: histogram items (largest segments first) with the in-CTA
+    // segments (largest first) spread among them in proportion to their keys,
+    // so that reads (histograms) and writes (in-CTA sorts) overlap throughout.
+    uint64_t large_keys = 0, small_keys = 0, large_done = 0, small_done = 0;
+    for (uint32_t s : large_ids) large_keys += (uint64_t)segs[s].n * segs[s].m;
+    for (uint32_t s : small_ids) small_keys += segs[s].n;
+    size_t si = 0;
     for (uint32_t s : large_ids) {
         const BatchSeg &g = segs[s];
         const uint64_t chunks = g.hist_items / g.m;
-        for (uint64_t c = 0; c < chunks; c++)
-            for (uint32_t t = 0; t < g.m; t++)
-                Q.push_back(BatchItem{kItemHist, s, c * tun.hist_chunk,
-                                      std::min<uint64_t>(g.n, (c + 1) * tun.hist_chunk), t, 0});
+        for (uint64_t c = 0; c < chunks; c++) {
+            for (uint32_t t = 0; t < g.m; t++) {
+                const uint64_t a0 = c * tun.hist_chunk, b0 = std::min<uint64_t>(g.n, (c + 1) * tun.hist_chunk);
+                Q.push_back(BatchItem{kItemHist, s, a0, b0, t, 0});
+                large_done += b0 - a0;
+                // small_done / small_keys keeps up with large_done / large_keys
+                while (si < small_ids.size() &&
+                       (double)small_done * (double)large_keys < (double)large_done * (double)small_keys) {
+                    Q.push_back(BatchItem{kItemSmall, small_ids[si], 0, 0, 0, 0});
+                    small_done += segs[small_ids[si]].n;
+                    si++;
+                }
+            }
+        }
     }
-    for (uint32_t s : small_ids) Q.push_back(BatchItem{kItemSmall, s, 0, 0, 0, 0});
+    for (; si < small_ids.size(); si++) Q.push_back(BatchItem{kItemSmall, small_ids[si], 0, 0, 0, 0});
     P->n_first = (uint32_t)Q.size();
     // Scan launch, in ticket order: each segment's chunks in ascending order
     // (a chunk's lookback only reaches earlier chunks of its segment), the

@@ -13,10 +13,10 @@
 //                        CTA: 16-bit shared-memory counters (a count never
 //                        exceeds n_s < 2^16), in-place CDF, output by
 //                        Algorithm 7's rule;
-//   scan launch    one CTA per 4096-bin chunk of a large segment's H: local
-//                  CDF + offsets (Algorithm 6) by a decoupled lookback chained
-//                  within the segment, the run table and the first run of each
-//                  output item;
+//   scan launch    one 256-thread CTA per 4096-bin chunk of a large
+//                  segment's H: local CDF + offsets (Algorithm 6) by a
+//                  decoupled lookback chained within the segment, the run
+//                  table and the first run of each output item;
 //   output launch  one CTA per output item: positions from the run table
 //                  (Algorithm 7's rule), as in the single-array output kernel.
 //
@@ -285,14 +285,21 @@ __global__ void __launch_bounds__(kSegThreads, 2) seg_first_kernel(BatchArgs a) 
     }
 }
 
-__global__ void __launch_bounds__(kSegThreads) seg_scan_kernel(BatchArgs a) {
+// One 4096-bin chunk per CTA of kScanCtaThreads threads (16 bins each): small
+// CTAs, so that several are resident per SM -- a chunk is mostly latency (its
+// loads, the lookback, the run-table stores).
+constexpr int kScanCtaThreads = 256;
+constexpr int kScanPerThread = kBatchScanChunk / kScanCtaThreads;  // 16
+
+__global__ void __launch_bounds__(kScanCtaThreads) seg_scan_kernel(BatchArgs a) {
     __shared__ uint32_t s_ticket;
-    __shared__ uint64_t s_warp[kSegThreads / 32];
+    __shared__ uint64_t s_warp[kScanCtaThreads / 32];
     __shared__ uint64_t s_prefix;
     __shared__ unsigned long long s_wait;
     __shared__ uint32_t s_cdf[kBatchScanChunk];
     __shared__ uint32_t s_runs[kBatchScanChunk];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int kWarps = kScanCtaThreads / 32;
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
@@ -306,27 +313,34 @@ __global__ void __launch_bounds__(kSegThreads) seg_scan_kernel(BatchArgs a) {
     uint32_t *run_end = a.ws_u32 + g.run_end_off;
     int32_t *run_val = reinterpret_cast<int32_t *>(a.ws_u32 + g.run_val_off);
     uint32_t *start_run = a.ws_u32 + g.start_run_off;
-    const uint32_t base = chunk * kBatchScanChunk + tid * 4;
+    const uint32_t cbase = chunk * kBatchScanChunk;
+    const uint32_t first = tid * kScanPerThread;  // this thread's bins in the chunk
 
-    // Four counts (H is padded to whole chunks), zeroed behind us.
-    uint4 *h4p = reinterpret_cast<uint4 *>(H + base);
-    const uint4 h4 = *h4p;
-    *h4p = make_uint4(0, 0, 0, 0);
-    const uint32_t c[4] = {h4.x, h4.y, h4.z, h4.w};
-    uint64_t incl[4];
+    // Sixteen counts per thread (H is padded to whole chunks), zeroed behind
+    // us; kept in shared memory for the second pass.
+    uint4 *h4p = reinterpret_cast<uint4 *>(H + cbase + first);
+    uint4 q[kScanPerThread / 4];
+#pragma unroll
+    for (int k = 0; k < kScanPerThread / 4; k++) q[k] = h4p[k];
+#pragma unroll
+    for (int k = 0; k < kScanPerThread / 4; k++) h4p[k] = make_uint4(0, 0, 0, 0);
     uint64_t run = 0;
 #pragma unroll
-    for (int i = 0; i < 4; i++) {
-        run += ((uint64_t)(c[i] > 0) << 32) | c[i];
-        incl[i] = run;
+    for (int k = 0; k < kScanPerThread / 4; k++) {
+        const uint32_t c4[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
+#pragma unroll
+        for (int e = 0; e < 4; e++) {
+            s_cdf[first + 4 * k + e] = c4[e];
+            run += ((uint64_t)(c4[e] > 0) << 32) | c4[e];
+        }
     }
     const uint64_t winc = warp_incl_scan_u64(run, lane);
     if (lane == 31) s_warp[warp] = winc;
     __syncthreads();
     if (warp == 0) {
-        const uint64_t wt = s_warp[lane];
+        const uint64_t wt = lane < kWarps ? s_warp[lane] : 0ull;
         const uint64_t wi = warp_incl_scan_u64(wt, lane);
-        s_warp[lane] = wi - wt;
+        if (lane < kWarps) s_warp[lane] = wi - wt;
         const uint64_t total = __shfl_sync(0xffffffffu, wi, 31);
         // Decoupled lookback within the segment.
         uint64_t prefix = 0;
@@ -351,8 +365,8 @@ __global__ void __launch_bounds__(kSegThreads) seg_scan_kernel(BatchArgs a) {
                     if (timed_out) break;
                     const unsigned incl_mask = __ballot_sync(0xffffffffu, (st >> 62) == 2);
                     if (incl_mask) {
-                        const int first = __ffs(incl_mask) - 1;
-                        prefix += warp_sum_u64((lane <= first) ? (st & kStValue) : 0);
+                        const int fi = __ffs(incl_mask) - 1;
+                        prefix += warp_sum_u64((lane <= fi) ? (st & kStValue) : 0);
                         break;
                     }
                     prefix += warp_sum_u64(st & kStValue);
@@ -370,21 +384,21 @@ __global__ void __launch_bounds__(kSegThreads) seg_scan_kernel(BatchArgs a) {
     }
     __syncthreads();
     const uint64_t chunk_prefix = s_prefix;
-    const uint64_t texcl = chunk_prefix + s_warp[warp] + (winc - run);
-#pragma unroll
-    for (int i = 0; i < 4; i++) {
-        const uint32_t v = base + i;
-        const uint64_t p = texcl + incl[i];
+    uint64_t p = chunk_prefix + s_warp[warp] + (winc - run);  // exclusive prefix of this thread
+    for (int i = 0; i < kScanPerThread; i++) {
+        const uint32_t v = cbase + first + i;
+        const uint32_t c = s_cdf[first + i];
+        p += ((uint64_t)(c > 0) << 32) | c;
         const uint32_t cnt_end = (uint32_t)p;
         const uint32_t runs = (uint32_t)(p >> 32);
-        s_cdf[tid * 4 + i] = cnt_end;
-        s_runs[tid * 4 + i] = runs;
+        s_cdf[first + i] = cnt_end;
+        s_runs[first + i] = runs;
         if (v >= g.R) continue;
         if (v == g.R - 1) {
             a.seg_ctl[it.seg].num_runs = runs;
             if (cnt_end != g.n) atomicOr(&a.ctl->status, kDevKeyOutOfRange);
         }
-        if (c[i] > 0) {
+        if (c > 0) {
             run_end[runs - 1] = cnt_end;
             run_val[runs - 1] = (int32_t)((uint32_t)g.minVal + v);
         }
@@ -397,7 +411,7 @@ __global__ void __launch_bounds__(kSegThreads) seg_scan_kernel(BatchArgs a) {
         const uint32_t fc = g.fill_chunk;
         const uint32_t j_lo = (uint32_t)(((uint64_t)pos_lo + fc - 1) / fc);
         const uint32_t j_hi = min((uint32_t)(((uint64_t)pos_hi + fc - 1) / fc), g.fill_items);
-        for (uint32_t j = j_lo + tid; j < j_hi; j += kSegThreads) {
+        for (uint32_t j = j_lo + tid; j < j_hi; j += kScanCtaThreads) {
             const uint32_t p0 = j * fc;
             uint32_t lo = 0, hi = kBatchScanChunk - 1;
             while (lo < hi) {
@@ -413,7 +427,11 @@ __global__ void __launch_bounds__(kSegThreads) seg_scan_kernel(BatchArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(kSegThreads) seg_fill_kernel(BatchArgs a) {
+// Output CTAs of 512 threads: four resident per SM, so that one CTA's
+// descriptor loads and window round trip overlap the others' stores.
+constexpr int kFillCtaThreads = 512;
+
+__global__ void __launch_bounds__(kFillCtaThreads) seg_fill_kernel(BatchArgs a) {
     __shared__ uint32_t s_end[kSegFillRuns];
     __shared__ int32_t s_val[kSegFillRuns];
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
@@ -504,11 +522,11 @@ __global__ void __launch_bounds__(kSegThreads) seg_fill_kernel(BatchArgs a) {
 
 namespace {
 
-cudaError_t launch_pdl(const void *fn, uint32_t grid, size_t smem, const BatchArgs &a, cudaStream_t s) {
+cudaError_t launch_pdl(const void *fn, uint32_t grid, int threads, const BatchArgs &a, cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
-    cfg.blockDim = dim3(kSegThreads);
-    cfg.dynamicSmemBytes = smem;
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = 0;
     cfg.stream = s;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -529,9 +547,11 @@ cudaError_t launch_batched(const BatchArgs &a, cudaStream_t s) {
         seg_first_kernel<<<a.n_first, kSegThreads, kSegSmemBytes, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (a.n_scan && (e = launch_pdl((const void *)seg_scan_kernel, a.n_scan, 0, a, s)) != cudaSuccess)
+    if (a.n_scan &&
+        (e = launch_pdl((const void *)seg_scan_kernel, a.n_scan, kScanCtaThreads, a, s)) != cudaSuccess)
         return e;
-    if (a.n_fill && (e = launch_pdl((const void *)seg_fill_kernel, a.n_fill, 0, a, s)) != cudaSuccess)
+    if (a.n_fill &&
+        (e = launch_pdl((const void *)seg_fill_kernel, a.n_fill, kFillCtaThreads, a, s)) != cudaSuccess)
         return e;
     return cudaSuccess;
 }

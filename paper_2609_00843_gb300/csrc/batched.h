@@ -7,19 +7,19 @@
 
 namespace rtcdf {
 
-// Three launches per plan, all of 1024-thread CTAs:
+// Three launches per plan:
 //   1. histogram items of the large segments and whole in-CTA sorts of the
-//      small ones (112 KB of shared memory each, two CTAs per SM);
-//   2. local CDFs + offsets: one CTA per 4096-bin chunk of a large segment's
-//      histogram, chained within the segment by a decoupled lookback;
-//   3. output items of the large segments.
+//      small ones (1024 threads, 112 KB of shared memory each, two per SM);
+//   2. local CDFs + offsets: one 256-thread CTA per 4096-bin chunk of a large
+//      segment's histogram, chained within the segment by a decoupled lookback;
+//   3. output items of the large segments (512-thread CTAs).
 constexpr int kSegThreads = 1024;
 constexpr size_t kSegSmemBytes = 112 * 1024;          // first launch, per CTA
 constexpr uint32_t kBatchSmallMaxN = 65535;           // 16-bit counters are exact below 2^16
 constexpr uint32_t kBatchSmallMaxR = 55296;           // 16-bit counters in 108 KB
 constexpr uint32_t kBatchTileMax = 28672;             // 32-bit tile histogram in 112 KB
 constexpr uint32_t kBatchScanChunk = 4096;            // bins per scan CTA (4 per thread)
-constexpr uint32_t kSegFillRuns = 4 * kSegThreads;    // run window of an output CTA
+constexpr uint32_t kSegFillRuns = 4096;               // run window of an output CTA
 constexpr uint64_t kBatchMaxR = 1ull << 20;
 
 enum : uint32_t { kItemHist = 0, kItemSmall = 1, kItemScan = 2, kItemFill = 3 };
