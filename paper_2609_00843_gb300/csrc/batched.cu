@@ -176,28 +176,52 @@ __device__ void do_small(const BatchArgs &a, const BatchSeg &g, uint32_t *sm) {
     if (tid == 0 && total != n) atomicOr(&a.ctl->status, kDevKeyOutOfRange);
     __syncthreads();
     // Output: position p holds minVal + min{v : CDF[v] >= p + 1} (Algorithm 7).
-    // Each warp takes a contiguous block of positions, lanes interleaved (one
-    // coalesced store per step); a lane's positions grow by 32, so after one
-    // binary search its value index only moves forward.
+    // 16-byte vectors: each warp takes a contiguous share, lanes interleaved
+    // (one coalesced store per step); a lane's value index only moves forward
+    // (the next value is tried first, then a binary search).  The positions
+    // before the first whole vector and after the last are written one by one.
     int32_t *out = a.out + g.out_off;
     const uint32_t lim = min(n, total);
+    const uint32_t head = min(lim, (uint32_t)(((16 - ((uintptr_t)out & 15)) & 15) / 4));
+    const uint32_t nvec = (lim - head) / 4;
+    int4 *vout = reinterpret_cast<int4 *>(out + head);
+    auto cdf = [&](uint32_t v) -> uint32_t { return c16[slot(v)]; };
+    auto first_above = [&](uint32_t lo, uint32_t p) -> uint32_t {  // min{v >= lo : cdf(v) > p}
+        uint32_t hi = R - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (cdf(mid) > p) hi = mid; else lo = mid + 1;
+        }
+        return lo;
+    };
     const uint32_t lane = tid & 31, warp = tid >> 5, nwarps = nt >> 5;
-    const uint32_t per_warp = ((lim + nwarps - 1) / nwarps + 31) & ~31u;
-    const uint32_t pb = warp * per_warp, pe = min(lim, pb + per_warp);
+    const uint32_t per_warp = ((nvec + nwarps - 1) / nwarps + 31) & ~31u;
+    const uint32_t wb = warp * per_warp, we = min(nvec, wb + per_warp);
     uint32_t v = 0;
     bool first = true;
-    for (uint32_t p = pb + lane; p < pe; p += 32) {
-        if (first || c16[slot(v)] <= p) {
-            uint32_t lo = first ? 0u : v + 1, hi = R - 1;
-            if (!first && c16[slot(lo)] > p) hi = lo;
-            while (lo < hi) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (c16[slot(mid)] > p) hi = mid; else lo = mid + 1;
-            }
-            v = lo;
+    for (uint32_t w = wb + lane; w < we; w += 32) {
+        const uint32_t q = head + 4 * w;
+        if (first || cdf(v) <= q) {
+            v = (!first && v + 1 < R && cdf(v + 1) > q) ? v + 1 : first_above(first ? 0u : v + 1, q);
             first = false;
         }
-        out[p] = (int32_t)(min_u + v);
+        if (cdf(v) >= q + 4) {
+            const int32_t val = (int32_t)(min_u + v);
+            vout[w] = make_int4(val, val, val, val);
+        } else {
+            int32_t r[4];
+            uint32_t vv = v;
+#pragma unroll
+            for (int e = 0; e < 4; e++) {
+                while (cdf(vv) <= q + e) vv++;
+                r[e] = (int32_t)(min_u + vv);
+            }
+            vout[w] = make_int4(r[0], r[1], r[2], r[3]);
+        }
+    }
+    if (tid < 8) {
+        const uint32_t p = tid < head ? tid : head + 4 * nvec + (tid - head);
+        if ((tid < head || tid - head < 4) && p < lim) out[p] = (int32_t)(min_u + first_above(0u, p));
     }
 }
 
