@@ -182,3 +182,27 @@ def test_profiled_launch_counts_every_item_and_sorts_the_same():
     assert plan.run(x.data_ptr(), out2.data_ptr(), ws.data_ptr(), wsb, s) == rtcdf.OK
     torch.cuda.synchronize()
     assert torch.equal(out, out2)
+
+
+def test_benchmark_batched_workload_every_segment():
+    """The benchmark's segmented workload itself (4096 segments, 5.8e8 keys,
+    the seed bench.py uses), replayed from a CUDA graph as the benchmark does:
+    every segment against the oracle."""
+    L, mn, R, dist, seeds = gen.batched_segments(gen.derive_seed(4), 4096)
+    x, offs, mns, mxs = make_segments(L, R, mn, dist, seeds)
+    out = torch.empty_like(x)
+    plan = rtcdf.BatchPlan(offs, mns, mxs)
+    wsb = plan.workspace_size()
+    ws = torch.zeros(wsb // 4 + 64, dtype=torch.int32, device="cuda")
+    st = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=st):
+        assert plan.run(x.data_ptr(), out.data_ptr(), ws.data_ptr(), wsb, st.cuda_stream) == 0
+    for _ in range(2):
+        out.fill_(-1)
+        torch.cuda.synchronize()
+        g.replay()
+        torch.cuda.synchronize()
+    assert rtcdf.rtcdf_batch_status_get(ws.data_ptr(), st.cuda_stream) == (rtcdf.OK, 0)
+    check_segments(x, out, offs, mns, mxs)

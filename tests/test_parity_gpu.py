@@ -299,3 +299,21 @@ def test_large_n1e9(R, dist):
     torch.cuda.empty_cache()
     ok, bad = oracle.check_sorted(a, b, 0, R)
     assert ok, f"first bad position {bad}"
+
+
+def test_largest_n_accepted():
+    """n = 2^32 - 1, the largest length the ABI accepts (32-bit counts and
+    positions): 17 GB in, 17 GB out, checked with the oracle's Lemma-3 checker;
+    n = 2^32 is refused on the host."""
+    n = (1 << 32) - 1
+    R = 1 << 12
+    x = dev_keys(n, -9, R, gen.UNIFORM, gen.derive_seed(4, 32))
+    out = gpu_sort(x, -9, -9 + R)
+    a = x.cpu().numpy()
+    b = out.cpu().numpy()
+    assert rtcdf.rtcdf_sort(x.data_ptr(), out.data_ptr(), n + 1, -9, -9 + R,
+                            stream_handle()) == rtcdf.ERR_INVALID_ARG
+    del x, out
+    torch.cuda.empty_cache()
+    ok, bad = oracle.check_sorted(a, b, -9, -9 + R)
+    assert ok, f"first bad position {bad}"

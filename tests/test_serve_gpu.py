@@ -95,3 +95,26 @@ def test_one_large_launch_at_a_time_still_matches():
     assert st.launches_single > 0
     for i in range(count):
         assert res[i].status == 0 and res[i].digest == alone[i].digest, i
+
+
+def test_benchmark_serving_trace_all_requests():
+    """The benchmark's serving workload (20000 requests, n log-uniform in
+    [1e4, 1e8], R log-uniform in [2^7, 2^18], 32 GB budget, Poisson arrivals):
+    every request's digest served in the mix equals its digest served alone,
+    and a seeded sample of requests matches the oracle."""
+    count = 20000
+    seed = gen.derive_seed(5)
+    n, mn, R, dist, seeds = gen.serving_requests(seed, count)
+    arr = gen.poisson_arrivals(seed, count, 13000.0)
+    reqs = rtcdf.make_requests(n, mn, mn + R, dist, seeds, arr)
+    cfg = rtcdf.ServerConfig(budget_bytes=32 << 30, num_streams=4, max_batch=256,
+                             single_min_keys=1 << 22, fill=gen.fill_function_address(), digests=1)
+    mix, st = rtcdf.rtcdf_serve_trace(cfg, reqs, count)
+    alone, _ = rtcdf.rtcdf_serve_sequential(cfg, reqs, count)
+    assert st.launches_batched > 0 and st.launches_single > 0
+    bad = [i for i in range(count) if mix[i].status != 0 or mix[i].digest != alone[i].digest]
+    assert not bad, f"{len(bad)} requests differ, first {bad[:5]}"
+    rng = np.random.default_rng(7)
+    small = np.nonzero(n <= 2_000_000)[0]
+    for i in rng.choice(small, size=min(40, small.size), replace=False):
+        assert mix[i].digest == oracle_digest(n[i], mn[i], R[i], dist[i], seeds[i]), i
