@@ -18,7 +18,7 @@ struct rtcdf_batch_plan {
     int device = 0;
     int workers = 0;
     uint32_t num_segs = 0, num_items = 0;
-    uint32_t n_first = 0, n_scan = 0, n_fill = 0;
+    uint32_t n_first = 0, n_scan = 0, n_small2 = 0, n_fill = 0;
     uint64_t total_keys = 0;
     size_t ws_bytes = 0;          // caller workspace needed
     size_t ctl_off = 0, segctl_off = 0;
@@ -99,6 +99,14 @@ int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P, const BatchTun
     };
     std::stable_sort(large_ids.begin(), large_ids.end(), by_size);
     std::stable_sort(small_ids.begin(), small_ids.end(), by_size);
+    // In-CTA segments with a narrow range run in the scan launch (256-thread
+    // CTAs); the others in the first launch.
+    std::vector<uint32_t> small2_ids;
+    {
+        std::vector<uint32_t> keep;
+        for (uint32_t s : small_ids) (segs[s].R <= kSmallInScanMaxR ? small2_ids : keep).push_back(s);
+        small_ids.swap(keep);
+    }
     std::vector<BatchItem> &Q = P->items;
     // First launch: histogram items (largest segments first) with the in-CTA
     // segments (largest first) spread among them in proportion to their keys,
@@ -137,6 +145,8 @@ int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P, const BatchTun
     for (uint32_t s : by_chunks)
         for (uint32_t c = 0; c < segs[s].scan_chunks; c++) Q.push_back(BatchItem{kItemScan, s, c, 0, 0, 0});
     P->n_scan = (uint32_t)Q.size() - P->n_first;
+    for (uint32_t s : small2_ids) Q.push_back(BatchItem{kItemSmall, s, 0, 0, 0, 0});
+    P->n_small2 = (uint32_t)small2_ids.size();
     // Output launch.
     for (uint32_t s : large_ids) {
         const BatchSeg &g = segs[s];
@@ -144,7 +154,7 @@ int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P, const BatchTun
             Q.push_back(BatchItem{kItemFill, s, (uint64_t)f * g.fill_chunk,
                                   std::min<uint64_t>(g.n, (uint64_t)(f + 1) * g.fill_chunk), 0, f});
     }
-    P->n_fill = (uint32_t)Q.size() - P->n_first - P->n_scan;
+    P->n_fill = (uint32_t)Q.size() - P->n_first - P->n_scan - P->n_small2;
     return 0;
 }
 
@@ -200,6 +210,7 @@ rtcdf_status rtcdf_batch_plan_create_ex(const int64_t *seg_offsets, const int64_
     p->num_items = (uint32_t)hp.items.size();
     p->n_first = hp.n_first;
     p->n_scan = hp.n_scan;
+    p->n_small2 = hp.n_small2;
     p->n_fill = hp.n_fill;
     p->total_keys = hp.total_keys;
     p->ws_bytes = hp.ws_words * 4;
@@ -286,6 +297,7 @@ rtcdf_status rtcdf_sort_batched_profiled(const rtcdf_batch_plan *plan, const int
     a.items = plan->d_items;
     a.n_first = plan->n_first;
     a.n_scan = plan->n_scan;
+    a.n_small2 = plan->n_small2;
     a.n_fill = plan->n_fill;
     a.num_segs = plan->num_segs;
     a.ws_u32 = ws;

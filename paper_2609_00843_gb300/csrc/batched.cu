@@ -123,11 +123,12 @@ __device__ __forceinline__ void count_key_pred(uint32_t s_base, uint32_t y, uint
 // One segment, n < 65536 keys, R <= kBatchSmallMaxR values, in one CTA.
 // Counters: W = ceil(R / 2) words; value v < W counts in the low half of word
 // v, value v >= W in the high half of word v - W.
-__device__ void do_small(const BatchArgs &a, const BatchSeg &g, uint32_t *sm) {
+// `sm` holds the counters (ceil(R / 2) words), `s_tmp` the block scan's
+// scratch (blockDim / 32 + 1 words).
+__device__ void do_small(const BatchArgs &a, const BatchSeg &g, uint32_t *sm, uint32_t *s_tmp) {
     const uint32_t R = g.R, n = g.n, nt = blockDim.x, tid = threadIdx.x;
     const uint32_t W = (R + 1) / 2;
     uint32_t *cnt = sm;
-    uint32_t *s_tmp = sm + kBatchSmallMaxR / 2;  // scan scratch
     for (uint32_t i = tid; i < W; i += nt) cnt[i] = 0;
     __syncthreads();
     const int32_t *in = a.in + g.off;
@@ -301,7 +302,7 @@ __global__ void __launch_bounds__(kSegThreads, 2) seg_first_kernel(BatchArgs a) 
     const unsigned long long t0 = (a.prof && threadIdx.x == 0) ? global_ns() : 0ull;
     const BatchItem it = a.items[blockIdx.x];
     const BatchSeg g = a.segs[it.seg];
-    if (it.kind == kItemSmall) do_small(a, g, sm);
+    if (it.kind == kItemSmall) do_small(a, g, sm, sm + kBatchSmallMaxR / 2);
     else do_hist(a, g, it, sm);
     if (a.prof) {
         __syncthreads();
@@ -320,10 +321,25 @@ __global__ void __launch_bounds__(kScanCtaThreads) seg_scan_kernel(BatchArgs a) 
     __shared__ uint64_t s_warp[kScanCtaThreads / 32];
     __shared__ uint64_t s_prefix;
     __shared__ unsigned long long s_wait;
-    __shared__ uint32_t s_cdf[kBatchScanChunk];
-    __shared__ uint32_t s_runs[kBatchScanChunk];
+    __shared__ uint32_t s_buf[2 * kBatchScanChunk];
+    uint32_t *s_cdf = s_buf, *s_runs = s_buf + kBatchScanChunk;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int kWarps = kScanCtaThreads / 32;
+    // The in-CTA segments come first in the grid (dispatched first; spreading
+    // them among the scan chunks was measured slower).
+    if (blockIdx.x < a.n_small2) {
+        // An in-CTA segment: independent of the first launch, so no wait.
+        asm volatile("griddepcontrol.launch_dependents;");
+        const unsigned long long ts = (a.prof && tid == 0) ? global_ns() : 0ull;
+        const BatchItem it = a.items[a.n_first + a.n_scan + blockIdx.x];
+        const BatchSeg g = a.segs[it.seg];
+        do_small(a, g, s_buf, s_buf + 2 * kBatchScanChunk - 64);
+        if (a.prof) {
+            __syncthreads();
+            if (tid == 0) prof_item(a, kItemSmall, ts, 0);
+        }
+        return;
+    }
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
     const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
@@ -462,7 +478,7 @@ __global__ void __launch_bounds__(kFillCtaThreads) seg_fill_kernel(BatchArgs a) 
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
     if (blockIdx.x == 0 && tid == 0) a.ctl->scan_ticket = 0;
-    const BatchItem it = a.items[a.n_first + a.n_scan + blockIdx.x];
+    const BatchItem it = a.items[a.n_first + a.n_scan + a.n_small2 + blockIdx.x];
     const BatchSeg g = a.segs[it.seg];
     if (it.aux == 0 && g.scan_chunks > 1) {
         // The segment's first output item leaves its lookback state zeroed.
@@ -571,8 +587,9 @@ cudaError_t launch_batched(const BatchArgs &a, cudaStream_t s) {
         seg_first_kernel<<<a.n_first, kSegThreads, kSegSmemBytes, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if (a.n_scan &&
-        (e = launch_pdl((const void *)seg_scan_kernel, a.n_scan, kScanCtaThreads, a, s)) != cudaSuccess)
+    if (a.n_scan + a.n_small2 &&
+        (e = launch_pdl((const void *)seg_scan_kernel, a.n_scan + a.n_small2, kScanCtaThreads, a, s)) !=
+            cudaSuccess)
         return e;
     if (a.n_fill &&
         (e = launch_pdl((const void *)seg_fill_kernel, a.n_fill, kFillCtaThreads, a, s)) != cudaSuccess)

@@ -11,7 +11,10 @@ namespace rtcdf {
 //   1. histogram items of the large segments and whole in-CTA sorts of the
 //      small ones (1024 threads, 112 KB of shared memory each, two per SM);
 //   2. local CDFs + offsets: one 256-thread CTA per 4096-bin chunk of a large
-//      segment's histogram, chained within the segment by a decoupled lookback;
+//      segment's histogram, chained within the segment by a decoupled lookback,
+//      plus the in-CTA sorts of the small segments with R <= kSmallInScanMaxR
+//      (these do not wait for the first launch, so they overlap its tail and
+//      the latency-bound scan chunks);
 //   3. output items of the large segments (512-thread CTAs).
 constexpr int kSegThreads = 1024;
 constexpr size_t kSegSmemBytes = 112 * 1024;          // first launch, per CTA
@@ -20,6 +23,7 @@ constexpr uint32_t kBatchSmallMaxR = 55296;           // 16-bit counters in 108 
 constexpr uint32_t kBatchTileMax = 28672;             // 32-bit tile histogram in 112 KB
 constexpr uint32_t kBatchScanChunk = 4096;            // bins per scan CTA (4 per thread)
 constexpr uint32_t kSegFillRuns = 4096;               // run window of an output CTA
+constexpr uint32_t kSmallInScanMaxR = 16000;          // in-CTA segments run by scan-launch CTAs
 constexpr uint64_t kBatchMaxR = 1ull << 20;
 
 enum : uint32_t { kItemHist = 0, kItemSmall = 1, kItemScan = 2, kItemFill = 3 };
@@ -60,8 +64,9 @@ struct BatchArgs {
     const int32_t *in;
     int32_t *out;
     const BatchSeg *segs;
-    const BatchItem *items;          // [first launch | scan launch | output launch]
-    uint32_t n_first, n_scan, n_fill;
+    const BatchItem *items;          // [first launch | scan chunks | in-CTA segments of the
+                                     //  scan launch | output launch]
+    uint32_t n_first, n_scan, n_small2, n_fill;
     uint32_t num_segs;
     uint32_t *ws_u32;                // workspace base
     BatchCtl *ctl;
@@ -81,8 +86,9 @@ struct SegSpec {
 };
 struct HostPlan {
     std::vector<BatchSeg> segs;
-    std::vector<BatchItem> items;    // [first launch | scan launch | output launch]
-    uint32_t n_first = 0, n_scan = 0, n_fill = 0;
+    std::vector<BatchItem> items;    // [first launch | scan chunks | in-CTA segments of the
+                                     //  scan launch | output launch]
+    uint32_t n_first = 0, n_scan = 0, n_small2 = 0, n_fill = 0;
     size_t ws_words = 0, ctl_off = 0, segctl_off = 0;
     uint32_t small_segs = 0, large_segs = 0;
     uint64_t total_keys = 0;

@@ -322,6 +322,7 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
                 a.items = reinterpret_cast<const BatchItem *>(tab + seg_b);
                 a.n_first = hp.n_first;
                 a.n_scan = hp.n_scan;
+                a.n_small2 = hp.n_small2;
                 a.n_fill = hp.n_fill;
                 a.num_segs = (uint32_t)hp.segs.size();
                 a.ws_u32 = ws;

@@ -26,14 +26,16 @@ static int check(const std::vector<SegSpec> &spec, const BatchTuning &tun) {
     HostPlan P;
     if (build_host_plan(spec.data(), (uint32_t)spec.size(), &P, tun)) return fail("plan rejected", 0, 0);
     const uint32_t S = (uint32_t)spec.size();
-    if ((size_t)P.n_first + P.n_scan + P.n_fill != P.items.size()) return fail("launch sizes", 0, 0);
+    if ((size_t)P.n_first + P.n_scan + P.n_small2 + P.n_fill != P.items.size()) return fail("launch sizes", 0, 0);
     std::vector<uint32_t> small_seen(S, 0), next_chunk(S, 0);
     std::vector<std::vector<std::pair<uint64_t, uint64_t>>> hist_rng(S), fill_rng(S);
     for (size_t q = 0; q < P.items.size(); q++) {
         const BatchItem &it = P.items[q];
         if (it.seg >= S) return fail("segment index", (long)q, it.seg);
         const BatchSeg &g = P.segs[it.seg];
-        const int launch = q < P.n_first ? 0 : (q < (size_t)P.n_first + P.n_scan ? 1 : 2);
+        // 0: first launch, 1: scan chunks, 3: in-CTA segments of the scan launch, 2: output launch
+        const size_t e1 = (size_t)P.n_first + P.n_scan, e3 = e1 + P.n_small2;
+        const int launch = q < P.n_first ? 0 : (q < e1 ? 1 : (q < e3 ? 3 : 2));
         switch (it.kind) {
             case kItemHist:
                 if (launch != 0) return fail("hist outside the first launch", (long)q, launch);
@@ -41,7 +43,8 @@ static int check(const std::vector<SegSpec> &spec, const BatchTuning &tun) {
                 hist_rng[it.seg].push_back({it.a * 1024 + it.tile, it.b});
                 break;
             case kItemSmall:
-                if (launch != 0) return fail("small outside the first launch", (long)q, launch);
+                if (launch != 0 && launch != 3) return fail("small in a wrong launch", (long)q, launch);
+                if ((launch == 3) != (g.R <= kSmallInScanMaxR)) return fail("small launch by range", (long)q, g.R);
                 small_seen[it.seg]++;
                 break;
             case kItemScan:
