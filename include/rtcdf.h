@@ -90,8 +90,11 @@ rtcdf_status rtcdf_workspace_size(int64_t R, size_t *bytes);
  * rtcdf_sort_ws -- rtcdf_sort with a caller-owned device workspace of
  * `ws_bytes` >= rtcdf_workspace_size(R).  No allocation happens inside, so the
  * call can be captured in a CUDA graph.  The workspace must be zero-filled
- * before its first use (cudaMemsetAsync(workspace, 0, ws_bytes, stream));
- * every call leaves it zero-filled again except for the status word.  Calls
+ * before its first use (cudaMemsetAsync(workspace, 0, ws_bytes, stream)).
+ * Every call leaves the parts that must start at zero (control block, lookback
+ * state, histogram) zeroed again -- the run tables it also holds are written
+ * before they are read -- so one workspace serves any sequence of sorts whose
+ * ranges it is large enough for; the status word is sticky until read.  Calls
  * that share one workspace must be ordered (same stream or events).
  */
 rtcdf_status rtcdf_sort_ws(const int32_t *in, int32_t *out, uint64_t n, int64_t minVal,
@@ -175,8 +178,8 @@ rtcdf_status rtcdf_tune_get(rtcdf_tune_entry *entries, int32_t capacity, int32_t
  * mean of r over all conditions wins.
  *
  * cases[i].in / .out are device arrays of .n keys in [.minVal, .maxVal);
- * `workspace` (256-byte aligned, zero-filled before first use, left zero-
- * filled) holds at least rtcdf_workspace_size(max R) bytes.  Host outputs:
+ * `workspace` (256-byte aligned, zero-filled before first use, then kept as
+ * rtcdf_sort_ws keeps it) holds at least rtcdf_workspace_size(max R) bytes.  Host outputs:
  * times_ms[c * num_candidates + k] (median ms; -1 if candidate k cannot run
  * case c on this device), geomean[k] (HUGE_VAL for a candidate that cannot
  * run every case), *best.  Synchronises `stream`; not capturable.  Returns
@@ -256,9 +259,12 @@ rtcdf_status rtcdf_sort_host(const int32_t *in, int32_t *out, uint64_t n, int64_
  * uploads it (this allocates and synchronises; do it once per segment layout).
  * rtcdf_sort_batched_ws then runs it with no host work and no allocation
  * (capturable in a CUDA graph; replay with new keys of the same shapes); its
- * workspace (rtcdf_batch_workspace_size bytes, 256-byte aligned) must be
- * zero-filled before first use and is left zero-filled except for the status
- * word, read with rtcdf_batch_status_get.  rtcdf_sort_batched is the one-shot
+ * workspace (rtcdf_batch_workspace_size bytes, 256-byte aligned) belongs to
+ * one plan: zero-fill it before its first use with that plan; every run leaves
+ * the parts that must start at zero (histograms, lookback state, control
+ * block) zeroed again, so the plan can be replayed on it, but its other parts
+ * hold per-run tables, so zero-fill it again before using it with another
+ * plan.  The status word is sticky until read with rtcdf_batch_status_get.  rtcdf_sort_batched is the one-shot
  * form: plan, allocate, run, read the status, free -- it synchronises.
  */
 typedef struct rtcdf_batch_plan rtcdf_batch_plan;
