@@ -6,8 +6,8 @@
 // in place are launched as soon as one of `num_streams` streams is free:
 // requests with at least `single_min_keys` keys alone, through the single-array
 // pipeline (Algorithms 4-7, three kernels); all other pending requests together,
-// as one persistent segmented launch (a lone small request, under light load,
-// also takes the single-array pipeline).  New arrivals keep being admitted while
+// as one segmented sort (its three launches; a lone small request, under light
+// load, also takes the single-array pipeline).  New arrivals keep being admitted while
 // earlier launches run, launches on different streams overlap on the device,
 // and a request's slot is released as soon as its launch completes.  Results
 // stay on the device; an optional order-dependent digest of each sorted output
@@ -253,9 +253,8 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
             }
             const double launch_t = secs(t0);
             // A lone request (large, or small with nothing to batch it with --
-            // light load) goes through the single-array pipeline: three short
-            // kernels cost less than a persistent launch over one segment plus
-            // its table upload.
+            // light load) goes through the single-array pipeline, which needs
+            // no table upload.
             const bool single = L.reqs.size() == 1;
             // One slab region per launch, released when it completes:
             // [segment table | work items | digest table | batch workspace].
