@@ -325,6 +325,13 @@ rtcdf_status rtcdf_sort_batched_profiled(const rtcdf_batch_plan *plan, const int
 rtcdf_status rtcdf_sort_batched(const int32_t *in, int32_t *out, const int64_t *seg_offsets,
                                 const int64_t *seg_minVal, const int64_t *seg_maxVal,
                                 int32_t num_segments, rtcdf_stream_t stream);
+/* rtcdf_sort_batched with the segment metadata (the same three arrays) in
+ * DEVICE memory, e.g. produced by earlier kernels on `stream`: they are copied
+ * to the host after that work (the plan is built on the host), then the call
+ * proceeds as rtcdf_sort_batched.  Synchronises `stream`. */
+rtcdf_status rtcdf_sort_batched_device(const int32_t *in, int32_t *out, const int64_t *d_seg_offsets,
+                                       const int64_t *d_seg_minVal, const int64_t *d_seg_maxVal,
+                                       int32_t num_segments, rtcdf_stream_t stream);
 
 /*
  * Continuous-batching server.  A trace of sort requests (arrival times

@@ -346,4 +346,23 @@ rtcdf_status rtcdf_sort_batched(const int32_t *in, int32_t *out, const int64_t *
     return st ? st : dst;
 }
 
+rtcdf_status rtcdf_sort_batched_device(const int32_t *in, int32_t *out, const int64_t *d_seg_offsets,
+                                       const int64_t *d_seg_minVal, const int64_t *d_seg_maxVal,
+                                       int32_t num_segments, rtcdf_stream_t stream) {
+    if (num_segments < 0) return RTCDF_ERR_INVALID_ARG;
+    if (num_segments > 0 && (!d_seg_offsets || !d_seg_minVal || !d_seg_maxVal)) return RTCDF_ERR_INVALID_ARG;
+    const size_t S = (size_t)num_segments;
+    std::vector<int64_t> offs(S + 1, 0), mn(S), mx(S);
+    cudaStream_t s = (cudaStream_t)stream;
+    // The plan is built on the host: bring the metadata over (ordered after
+    // the work on `stream` that produced it).
+    if (S > 0 &&
+        (cudaMemcpyAsync(offs.data(), d_seg_offsets, (S + 1) * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaMemcpyAsync(mn.data(), d_seg_minVal, S * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaMemcpyAsync(mx.data(), d_seg_maxVal, S * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+         cudaStreamSynchronize(s) != cudaSuccess))
+        return RTCDF_ERR_CUDA;
+    return rtcdf_sort_batched(in, out, offs.data(), mn.data(), mx.data(), num_segments, stream);
+}
+
 }  // extern "C"

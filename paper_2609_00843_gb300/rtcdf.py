@@ -141,6 +141,8 @@ def lib():
             L.rtcdf_sort_batched_profiled.argtypes = [vp, vp, vp, vp, sz, vp, vp]
             L.rtcdf_sort_batched_profiled.restype = ctypes.c_int
             L.rtcdf_sort_batched.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+            L.rtcdf_sort_batched_device.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+            L.rtcdf_sort_batched_device.restype = ctypes.c_int
             L.rtcdf_tune_n_class.argtypes = [u64]
             L.rtcdf_tune_n_class.restype = i32
             L.rtcdf_tune_set.argtypes = [ctypes.POINTER(TuneEntry), i32]
@@ -280,6 +282,13 @@ def rtcdf_sort_batched(in_ptr: int, out_ptr: int, seg_offsets, seg_minVal, seg_m
     mn, mnp = _i64_array(seg_minVal)
     mx, mxp = _i64_array(seg_maxVal)
     return lib().rtcdf_sort_batched(in_ptr, out_ptr, op, mnp, mxp, len(mn), stream)
+
+
+def rtcdf_sort_batched_device(in_ptr: int, out_ptr: int, d_offsets_ptr: int, d_min_ptr: int,
+                              d_max_ptr: int, num_segments: int, stream: int = 0) -> int:
+    """rtcdf_sort_batched with int64 segment metadata in device memory."""
+    return lib().rtcdf_sort_batched_device(in_ptr, out_ptr, d_offsets_ptr, d_min_ptr, d_max_ptr,
+                                           num_segments, stream)
 
 
 def make_requests(n, minVal, maxVal, dist, seed, arrival_s):
