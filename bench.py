@@ -751,21 +751,6 @@ def main():
         "timed_region_ms": round(total_ms, 3),
     }
 
-    # On-GPU comparison: CUB DeviceRadixSort restricted to bits [0, ceil(log2 R))
-    # on keys normalised to uint32 (normalise / denormalise timed apart).
-    if not args.no_cub and rank == 0:
-        line["cub_comparison"] = cub_comparison(cases, ins, outs, n, stream, nsteps, solo_ms)
-
-    if not args.no_single and rank == 0:
-        line["single"] = single_config(stream)
-
-    if not args.no_batched and rank == 0:
-        line["batched"] = batched_comparison(args, stream, args.batched_segments)
-
-    if not args.no_serve and rank == 0:
-        line["serve"] = serving_comparison(args.serve_requests)
-
-
     # End to end through the C ABI with host buffers (rtcdf_sort_host): pinned
     # host input -> chunked upload overlapped with the histogram -> scan and
     # output -> download overlapped with the next array's upload -> host.
@@ -824,6 +809,21 @@ def main():
         line["e2e"]["frac_of_link_bound"] = round(e_val / world / bound, 4)
         del d_tmp
         del pin_in, pin_out
+
+    # On-GPU comparison: CUB DeviceRadixSort restricted to bits [0, ceil(log2 R))
+    # on keys normalised to uint32 (normalise / denormalise timed apart).
+    if not args.no_cub and rank == 0:
+        line["cub_comparison"] = cub_comparison(cases, ins, outs, n, stream, nsteps, solo_ms)
+
+    if not args.no_single and rank == 0:
+        line["single"] = single_config(stream)
+
+    if not args.no_batched and rank == 0:
+        line["batched"] = batched_comparison(args, stream, args.batched_segments)
+
+    if not args.no_serve and rank == 0:
+        line["serve"] = serving_comparison(args.serve_requests)
+
 
     if rank == 0 and not args.no_cpu_baseline:
         host = [x.cpu().numpy() for x in ins]
