@@ -104,8 +104,10 @@ rtcdf_status rtcdf_sort_ws(const int32_t *in, int32_t *out, uint64_t n, int64_t 
 /*
  * rtcdf_status_get -- wait for `stream`, then return in *device_status the
  * RTCDF_DEV_* bits recorded by sorts on the library-owned workspace of
- * `stream` since the last read, and clear them.  Returns
- * RTCDF_ERR_KEY_OUT_OF_RANGE / RTCDF_ERR_TIMEOUT when a bit is set.
+ * `stream` since the last read, and clear them.  Returns RTCDF_ERR_TIMEOUT
+ * when a bounded wait ran out (checked first: the other findings of that sort
+ * are then unreliable), else RTCDF_ERR_KEY_OUT_OF_RANGE when a key lay
+ * outside its range.
  */
 rtcdf_status rtcdf_status_get(rtcdf_stream_t stream, int32_t *device_status);
 

@@ -317,8 +317,9 @@ rtcdf_status rtcdf_batch_status_get(void *workspace, rtcdf_stream_t stream, int3
     if (cudaMemsetAsync(&ctl->status, 0, 4, (cudaStream_t)stream) != cudaSuccess) return RTCDF_ERR_CUDA;
     if (cudaStreamSynchronize((cudaStream_t)stream) != cudaSuccess) return RTCDF_ERR_CUDA;
     if (device_status) *device_status = (int32_t)v;
-    if (v & kDevKeyOutOfRange) return RTCDF_ERR_KEY_OUT_OF_RANGE;
+    // A wait that ran out makes every other finding unreliable: report it first.
     if (v & kDevTimeout) return RTCDF_ERR_TIMEOUT;
+    if (v & kDevKeyOutOfRange) return RTCDF_ERR_KEY_OUT_OF_RANGE;
     return RTCDF_OK;
 }
 

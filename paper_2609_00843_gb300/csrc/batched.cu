@@ -345,6 +345,7 @@ __global__ void __launch_bounds__(kScanCtaThreads) seg_scan_kernel(BatchArgs a) 
     const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
     if (tid == 0) s_ticket = atomicAdd(&a.ctl->scan_ticket, 1u);
     __syncthreads();
+    if (s_ticket >= a.n_scan) return;  // only with a workspace whose ticket was not zero
     const BatchItem it = a.items[a.n_first + s_ticket];
     const BatchSeg g = a.segs[it.seg];
     const uint32_t chunk = (uint32_t)it.a;

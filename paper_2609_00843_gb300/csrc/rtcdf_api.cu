@@ -273,8 +273,9 @@ rtcdf_status read_status(void *ws, cudaStream_t s, int32_t *out) {
     if (cudaMemsetAsync(&ctl->status, 0, 4, s) != cudaSuccess) return RTCDF_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return RTCDF_ERR_CUDA;
     if (out) *out = (int32_t)v;
-    if (v & kDevKeyOutOfRange) return RTCDF_ERR_KEY_OUT_OF_RANGE;
+    // A wait that ran out makes every other finding unreliable: report it first.
     if (v & kDevTimeout) return RTCDF_ERR_TIMEOUT;
+    if (v & kDevKeyOutOfRange) return RTCDF_ERR_KEY_OUT_OF_RANGE;
     return RTCDF_OK;
 }
 

@@ -111,6 +111,11 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs a) {
         __syncthreads();
     }
     const uint32_t chunk = single ? 0u : s_chunk;
+    // A ticket past the last chunk only happens with a workspace whose ticket
+    // was not zero (not cleared, or shared by unordered calls): take no chunk.
+    // The chunk that ticket stood for is then never published, and the
+    // lookback of its successor runs out and records kDevTimeout.
+    if (chunk >= a.chunks) return;
     const uint32_t cbase = chunk * kScanChunk;
     const uint32_t base = cbase + tid * kScanItems;
 

@@ -317,3 +317,28 @@ def test_largest_n_accepted():
     torch.cuda.empty_cache()
     ok, bad = oracle.check_sorted(a, b, -9, -9 + R)
     assert ok, f"first bad position {bad}"
+
+
+def test_bounded_wait_runs_out_and_reports_timeout():
+    """Failure detection without a GPU fault: a workspace whose scan ticket is
+    not zero makes one lookback chunk go unpublished; its successor's bounded
+    wait runs out, the sort returns, the device status says TIMEOUT, and the
+    context stays usable (the next sort on a cleared workspace is exact)."""
+    R, n = 1 << 14, 200_000                      # four scan chunks
+    x = dev_keys(n, 0, R, gen.UNIFORM, gen.derive_seed(80))
+    out = torch.empty_like(x)
+    wsb = rtcdf.rtcdf_workspace_size(R)
+    ws = torch.zeros(wsb // 4 + 64, dtype=torch.int32, device="cuda")
+    ws[1] = 1                                    # control block word 1: the scan ticket
+    s = stream_handle()
+    p = rtcdf.Params(hist_threads=1024)
+    rc = rtcdf.rtcdf_sort_ex(x.data_ptr(), out.data_ptr(), n, 0, R, p, ws.data_ptr(), wsb, None, s)
+    assert rc == rtcdf.OK
+    rc, bits = rtcdf.rtcdf_ws_status_get(ws.data_ptr(), s)
+    assert rc == rtcdf.ERR_TIMEOUT and bits & rtcdf.DEV_TIMEOUT, (rc, bits)
+    ws.zero_()
+    out.fill_(0)
+    rc = rtcdf.rtcdf_sort_ex(x.data_ptr(), out.data_ptr(), n, 0, R, p, ws.data_ptr(), wsb, None, s)
+    assert rc == rtcdf.OK
+    assert rtcdf.rtcdf_ws_status_get(ws.data_ptr(), s) == (rtcdf.OK, 0)
+    assert_matches_oracle(x, out, 0, R)
