@@ -290,7 +290,10 @@ typedef struct {
     int32_t hist_chunk;   /* keys per histogram item of a large segment (>= 4096; default 524288) */
     int32_t fill_chunk;   /* output positions per output item (>= 4096; default 65536) */
     int32_t small_max_n;  /* longest segment sorted inside one CTA (<= 65535; default 65535) */
-    int32_t reserved[5];
+    int32_t small_scan_max_R; /* in-CTA segments with R up to this are sorted by 256-thread CTAs
+                                 of the scan launch, wider ones by 1024-thread CTAs of the first
+                                 launch (1 .. 16768; default 16000) */
+    int32_t reserved[4];
 } rtcdf_batch_params;
 
 /* rtcdf_batch_plan_create with explicit work-item sizes (`params` may be NULL). */

@@ -104,7 +104,7 @@ int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P, const BatchTun
     std::vector<uint32_t> small2_ids;
     {
         std::vector<uint32_t> keep;
-        for (uint32_t s : small_ids) (segs[s].R <= kSmallInScanMaxR ? small2_ids : keep).push_back(s);
+        for (uint32_t s : small_ids) (segs[s].R <= tun.small_scan_max_R ? small2_ids : keep).push_back(s);
         small_ids.swap(keep);
     }
     std::vector<BatchItem> &Q = P->items;
@@ -178,11 +178,13 @@ rtcdf_status rtcdf_batch_plan_create_ex(const int64_t *seg_offsets, const int64_
     if (params) {
         if (params->hist_chunk < 0 || (params->hist_chunk > 0 && params->hist_chunk < 4096) ||
             params->fill_chunk < 0 || (params->fill_chunk > 0 && params->fill_chunk < 4096) ||
-            params->small_max_n < 0 || params->small_max_n > (int32_t)kBatchSmallMaxN)
+            params->small_max_n < 0 || params->small_max_n > (int32_t)kBatchSmallMaxN ||
+            params->small_scan_max_R < 0 || params->small_scan_max_R > (int32_t)kSmallInScanCapR)
             return RTCDF_ERR_INVALID_ARG;
         if (params->hist_chunk) tun.hist_chunk = (uint64_t)params->hist_chunk;
         if (params->fill_chunk) tun.fill_chunk = (uint32_t)params->fill_chunk;
         if (params->small_max_n) tun.small_max_n = (uint32_t)params->small_max_n;
+        if (params->small_scan_max_R) tun.small_scan_max_R = (uint32_t)params->small_scan_max_R;
     }
     *plan_out = nullptr;
     if (num_segments > 0 && (!seg_offsets || !seg_minVal || !seg_maxVal)) return RTCDF_ERR_INVALID_ARG;

@@ -121,13 +121,15 @@ __device__ __forceinline__ void count_key_pred(uint32_t s_base, uint32_t y, uint
 
 // ---------------------------------------------------------------- SMALL
 // One segment, n < 65536 keys, R <= kBatchSmallMaxR values, in one CTA.
-// Counters: W = ceil(R / 2) words; value v < W counts in the low half of word
-// v, value v >= W in the high half of word v - W.
-// `sm` holds the counters (ceil(R / 2) words), `s_tmp` the block scan's
-// scratch (blockDim / 32 + 1 words).
-__device__ void do_small(const BatchArgs &a, const BatchSeg &g, uint32_t *sm, uint32_t *s_tmp) {
+// WIDE: one 32-bit counter per value (R words).  Otherwise 16-bit counters,
+// W = ceil(R / 2) words: value v < W counts in the low half of word v, value
+// v >= W in the high half of word v - W.
+// `sm` holds the counters, `s_tmp` the block scan's scratch (blockDim / 32 + 1
+// words).
+template <bool WIDE>
+__device__ void do_small_impl(const BatchArgs &a, const BatchSeg &g, uint32_t *sm, uint32_t *s_tmp) {
     const uint32_t R = g.R, n = g.n, nt = blockDim.x, tid = threadIdx.x;
-    const uint32_t W = (R + 1) / 2;
+    const uint32_t W = WIDE ? R : (R + 1) / 2;
     uint32_t *cnt = sm;
     for (uint32_t i = tid; i < W; i += nt) cnt[i] = 0;
     __syncthreads();
@@ -136,10 +138,14 @@ __device__ void do_small(const BatchArgs &a, const BatchSeg &g, uint32_t *sm, ui
     const uint32_t s_base = (uint32_t)__cvta_generic_to_shared(cnt);
     auto count1 = [&](int32_t key) {
         const uint32_t x = (uint32_t)key - min_u;
-        const bool lo = x < W, hi = !lo && x < R;
-        const uint32_t wv = lo ? x : x - W;
-        red_lo(s_base + 4u * wv, lo);
-        red_hi(s_base + 4u * wv, hi);
+        if (WIDE) {
+            count_key_pred(s_base, x, R);
+        } else {
+            const bool lo = x < W, hi = !lo && x < R;
+            const uint32_t wv = lo ? x : x - W;
+            red_lo(s_base + 4u * wv, lo);
+            red_hi(s_base + 4u * wv, hi);
+        }
     };
     const uint32_t lead_a = (uint32_t)(((16 - ((uintptr_t)in & 15)) & 15) / 4);
     const uint32_t lead = lead_a < n ? lead_a : n;
@@ -160,19 +166,25 @@ __device__ void do_small(const BatchArgs &a, const BatchSeg &g, uint32_t *sm, ui
     if (tid < lead) count1(in[tid]);
     for (uint32_t i = lead + 4 * nv + tid; i < n; i += nt) count1(in[i]);
     __syncthreads();
-    // In-place inclusive CDF over the 16-bit counters (values <= n < 2^16).
+    // In-place inclusive CDF over the counters (values <= n < 2^16).  Each
+    // thread takes an odd number of consecutive values, so that the 32 lanes
+    // of a warp step through 32 distinct banks.
     uint16_t *c16 = reinterpret_cast<uint16_t *>(cnt);
     auto slot = [&](uint32_t v) -> uint32_t { return v < W ? 2u * v : 2u * (v - W) + 1u; };
-    const uint32_t per = (R + nt - 1) / nt;
+    auto get = [&](uint32_t v) -> uint32_t { return WIDE ? cnt[v] : (uint32_t)c16[slot(v)]; };
+    auto put = [&](uint32_t v, uint32_t x) {
+        if (WIDE) cnt[v] = x; else c16[slot(v)] = (uint16_t)x;
+    };
+    const uint32_t per = ((R + nt - 1) / nt) | 1u;
     const uint32_t b0 = min(R, tid * per), b1 = min(R, b0 + per);
     uint32_t local = 0;
-    for (uint32_t v = b0; v < b1; v++) local += c16[slot(v)];
+    for (uint32_t v = b0; v < b1; v++) local += get(v);
     uint32_t total = 0;
     const uint32_t ex = block_excl_scan_u32(local, s_tmp, &total);
     uint32_t run = ex;
     for (uint32_t v = b0; v < b1; v++) {
-        run += c16[slot(v)];
-        c16[slot(v)] = (uint16_t)run;
+        run += get(v);
+        put(v, run);
     }
     if (tid == 0 && total != n) atomicOr(&a.ctl->status, kDevKeyOutOfRange);
     __syncthreads();
@@ -186,9 +198,26 @@ __device__ void do_small(const BatchArgs &a, const BatchSeg &g, uint32_t *sm, ui
     const uint32_t head = min(lim, (uint32_t)(((16 - ((uintptr_t)out & 15)) & 15) / 4));
     const uint32_t nvec = (lim - head) / 4;
     int4 *vout = reinterpret_cast<int4 *>(out + head);
-    auto cdf = [&](uint32_t v) -> uint32_t { return c16[slot(v)]; };
+    auto cdf = [&](uint32_t v) -> uint32_t { return get(v); };
     auto first_above = [&](uint32_t lo, uint32_t p) -> uint32_t {  // min{v >= lo : cdf(v) > p}
         uint32_t hi = R - 1;
+        while (lo < hi) {
+            const uint32_t mid = (lo + hi) >> 1;
+            if (cdf(mid) > p) hi = mid; else lo = mid + 1;
+        }
+        return lo;
+    };
+    // The same from a value known to be close: steps of 1, 2, 4, ... until the
+    // CDF exceeds p, then a binary search inside the last step -- O(log gap),
+    // so sparse stretches of the range (the tails of a peaked shape, n << R)
+    // are crossed in a few reads.
+    auto next_above = [&](uint32_t lo, uint32_t p) -> uint32_t {
+        uint32_t hi = lo, step = 1;
+        while (cdf(hi) <= p) {  // cdf(R - 1) = total > p ends it
+            lo = hi + 1;
+            hi = min(R - 1, hi + step);
+            step <<= 1;
+        }
         while (lo < hi) {
             const uint32_t mid = (lo + hi) >> 1;
             if (cdf(mid) > p) hi = mid; else lo = mid + 1;
@@ -202,9 +231,11 @@ __device__ void do_small(const BatchArgs &a, const BatchSeg &g, uint32_t *sm, ui
     bool first = true;
     for (uint32_t w = wb + lane; w < we; w += 32) {
         const uint32_t q = head + 4 * w;
-        if (first || cdf(v) <= q) {
-            v = (!first && v + 1 < R && cdf(v + 1) > q) ? v + 1 : first_above(first ? 0u : v + 1, q);
+        if (first) {
+            v = first_above(0u, q);
             first = false;
+        } else if (cdf(v) <= q) {
+            v = next_above(v + 1, q);
         }
         if (cdf(v) >= q + 4) {
             const int32_t val = (int32_t)(min_u + v);
@@ -214,7 +245,7 @@ __device__ void do_small(const BatchArgs &a, const BatchSeg &g, uint32_t *sm, ui
             uint32_t vv = v;
 #pragma unroll
             for (int e = 0; e < 4; e++) {
-                while (cdf(vv) <= q + e) vv++;
+                if (cdf(vv) <= q + e) vv = next_above(vv + 1, q + e);
                 r[e] = (int32_t)(min_u + vv);
             }
             vout[w] = make_int4(r[0], r[1], r[2], r[3]);
@@ -224,6 +255,13 @@ __device__ void do_small(const BatchArgs &a, const BatchSeg &g, uint32_t *sm, ui
         const uint32_t p = tid < head ? tid : head + 4 * nvec + (tid - head);
         if ((tid < head || tid - head < 4) && p < lim) out[p] = (int32_t)(min_u + first_above(0u, p));
     }
+}
+
+// 32-bit counters when R of them fit in the `cap` words before s_tmp.
+__device__ __forceinline__ void do_small(const BatchArgs &a, const BatchSeg &g, uint32_t *sm, uint32_t cap,
+                                         uint32_t *s_tmp) {
+    if (g.R <= cap) do_small_impl<true>(a, g, sm, s_tmp);
+    else do_small_impl<false>(a, g, sm, s_tmp);
 }
 
 // ---------------------------------------------------------------- HIST
@@ -302,7 +340,7 @@ __global__ void __launch_bounds__(kSegThreads, 2) seg_first_kernel(BatchArgs a) 
     const unsigned long long t0 = (a.prof && threadIdx.x == 0) ? global_ns() : 0ull;
     const BatchItem it = a.items[blockIdx.x];
     const BatchSeg g = a.segs[it.seg];
-    if (it.kind == kItemSmall) do_small(a, g, sm, sm + kBatchSmallMaxR / 2);
+    if (it.kind == kItemSmall) do_small(a, g, sm, kBatchSmallMaxR / 2, sm + kBatchSmallMaxR / 2);
     else do_hist(a, g, it, sm);
     if (a.prof) {
         __syncthreads();
@@ -316,13 +354,20 @@ __global__ void __launch_bounds__(kSegThreads, 2) seg_first_kernel(BatchArgs a) 
 constexpr int kScanCtaThreads = 256;
 constexpr int kScanPerThread = kBatchScanChunk / kScanCtaThreads;  // 16
 
-__global__ void __launch_bounds__(kScanCtaThreads) seg_scan_kernel(BatchArgs a) {
+// The chunk's runs are staged in shared memory before they are written out.
+// Shared index of the chunk's r-th run: one padding word per 32, so that the
+// consecutive runs of the 32 lanes of a warp (16 apart in a dense chunk) fall
+// in 32 distinct banks.
+__device__ __forceinline__ uint32_t run_slot(uint32_t r) { return r + (r >> 5); }
+
+__global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs a) {
     __shared__ uint32_t s_ticket;
     __shared__ uint64_t s_warp[kScanCtaThreads / 32];
-    __shared__ uint64_t s_prefix;
+    __shared__ uint64_t s_prefix, s_total;
     __shared__ unsigned long long s_wait;
-    __shared__ uint32_t s_buf[2 * kBatchScanChunk];
-    uint32_t *s_cdf = s_buf, *s_runs = s_buf + kBatchScanChunk;
+    __shared__ uint32_t s_buf[kScanSmemWords];
+    uint32_t *s_end = s_buf;
+    int32_t *s_val = reinterpret_cast<int32_t *>(s_buf + kScanStageWords);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int kWarps = kScanCtaThreads / 32;
     // The in-CTA segments come first in the grid (dispatched first; spreading
@@ -333,7 +378,7 @@ __global__ void __launch_bounds__(kScanCtaThreads) seg_scan_kernel(BatchArgs a) 
         const unsigned long long ts = (a.prof && tid == 0) ? global_ns() : 0ull;
         const BatchItem it = a.items[a.n_first + a.n_scan + blockIdx.x];
         const BatchSeg g = a.segs[it.seg];
-        do_small(a, g, s_buf, s_buf + 2 * kBatchScanChunk - 64);
+        do_small(a, g, s_buf, kScanSmemWords - 64, s_buf + kScanSmemWords - 64);
         if (a.prof) {
             __syncthreads();
             if (tid == 0) prof_item(a, kItemSmall, ts, 0);
@@ -357,23 +402,17 @@ __global__ void __launch_bounds__(kScanCtaThreads) seg_scan_kernel(BatchArgs a) 
     const uint32_t cbase = chunk * kBatchScanChunk;
     const uint32_t first = tid * kScanPerThread;  // this thread's bins in the chunk
 
-    // Sixteen counts per thread (H is padded to whole chunks), zeroed behind
-    // us; kept in shared memory for the second pass.
+    // Sixteen counts per thread (H is padded to whole chunks).  They are read
+    // again after the lookback (L1 hits) rather than held in registers across
+    // it, and zeroed then.
     uint4 *h4p = reinterpret_cast<uint4 *>(H + cbase + first);
-    uint4 q[kScanPerThread / 4];
-#pragma unroll
-    for (int k = 0; k < kScanPerThread / 4; k++) q[k] = h4p[k];
-#pragma unroll
-    for (int k = 0; k < kScanPerThread / 4; k++) h4p[k] = make_uint4(0, 0, 0, 0);
     uint64_t run = 0;
 #pragma unroll
     for (int k = 0; k < kScanPerThread / 4; k++) {
-        const uint32_t c4[4] = {q[k].x, q[k].y, q[k].z, q[k].w};
+        const uint4 q = h4p[k];
+        const uint32_t c4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int e = 0; e < 4; e++) {
-            s_cdf[first + 4 * k + e] = c4[e];
-            run += ((uint64_t)(c4[e] > 0) << 32) | c4[e];
-        }
+        for (int e = 0; e < 4; e++) run += ((uint64_t)(c4[e] > 0) << 32) | c4[e];
     }
     const uint64_t winc = warp_incl_scan_u64(run, lane);
     if (lane == 31) s_warp[warp] = winc;
@@ -420,46 +459,60 @@ __global__ void __launch_bounds__(kScanCtaThreads) seg_scan_kernel(BatchArgs a) 
         }
         if (lane == 0) {
             s_prefix = prefix;
+            s_total = total;
             s_wait = waited;
         }
     }
     __syncthreads();
-    const uint64_t chunk_prefix = s_prefix;
-    uint64_t p = chunk_prefix + s_warp[warp] + (winc - run);  // exclusive prefix of this thread
+    // Positions before the chunk and runs before the chunk (in the segment).
+    const uint32_t pos_lo = (uint32_t)s_prefix, run_base = (uint32_t)(s_prefix >> 32);
+    uint64_t p = s_warp[warp] + (winc - run);  // exclusive prefix of this thread in the chunk
+    uint32_t c[kScanPerThread];
+#pragma unroll
+    for (int k = 0; k < kScanPerThread / 4; k++) {
+        const uint4 q = h4p[k];
+        c[4 * k] = q.x; c[4 * k + 1] = q.y; c[4 * k + 2] = q.z; c[4 * k + 3] = q.w;
+    }
+#pragma unroll
+    for (int k = 0; k < kScanPerThread / 4; k++) h4p[k] = make_uint4(0, 0, 0, 0);
+#pragma unroll
     for (int i = 0; i < kScanPerThread; i++) {
         const uint32_t v = cbase + first + i;
-        const uint32_t c = s_cdf[first + i];
-        p += ((uint64_t)(c > 0) << 32) | c;
-        const uint32_t cnt_end = (uint32_t)p;
-        const uint32_t runs = (uint32_t)(p >> 32);
-        s_cdf[first + i] = cnt_end;
-        s_runs[first + i] = runs;
-        if (v >= g.R) continue;
-        if (v == g.R - 1) {
-            a.seg_ctl[it.seg].num_runs = runs;
-            if (cnt_end != g.n) atomicOr(&a.ctl->status, kDevKeyOutOfRange);
+        p += ((uint64_t)(c[i] > 0) << 32) | c[i];
+        const uint32_t cnt_end = pos_lo + (uint32_t)p;  // sum_{u<=v} c_u
+        const uint32_t runs = (uint32_t)(p >> 32);      // non-empty values of the chunk up to v
+        if (c[i] > 0) {
+            s_end[run_slot(runs - 1)] = cnt_end;
+            s_val[run_slot(runs - 1)] = (int32_t)((uint32_t)g.minVal + v);
         }
-        if (c > 0) {
-            run_end[runs - 1] = cnt_end;
-            run_val[runs - 1] = (int32_t)((uint32_t)g.minVal + v);
+        if (v == g.R - 1) {
+            a.seg_ctl[it.seg].num_runs = run_base + runs;
+            if (cnt_end != g.n) atomicOr(&a.ctl->status, kDevKeyOutOfRange);
         }
     }
     __syncthreads();
+    // The chunk's runs, written out coalesced.
+    const uint32_t chunk_runs = (uint32_t)(s_total >> 32);
+    for (uint32_t r = tid; r < chunk_runs; r += kScanCtaThreads) {
+        run_end[run_base + r] = s_end[run_slot(r)];
+        run_val[run_base + r] = s_val[run_slot(r)];
+    }
     // Output items whose first position j * fill_chunk lies in the chunk's
-    // positions [pos_lo, pos_hi): the run holding it (Algorithm 7's rule).
-    const uint32_t pos_lo = (uint32_t)chunk_prefix, pos_hi = s_cdf[kBatchScanChunk - 1];
+    // positions [pos_lo, pos_hi): the run holding it, i.e. the first run
+    // whose end exceeds it (Algorithm 7's rule).
+    const uint32_t pos_hi = pos_lo + (uint32_t)s_total;
     if (pos_hi > pos_lo) {
         const uint32_t fc = g.fill_chunk;
         const uint32_t j_lo = (uint32_t)(((uint64_t)pos_lo + fc - 1) / fc);
         const uint32_t j_hi = min((uint32_t)(((uint64_t)pos_hi + fc - 1) / fc), g.fill_items);
         for (uint32_t j = j_lo + tid; j < j_hi; j += kScanCtaThreads) {
             const uint32_t p0 = j * fc;
-            uint32_t lo = 0, hi = kBatchScanChunk - 1;
+            uint32_t lo = 0, hi = chunk_runs - 1;
             while (lo < hi) {
                 const uint32_t mid = (lo + hi) >> 1;
-                if (s_cdf[mid] > p0) hi = mid; else lo = mid + 1;
+                if (s_end[run_slot(mid)] > p0) hi = mid; else lo = mid + 1;
             }
-            start_run[j] = s_runs[lo] - 1;
+            start_run[j] = run_base + lo;
         }
     }
     if (a.prof) {

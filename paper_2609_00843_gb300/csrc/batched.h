@@ -23,7 +23,13 @@ constexpr uint32_t kBatchSmallMaxR = 55296;           // 16-bit counters in 108 
 constexpr uint32_t kBatchTileMax = 28672;             // 32-bit tile histogram in 112 KB
 constexpr uint32_t kBatchScanChunk = 4096;            // bins per scan CTA (4 per thread)
 constexpr uint32_t kSegFillRuns = 4096;               // run window of an output CTA
-constexpr uint32_t kSmallInScanMaxR = 16000;          // in-CTA segments run by scan-launch CTAs
+constexpr uint32_t kSmallInScanMaxR = 16000;          // default: in-CTA segments run by scan-launch CTAs
+// Shared memory of a scan-launch CTA (words): the chunk's staged runs (end and
+// value, one padding word per 32), reused for an in-CTA segment's counters and
+// its block-scan scratch (the last 64 words).
+constexpr uint32_t kScanStageWords = kBatchScanChunk + kBatchScanChunk / 32;
+constexpr uint32_t kScanSmemWords = 2 * kScanStageWords;
+constexpr uint32_t kSmallInScanCapR = 2 * (kScanSmemWords - 64);  // 16-bit counters
 constexpr uint64_t kBatchMaxR = 1ull << 20;
 
 enum : uint32_t { kItemHist = 0, kItemSmall = 1, kItemScan = 2, kItemFill = 3 };
@@ -99,6 +105,7 @@ struct BatchTuning {
     uint64_t hist_chunk = 1ull << 19;   // keys per HIST item
     uint32_t fill_chunk = 1u << 16;     // positions per FILL item
     uint32_t small_max_n = kBatchSmallMaxN;
+    uint32_t small_scan_max_R = kSmallInScanMaxR;
 };
 
 // 0, or the rtcdf_status for the first segment with a bad length or range

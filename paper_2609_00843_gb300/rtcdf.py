@@ -48,7 +48,8 @@ class Params(ctypes.Structure):
 
 class BatchParams(ctypes.Structure):
     _fields_ = [("hist_chunk", ctypes.c_int32), ("fill_chunk", ctypes.c_int32),
-                ("small_max_n", ctypes.c_int32), ("reserved", ctypes.c_int32 * 5)]
+                ("small_max_n", ctypes.c_int32), ("small_scan_max_R", ctypes.c_int32),
+                ("reserved", ctypes.c_int32 * 4)]
 
 
 class TuneEntry(ctypes.Structure):

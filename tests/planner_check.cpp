@@ -44,7 +44,7 @@ static int check(const std::vector<SegSpec> &spec, const BatchTuning &tun) {
                 break;
             case kItemSmall:
                 if (launch != 0 && launch != 3) return fail("small in a wrong launch", (long)q, launch);
-                if ((launch == 3) != (g.R <= kSmallInScanMaxR)) return fail("small launch by range", (long)q, g.R);
+                if ((launch == 3) != (g.R <= tun.small_scan_max_R)) return fail("small launch by range", (long)q, g.R);
                 small_seen[it.seg]++;
                 break;
             case kItemScan:
@@ -134,10 +134,12 @@ int main(int argc, char **argv) {
         spec[s] = SegSpec{off, off, n, mn, mn + R};
         off += n;
     }
-    BatchTuning tunings[4];
+    BatchTuning tunings[6];
     tunings[1].hist_chunk = 4096; tunings[1].fill_chunk = 4096; tunings[1].small_max_n = 100;
     tunings[2].hist_chunk = 1ull << 22; tunings[2].fill_chunk = 1u << 20; tunings[2].small_max_n = 1;
     tunings[3].hist_chunk = 5000; tunings[3].fill_chunk = 6000;
+    tunings[4].small_scan_max_R = 1;
+    tunings[5].small_scan_max_R = kSmallInScanCapR;
     for (auto &t : tunings)
         if (check(spec, t)) return 1;
     std::printf("OK\n");
