@@ -616,7 +616,8 @@ __global__ void __launch_bounds__(kFillCtaThreads) seg_fill_kernel(BatchArgs a) 
 
 namespace {
 
-cudaError_t launch_pdl(const void *fn, uint32_t grid, int threads, const BatchArgs &a, cudaStream_t s) {
+cudaError_t launch_dep(const void *fn, uint32_t grid, int threads, const BatchArgs &a, bool programmatic,
+                       cudaStream_t s) {
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(grid);
     cfg.blockDim = dim3(threads);
@@ -626,7 +627,7 @@ cudaError_t launch_pdl(const void *fn, uint32_t grid, int threads, const BatchAr
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[0].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = programmatic ? 1 : 0;
     void *args[] = {const_cast<BatchArgs *>(&a)};
     return cudaLaunchKernelExC(&cfg, fn, args);
 }
@@ -637,16 +638,22 @@ cudaError_t launch_batched(const BatchArgs &a, cudaStream_t s) {
     cudaError_t e = cudaFuncSetAttribute(seg_first_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSegSmemBytes);
     if (e != cudaSuccess) return e;
+    // A launch is a programmatic dependent only of the plan's own launch
+    // before it (whose work it waits for, or which its CTAs do not read):
+    // the first launch issued waits for all earlier work in the stream.
+    bool chained = false;
     if (a.n_first) {
         seg_first_kernel<<<a.n_first, kSegThreads, kSegSmemBytes, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+        chained = true;
     }
-    if (a.n_scan + a.n_small2 &&
-        (e = launch_pdl((const void *)seg_scan_kernel, a.n_scan + a.n_small2, kScanCtaThreads, a, s)) !=
-            cudaSuccess)
-        return e;
+    if (a.n_scan + a.n_small2) {
+        e = launch_dep((const void *)seg_scan_kernel, a.n_scan + a.n_small2, kScanCtaThreads, a, chained, s);
+        if (e != cudaSuccess) return e;
+        chained = true;
+    }
     if (a.n_fill &&
-        (e = launch_pdl((const void *)seg_fill_kernel, a.n_fill, kFillCtaThreads, a, s)) != cudaSuccess)
+        (e = launch_dep((const void *)seg_fill_kernel, a.n_fill, kFillCtaThreads, a, chained, s)) != cudaSuccess)
         return e;
     return cudaSuccess;
 }

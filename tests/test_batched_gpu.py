@@ -221,3 +221,32 @@ def test_device_resident_metadata():
                                          d_mx.data_ptr(), len(lengths), stream_handle())
     assert rc == rtcdf.OK, rtcdf.rtcdf_status_str(rc)
     check_segments(x, out, offs, mn, mx)
+
+
+def test_plans_chained_on_one_stream_read_each_others_output():
+    """A plan whose only launch is the first one (wide-range in-CTA segments)
+    followed on the same stream by a plan whose only launch is the scan
+    launch (narrow-range in-CTA segments, which wait for nothing inside their
+    own plan) that reads the first plan's output: the second plan's first
+    launch must still wait for all earlier work in the stream."""
+    S, n, r_keys = 64, 60_000, 10_000
+    lengths, mins = [n] * S, [(-1) ** i * 1000 * i for i in range(S)]
+    x, offs, mn, _ = make_segments(lengths, [r_keys] * S, mins, [i % 3 for i in range(S)],
+                                   [gen.derive_seed(81, i) for i in range(S)])
+    wide = rtcdf.BatchPlan(offs, mn, mn + 30_000)     # R > 16000: first launch only
+    narrow = rtcdf.BatchPlan(offs, mn, mn + r_keys)   # R <= 16000: scan launch only
+    assert wide.info()["small_segments"] == S and narrow.info()["small_segments"] == S
+    ws_w = torch.zeros(max(256, wide.workspace_size()) // 4 + 64, dtype=torch.int32, device="cuda")
+    ws_n = torch.zeros(max(256, narrow.workspace_size()) // 4 + 64, dtype=torch.int32, device="cuda")
+    mid = torch.empty_like(x)
+    out = torch.empty_like(x)
+    s = stream_handle()
+    for _ in range(5):
+        mid.fill_(1 << 30)  # outside every range: a read before the first plan wrote it is an error
+        assert wide.run(x.data_ptr(), mid.data_ptr(), ws_w.data_ptr(), ws_w.numel() * 4, s) == rtcdf.OK
+        assert narrow.run(mid.data_ptr(), out.data_ptr(), ws_n.data_ptr(), ws_n.numel() * 4, s) == rtcdf.OK
+        assert rtcdf.rtcdf_batch_status_get(ws_w.data_ptr(), s) == (rtcdf.OK, 0)
+        assert rtcdf.rtcdf_batch_status_get(ws_n.data_ptr(), s) == (rtcdf.OK, 0)
+    check_segments(x, out, offs, mn, mn + r_keys)
+    wide.close()
+    narrow.close()
