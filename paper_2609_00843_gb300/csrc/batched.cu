@@ -385,14 +385,18 @@ __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs 
         }
         return;
     }
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;");
-    const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
+    // The ticket and the chunk's descriptors come from plan data, not from the
+    // first launch: fetched before waiting for it.  (The ticket counter was
+    // reset by the previous run's output launch, which finished before this
+    // plan's first launch began.)
     if (tid == 0) s_ticket = atomicAdd(&a.ctl->scan_ticket, 1u);
     __syncthreads();
     if (s_ticket >= a.n_scan) return;  // only with a workspace whose ticket was not zero
     const BatchItem it = a.items[a.n_first + s_ticket];
     const BatchSeg g = a.segs[it.seg];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
+    const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
     const uint32_t chunk = (uint32_t)it.a;
     uint32_t *H = a.ws_u32 + g.hist_off;
     uint64_t *state = reinterpret_cast<uint64_t *>(a.ws_u32 + g.state_off);
@@ -402,9 +406,9 @@ __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs 
     const uint32_t cbase = chunk * kBatchScanChunk;
     const uint32_t first = tid * kScanPerThread;  // this thread's bins in the chunk
 
-    // Sixteen counts per thread (H is padded to whole chunks).  They are read
-    // again after the lookback (L1 hits) rather than held in registers across
-    // it, and zeroed then.
+    // Sixteen counts per thread (H is padded to whole chunks), zeroed behind
+    // us.  They wait for the second pass in shared memory (in the staging
+    // area, which is not written before they are read back).
     uint4 *h4p = reinterpret_cast<uint4 *>(H + cbase + first);
     uint64_t run = 0;
 #pragma unroll
@@ -412,8 +416,13 @@ __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs 
         const uint4 q = h4p[k];
         const uint32_t c4[4] = {q.x, q.y, q.z, q.w};
 #pragma unroll
-        for (int e = 0; e < 4; e++) run += ((uint64_t)(c4[e] > 0) << 32) | c4[e];
+        for (int e = 0; e < 4; e++) {
+            run += ((uint64_t)(c4[e] > 0) << 32) | c4[e];
+            s_buf[run_slot(first + 4 * k + e)] = c4[e];
+        }
     }
+#pragma unroll
+    for (int k = 0; k < kScanPerThread / 4; k++) h4p[k] = make_uint4(0, 0, 0, 0);
     const uint64_t winc = warp_incl_scan_u64(run, lane);
     if (lane == 31) s_warp[warp] = winc;
     __syncthreads();
@@ -469,12 +478,8 @@ __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs 
     uint64_t p = s_warp[warp] + (winc - run);  // exclusive prefix of this thread in the chunk
     uint32_t c[kScanPerThread];
 #pragma unroll
-    for (int k = 0; k < kScanPerThread / 4; k++) {
-        const uint4 q = h4p[k];
-        c[4 * k] = q.x; c[4 * k + 1] = q.y; c[4 * k + 2] = q.z; c[4 * k + 3] = q.w;
-    }
-#pragma unroll
-    for (int k = 0; k < kScanPerThread / 4; k++) h4p[k] = make_uint4(0, 0, 0, 0);
+    for (int i = 0; i < kScanPerThread; i++) c[i] = s_buf[run_slot(first + i)];
+    __syncthreads();  // every count read before the staging area is written
 #pragma unroll
     for (int i = 0; i < kScanPerThread; i++) {
         const uint32_t v = cbase + first + i;
