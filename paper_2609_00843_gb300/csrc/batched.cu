@@ -534,11 +534,13 @@ __global__ void __launch_bounds__(kFillCtaThreads) seg_fill_kernel(BatchArgs a) 
     __shared__ uint32_t s_end[kSegFillRuns];
     __shared__ int32_t s_val[kSegFillRuns];
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
+    // The item and its segment are plan data: fetched before waiting for the
+    // scan launch.
+    const BatchItem it = a.items[a.n_first + a.n_scan + a.n_small2 + blockIdx.x];
+    const BatchSeg g = a.segs[it.seg];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
     if (blockIdx.x == 0 && tid == 0) a.ctl->scan_ticket = 0;
-    const BatchItem it = a.items[a.n_first + a.n_scan + a.n_small2 + blockIdx.x];
-    const BatchSeg g = a.segs[it.seg];
     if (it.aux == 0 && g.scan_chunks > 1) {
         // The segment's first output item leaves its lookback state zeroed.
         uint64_t *state = reinterpret_cast<uint64_t *>(a.ws_u32 + g.state_off);

@@ -100,16 +100,19 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs a) {
     __shared__ uint32_t s_runs[kScanChunk];  // non-empty values u <= v
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
 
-    // Launched as a programmatic dependent of the histogram: wait until that
-    // grid has finished and its writes are visible, then let the output
-    // kernel be scheduled (it waits for this grid in the same way).
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;");
+    // Launched as a programmatic dependent of the histogram.  The chunk ticket
+    // does not depend on it (the counter was reset by the previous sort's
+    // output kernel, which finished before this sort's histogram began), so
+    // it is taken first; then wait until the histogram grid has finished and
+    // its writes are visible, and let the output kernel be scheduled (it
+    // waits for this grid in the same way).
     const bool single = (a.chunks == 1);  // R <= kScanChunk: no lookback at all
     if (!single) {
         if (tid == 0) s_chunk = atomicAdd(&a.ctl->scan_ticket, 1u);
         __syncthreads();
     }
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    asm volatile("griddepcontrol.launch_dependents;");
     const uint32_t chunk = single ? 0u : s_chunk;
     // A ticket past the last chunk only happens with a workspace whose ticket
     // was not zero (not cleared, or shared by unordered calls): take no chunk.
