@@ -148,14 +148,23 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
         cudaStreamCreateWithFlags(&streams[k], cudaStreamNonBlocking);
     }
     // Inputs are written on their own streams (round robin), so writing the
-    // next arrivals overlaps the sorts already running.
+    // next arrivals overlaps the sorts already running.  Each request's write
+    // is marked by an event (from a pool, returned when the request retires):
+    // a launch waits for its own requests' inputs only.
     std::vector<cudaStream_t> fill_streams(K);
-    std::vector<cudaEvent_t> fill_evs(K);
-    for (int k = 0; k < K; k++) {
-        cudaStreamCreateWithFlags(&fill_streams[k], cudaStreamNonBlocking);
-        cudaEventCreateWithFlags(&fill_evs[k], cudaEventDisableTiming);
-    }
+    for (int k = 0; k < K; k++) cudaStreamCreateWithFlags(&fill_streams[k], cudaStreamNonBlocking);
     int fill_rr = 0;
+    std::vector<cudaEvent_t> ev_pool, req_ev((size_t)count, nullptr);
+    auto take_event = [&]() {
+        cudaEvent_t e = nullptr;
+        if (!ev_pool.empty()) {
+            e = ev_pool.back();
+            ev_pool.pop_back();
+        } else {
+            cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        }
+        return e;
+    };
     uint64_t *d_digest = nullptr;
     if (want_digest) {
         cudaMalloc(&d_digest, sizeof(uint64_t) * (size_t)std::max<int64_t>(1, count));
@@ -190,7 +199,6 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
         bool progressed = false;
         const double now = secs(t0);
         // 1. Admit arrived requests, in order, while their slots fit.
-        bool admitted = false;
         while (next < count && reqs[next].arrival_s <= now) {
             const rtcdf_request &r = reqs[next];
             size_t off = 0;
@@ -210,18 +218,20 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
             int32_t *in = reinterpret_cast<int32_t *>(slab + off);
             const int fs = fill_rr;
             fill_rr = (fill_rr + 1) % K;
-            if (r.n && cfg->fill(in, r.n, 0, r.minVal, r.maxVal - r.minVal, r.dist, r.seed,
-                                 (rtcdf_stream_t)fill_streams[fs]) != 0) {
-                err = RTCDF_ERR_CUDA;
-                break;
+            if (r.n) {
+                if (cfg->fill(in, r.n, 0, r.minVal, r.maxVal - r.minVal, r.dist, r.seed,
+                              (rtcdf_stream_t)fill_streams[fs]) != 0) {
+                    err = RTCDF_ERR_CUDA;
+                    break;
+                }
+                req_ev[next] = take_event();
+                cudaEventRecord(req_ev[next], fill_streams[fs]);
             }
             results[next].admit_s = secs(t0);
             pending.push_back(next);
             next++;
-            admitted = progressed = true;
+            progressed = true;
         }
-        if (admitted)
-            for (int k = 0; k < K; k++) cudaEventRecord(fill_evs[k], fill_streams[k]);
         // 2. Launch pending requests on free streams.
         while (!pending.empty() && !err) {
             int k = -1;
@@ -229,8 +239,6 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
                 if (!stream_busy[j]) { k = j; break; }
             if (k < 0) break;
             cudaStream_t s = streams[k];
-            for (int f = 0; f < K; f++)  // inputs written before the sort reads them
-                cudaStreamWaitEvent(s, fill_evs[f], 0);
             Launch L;
             L.stream = k;
             // A large request alone (while fewer than max_large of them run),
@@ -251,6 +259,8 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
                 }
                 if (L.reqs.empty()) break;  // only large requests wait: a large launch must finish
             }
+            for (int64_t i : L.reqs)  // inputs written before the sort reads them
+                if (req_ev[i]) cudaStreamWaitEvent(s, req_ev[i], 0);
             const double launch_t = secs(t0);
             // A lone request (large, or small with nothing to batch it with --
             // light load) goes through the single-array pipeline, which needs
@@ -365,6 +375,8 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
                     results[i].done_s = t;
                     results[i].status = 0;
                     alloc.release(slot_off[i], slot_bytes[i]);
+                    if (req_ev[i]) ev_pool.push_back(req_ev[i]);  // complete: the launch waited for it
+                    req_ev[i] = nullptr;
                     done++;
                 }
                 if (L.ws_bytes) alloc.release(L.ws_off, L.ws_bytes);
@@ -402,10 +414,10 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
         cudaStreamDestroy(streams[k]);
         cudaFreeHost(stage[k]);
     }
-    for (int k = 0; k < K; k++) {
-        cudaStreamDestroy(fill_streams[k]);
-        cudaEventDestroy(fill_evs[k]);
-    }
+    for (int k = 0; k < K; k++) cudaStreamDestroy(fill_streams[k]);
+    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : req_ev)
+        if (e) cudaEventDestroy(e);
     cudaFree(d_digest);
     cudaFree(slab);
     if (err) return err;
