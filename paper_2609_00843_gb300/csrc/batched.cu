@@ -287,14 +287,27 @@ __device__ void do_hist(const BatchArgs &a, const BatchSeg &g, const BatchItem &
         count_key_pred(s_base, (uint32_t)k.w - base, w);
     };
     uint64_t v = tid;
-    for (; v + 3 * nt < nv; v += 4 * nt) {
-        int4 k[4];
+    if (g.m == 1) {
+        // One tile: every key is read once, so stream it (evict first).
+        for (; v + 3 * nt < nv; v += 4 * nt) {
+            int4 k[4];
 #pragma unroll
-        for (int u = 0; u < 4; u++) k[u] = __ldg(vin + v + u * nt);
+            for (int u = 0; u < 4; u++) k[u] = __ldcs(vin + v + u * nt);
 #pragma unroll
-        for (int u = 0; u < 4; u++) count4(k[u]);
+            for (int u = 0; u < 4; u++) count4(k[u]);
+        }
+        for (; v < nv; v += nt) count4(__ldcs(vin + v));
+    } else {
+        // Several tiles: the other tiles' items read the same chunk (L2 hits).
+        for (; v + 3 * nt < nv; v += 4 * nt) {
+            int4 k[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) k[u] = __ldg(vin + v + u * nt);
+#pragma unroll
+            for (int u = 0; u < 4; u++) count4(k[u]);
+        }
+        for (; v < nv; v += nt) count4(__ldg(vin + v));
     }
-    for (; v < nv; v += nt) count4(__ldg(vin + v));
     if (tid < lead) count_key_pred(s_base, (uint32_t)in[k0 + tid] - base, w);
     for (uint64_t i = k0 + lead + 4 * nv + tid; i < k1; i += nt)
         count_key_pred(s_base, (uint32_t)in[i] - base, w);
