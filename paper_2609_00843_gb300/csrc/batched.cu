@@ -343,6 +343,19 @@ __device__ __forceinline__ uint32_t first_after(const uint32_t *e, uint32_t lo, 
     return lo;
 }
 
+// The same when the answer is expected close to lo: probes lo, lo + 1,
+// lo + 3, lo + 7, ... until e exceeds p, then a binary search inside the last
+// step -- O(log(j - lo)) reads.
+__device__ __forceinline__ uint32_t next_after(const uint32_t *e, uint32_t lo, uint32_t hi, uint32_t p) {
+    uint32_t probe = lo, step = 1;
+    while (e[probe] <= p) {  // e[hi] > p ends it
+        lo = probe + 1;
+        probe = min(hi, probe + step);
+        step <<= 1;
+    }
+    return first_after(e, lo, probe, p);
+}
+
 }  // namespace
 
 __global__ void __launch_bounds__(kSegThreads, 2) seg_first_kernel(BatchArgs a) {
@@ -597,7 +610,7 @@ __global__ void __launch_bounds__(kFillCtaThreads) seg_fill_kernel(BatchArgs a) 
             uint32_t j = 0;
             for (uint32_t w = wb + lane; w < we; w += 32) {
                 const uint32_t q = head + 4 * w;
-                if (s_end[j] <= q) j = (s_end[j + 1] > q) ? j + 1 : first_after(s_end, j + 2, nw - 1, q);
+                if (s_end[j] <= q) j = next_after(s_end, j + 1, nw - 1, q);
                 if (s_end[j] >= q + 4) {
                     const int32_t v = s_val[j];
                     __stcs(vout + w, make_int4(v, v, v, v));

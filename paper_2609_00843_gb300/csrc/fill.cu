@@ -29,6 +29,20 @@ __device__ __forceinline__ int first_run_after(const uint32_t *s_end, int lo, in
     return lo;
 }
 
+// The same when the answer is expected close to lo: probes lo, lo + 1,
+// lo + 3, lo + 7, ... until s_end exceeds p, then a binary search inside the
+// last step -- O(log(j - lo)) reads, so a lane that crosses a few short runs
+// between its vectors does not pay a search over the whole window.
+__device__ __forceinline__ int next_run_after(const uint32_t *s_end, int lo, int hi, uint32_t p) {
+    int probe = lo, step = 1;
+    while (s_end[probe] <= p) {  // s_end[hi] > p ends it
+        lo = probe + 1;
+        probe = min(hi, probe + step);
+        step <<= 1;
+    }
+    return first_run_after(s_end, lo, probe, p);
+}
+
 // Runs per shared-memory window: four per thread, so that a CTA whose
 // positions cross thousands of short runs (the tails of a peaked distribution
 // over a wide range) needs few window rounds -- each round costs a global
@@ -100,7 +114,7 @@ __global__ void __launch_bounds__(WIN) fill_kernel(FillArgs a) {
                 const uint32_t q = head + 4 * w;
                 if (s_end[j] <= q) {
                     // s_end[nw - 1] > q, so j + 1 <= nw - 1.
-                    j = (s_end[j + 1] > q) ? j + 1 : first_run_after(s_end, j + 2, nw - 1, q);
+                    j = next_run_after(s_end, j + 1, nw - 1, q);
                 }
                 if (s_end[j] >= q + 4) {
                     const int32_t v = s_val[j];
