@@ -615,12 +615,16 @@ __global__ void __launch_bounds__(kFillCtaThreads) seg_fill_kernel(BatchArgs a) 
                     const int32_t v = s_val[j];
                     __stcs(vout + w, make_int4(v, v, v, v));
                 } else {
+                    // Positions q..q+3 lie in runs j..j+3: q+e lies in run j
+                    // plus the number of runs among j, j+1, j+2 that end at or
+                    // before it (ends read independently, clamped to the
+                    // window's last run, whose end exceeds every position).
+                    const uint32_t e0 = s_end[j], e1 = s_end[min(j + 1, nw - 1)], e2 = s_end[min(j + 2, nw - 1)];
                     int32_t r[4];
-                    uint32_t jj = j;
 #pragma unroll
                     for (int e = 0; e < 4; e++) {
-                        while (s_end[jj] <= q + e) jj++;
-                        r[e] = s_val[jj];
+                        const uint32_t p = q + e;
+                        r[e] = s_val[j + (p >= e0) + (p >= e1) + (p >= e2)];
                     }
                     __stcs(vout + w, make_int4(r[0], r[1], r[2], r[3]));
                 }
