@@ -191,8 +191,8 @@ __device__ void do_small_impl(const BatchArgs &a, const BatchSeg &g, uint32_t *s
     // Output: position p holds minVal + min{v : CDF[v] >= p + 1} (Algorithm 7).
     // 16-byte vectors: each warp takes a contiguous share, lanes interleaved
     // (one coalesced store per step); a lane's value index only moves forward
-    // (the next value is tried first, then a binary search).  The positions
-    // before the first whole vector and after the last are written one by one.
+    // (a galloping search from the current value).  The positions before the
+    // first whole vector and after the last are written one by one.
     int32_t *out = a.out + g.out_off;
     const uint32_t lim = min(n, total);
     const uint32_t head = min(lim, (uint32_t)(((16 - ((uintptr_t)out & 15)) & 15) / 4));

@@ -7,11 +7,13 @@
 // run_val[k] = that value's key): it copies a window of consecutive runs into
 // shared memory, then every thread writes 16-byte vectors of its positions,
 // finding the run of a position with the same rule (smallest k with
-// run_end[k] >= p + 1), starting from the run of its previous vector (the
-// next run is tried first, then a binary search).  When a whole vector lies
-// inside one run -- the common case -- that is one shared load and one
-// compare before the store.  The few positions of a window that
-// do not fill a whole aligned vector are written one by one.
+// run_end[k] >= p + 1), starting from the run of its previous vector (a
+// galloping search: the next run, then steps of 2, 4, ... runs, then a binary
+// search inside the last step).  When a whole vector lies inside one run --
+// the common case -- that is one shared load and one compare before the
+// store; a vector across runs reads the next runs' ends independently.  The
+// few positions of a window that do not fill a whole aligned vector are
+// written one by one.
 //
 // All positions are below n < 2^32, so the index arithmetic is 32-bit.  The
 // CTA also clears the scan's lookback state so the workspace is ready for the
