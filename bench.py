@@ -270,6 +270,17 @@ def single_config(stream):
             flush.fill_(1)
     warm = paper_protocol_ms(once, stream)
     cold = paper_protocol_ms(once, stream, between=do_flush)
+    # The same sort captured once in a CUDA graph and replayed (no host work
+    # per sort: what a caller that replays a captured pipeline sees).
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=stream):
+        once()
+    stream.synchronize()
+
+    def replay():
+        with torch.cuda.stream(stream):
+            g.replay()
+    graph = paper_protocol_ms(replay, stream)
     # host wall-clock of one call + synchronisation (what a blocking caller sees)
     walls = []
     for _ in range(30):
@@ -279,11 +290,13 @@ def single_config(stream):
         walls.append((time.perf_counter() - t0) * 1e3)
     res = {"workload": "n=1e6 int32, minVal=0, R=2^7, uniform, seed 0",
            "warm_ms": round(warm, 5), "l2_flushed_ms": round(cold, 5),
+           "graph_replay_ms": round(graph, 5),
            "warm_GKeys_s": round(n / (warm * 1e-3) / 1e9, 2),
+           "graph_replay_GKeys_s": round(n / (graph * 1e-3) / 1e9, 2),
            "l2_flushed_GKeys_s": round(n / (cold * 1e-3) / 1e9, 2),
            "host_wall_ms_median": round(statistics.median(walls), 4),
            "note": "launch-latency bound: 8n bytes at the copy bandwidth take ~1.2 us"}
-    del x, out, flush, ws
+    del g, x, out, flush, ws
     return res
 
 
