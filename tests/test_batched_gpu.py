@@ -250,3 +250,28 @@ def test_plans_chained_on_one_stream_read_each_others_output():
     check_segments(x, out, offs, mn, mn + r_keys)
     wide.close()
     narrow.close()
+
+
+@pytest.mark.parametrize("scan_max_R", [0, 16768])
+def test_in_cta_counter_layouts_at_their_capacity(scan_max_R):
+    """In-CTA segments at every counter-layout boundary: 32-bit counters up to
+    8384 values in a scan-launch CTA and 27648 in a first-launch CTA, 16-bit
+    split counters above that, up to 16768 values in a scan-launch CTA (its
+    whole shared memory, with the plan parameter at its maximum) and 55296 in
+    a first-launch CTA; each range with 65535 keys of every shape and a short
+    segment whose keys leave most values empty."""
+    Rs = [8384, 8385, 16000, 16768, 27648, 27649, 55296]
+    lengths, ranges, mins, dists = [], [], [], []
+    for i, R in enumerate(Rs):
+        for d in (gen.UNIFORM, gen.NORMAL, gen.ALL_EQUAL):
+            lengths.append(65535); ranges.append(R); mins.append(-(1 << 20) + 977 * i); dists.append(d)
+        lengths.append(777); ranges.append(R); mins.append(5000 * i); dists.append(gen.UNIFORM)
+    seeds = [gen.derive_seed(82, i) for i in range(len(lengths))]
+    x, offs, mn, mx = make_segments(lengths, ranges, mins, dists, seeds, pad_front=1)
+    out = torch.full_like(x, 0x7FFFFFFF)
+    p = rtcdf.BatchParams(small_scan_max_R=scan_max_R)
+    plan, ws, wsb, rc, bits = run_plan(x, out, offs, mn, mx, p)
+    assert (rc, bits) == (rtcdf.OK, 0)
+    assert plan.info()["small_segments"] == len(lengths)
+    check_segments(x, out, offs, mn, mx)
+    plan.close()
