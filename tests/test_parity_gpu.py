@@ -257,6 +257,11 @@ def test_sparse_wide_ranges():
         assert_matches_oracle(x, out, 0, R)
     x = dev_keys(1_000_000, 0, 1 << 24, gen.UNIFORM, 16)
     assert_matches_oracle(x, gpu_sort(x, 0, 1 << 24), 0, 1 << 24)
+    # Runs of two or three keys: most vectors straddle runs and each output
+    # CTA walks its positions in several windows of runs.
+    for dist in (gen.UNIFORM, gen.NORMAL):
+        x = dev_keys(10_000_000, -3, 1 << 22, dist, 17 + dist)
+        assert_matches_oracle(x, gpu_sort(x, -3, -3 + (1 << 22)), -3, -3 + (1 << 22))
 
 
 def test_host_and_device_generators_agree():
