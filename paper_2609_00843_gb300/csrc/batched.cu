@@ -607,24 +607,32 @@ __global__ void __launch_bounds__(kFillCtaThreads) seg_fill_kernel(BatchArgs a) 
             const uint32_t per_warp = ((nvec + nwarps - 1) / nwarps + 31) & ~31u;
             const uint32_t wb = w_lo + warp * per_warp;
             const uint32_t we = min(w_hi, wb + per_warp);
+            // The run of this lane's last vector, its end and value in
+            // registers (no shared-memory read inside the same run).
             uint32_t j = 0;
+            uint32_t ej = s_end[0];
+            int32_t vj = s_val[0];
             for (uint32_t w = wb + lane; w < we; w += 32) {
                 const uint32_t q = head + 4 * w;
-                if (s_end[j] <= q) j = next_after(s_end, j + 1, nw - 1, q);
-                if (s_end[j] >= q + 4) {
-                    const int32_t v = s_val[j];
-                    __stcs(vout + w, make_int4(v, v, v, v));
+                if (ej <= q) {
+                    j = next_after(s_end, j + 1, nw - 1, q);
+                    ej = s_end[j];
+                    vj = s_val[j];
+                }
+                if (ej >= q + 4) {
+                    __stcs(vout + w, make_int4(vj, vj, vj, vj));
                 } else {
                     // Positions q..q+3 lie in runs j..j+3: q+e lies in run j
                     // plus the number of runs among j, j+1, j+2 that end at or
                     // before it (ends read independently, clamped to the
                     // window's last run, whose end exceeds every position).
-                    const uint32_t e0 = s_end[j], e1 = s_end[min(j + 1, nw - 1)], e2 = s_end[min(j + 2, nw - 1)];
+                    const uint32_t e1 = s_end[min(j + 1, nw - 1)], e2 = s_end[min(j + 2, nw - 1)];
                     int32_t r[4];
+                    r[0] = vj;  // q < ej
 #pragma unroll
-                    for (int e = 0; e < 4; e++) {
+                    for (int e = 1; e < 4; e++) {
                         const uint32_t p = q + e;
-                        r[e] = s_val[j + (p >= e0) + (p >= e1) + (p >= e2)];
+                        r[e] = s_val[j + (p >= ej) + (p >= e1) + (p >= e2)];
                     }
                     __stcs(vout + w, make_int4(r[0], r[1], r[2], r[3]));
                 }
