@@ -43,16 +43,36 @@ __device__ __forceinline__ void count_key(uint32_t s_base, uint32_t y, uint32_t 
         ::"r"(y), "r"(w), "r"(s_base + 4u * y));
 }
 
-template <bool STREAMING, int UNROLL>
+// S[min(y, w)] += 1: a key outside the tile adds to the trash word S[w]
+// instead of being predicated off; all such lanes of a warp hit one address
+// with an immediate increment and are combined.
+__device__ __forceinline__ void count_key_trash(uint32_t s_base, uint32_t y, uint32_t w) {
+    const uint32_t yy = y < w ? y : w;
+    asm volatile("red.shared.add.u32 [%0], 1;" ::"r"(s_base + 4u * yy));
+}
+
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
+// ADAPT (2 to 8 tiles): out-of-tile keys go to a trash word, and the m CTAs
+// that read the same vectors prefetch them into L2 two iterations ahead --
+// unless a sample of the input (one vector per warp) shows one tile holding
+// more than 2/m of the keys without holding nearly all of them: the CTAs of
+// such tiles then run at unequal speeds and the prefetches cost more than
+// they save.  The choice changes only the speed, never the counts.
+template <bool STREAMING, int UNROLL, bool ADAPT>
 __global__ void __launch_bounds__(1024) hist_kernel(HistArgs a) {
     extern __shared__ uint32_t S[];
+    __shared__ uint32_t s_tc[8];
     const uint32_t t = blockIdx.x % a.m;
     const uint32_t q = blockIdx.x / a.m;
     const uint32_t b = t * a.T;
     const uint32_t w = min(a.T, a.R - b);
     const int tid = threadIdx.x, nt = blockDim.x;
 
-    for (uint32_t i = tid; i < w; i += nt) S[i] = 0;
+    for (uint32_t i = tid; i < w + (ADAPT ? 1u : 0u); i += nt) S[i] = 0;  // + the trash word
+    if (ADAPT && tid < 8) s_tc[tid] = 0;
     __syncthreads();
 
     const uint32_t base = a.min_u + b;  // key - base = position inside the tile
@@ -65,16 +85,52 @@ __global__ void __launch_bounds__(1024) hist_kernel(HistArgs a) {
     const uint64_t stride = (uint64_t)a.g * nt;
     const uint64_t nvec = a.nvec;
     uint64_t v = (uint64_t)q * nt + tid;
-    for (; v + (UNROLL - 1) * stride < nvec; v += UNROLL * stride) {
+    bool pf = false;
+    if (ADAPT) {
+        if ((tid & 31) == 0 && v < nvec) {
+            const int4 k = __ldg(vin + v);
+            const uint32_t y[4] = {(uint32_t)k.x - a.min_u, (uint32_t)k.y - a.min_u,
+                                   (uint32_t)k.z - a.min_u, (uint32_t)k.w - a.min_u};
+#pragma unroll
+            for (int e = 0; e < 4; e++)
+                if (y[e] < a.R) atomicAdd(&s_tc[min(y[e] / a.T, 7u)], 1u);
+        }
+        __syncthreads();
+        uint32_t tot = 0, mx = 0;
+#pragma unroll
+        for (int i = 0; i < 8; i++) {
+            tot += s_tc[i];
+            mx = max(mx, s_tc[i]);
+        }
+        pf = tot > 0 && (mx * a.m <= 2 * tot || mx * 10 >= 9 * tot);
+    }
+    uint64_t vb = (uint64_t)q * nt;  // thread 0's vector of the iteration
+    for (; v + (UNROLL - 1) * stride < nvec; v += UNROLL * stride, vb += UNROLL * stride) {
+        if (ADAPT && pf && tid == 0) {
+            // This CTA's share (u = t, t + m, ...) of the vectors its group
+            // reads two iterations from now.
+            const uint64_t ahead = vb + 2ull * UNROLL * stride;
+            for (uint32_t u = t; u < (uint32_t)UNROLL; u += a.m) {
+                const uint64_t s0 = ahead + (uint64_t)u * stride;
+                if (s0 + nt <= nvec) prefetch_l2(vin + s0, 16u * nt);
+            }
+        }
         int4 k[UNROLL];
 #pragma unroll
         for (int u = 0; u < UNROLL; u++) k[u] = load_vec<STREAMING>(vin + v + u * stride);
 #pragma unroll
         for (int u = 0; u < UNROLL; u++) {
-            count_key(s_base, (uint32_t)k[u].x - base, w);
-            count_key(s_base, (uint32_t)k[u].y - base, w);
-            count_key(s_base, (uint32_t)k[u].z - base, w);
-            count_key(s_base, (uint32_t)k[u].w - base, w);
+            if (ADAPT) {
+                count_key_trash(s_base, (uint32_t)k[u].x - base, w);
+                count_key_trash(s_base, (uint32_t)k[u].y - base, w);
+                count_key_trash(s_base, (uint32_t)k[u].z - base, w);
+                count_key_trash(s_base, (uint32_t)k[u].w - base, w);
+            } else {
+                count_key(s_base, (uint32_t)k[u].x - base, w);
+                count_key(s_base, (uint32_t)k[u].y - base, w);
+                count_key(s_base, (uint32_t)k[u].z - base, w);
+                count_key(s_base, (uint32_t)k[u].w - base, w);
+            }
         }
     }
     for (; v < nvec; v += stride) {
@@ -102,9 +158,23 @@ __global__ void __launch_bounds__(1024) hist_kernel(HistArgs a) {
     }
 }
 
-template <bool STREAMING>
-const void *hist_fn(int unroll) {
-    return unroll == 8 ? (const void *)hist_kernel<STREAMING, 8> : (const void *)hist_kernel<STREAMING, 4>;
+// Kernel variant: streaming loads for one tile; the adaptive form for 2 to 8
+// tiles; the plain predicated form beyond.
+enum HistVariant { kHistStreaming = 0, kHistAdaptive = 1, kHistPlain = 2 };
+int hist_variant(bool streaming, uint32_t m) {
+    return streaming ? kHistStreaming : (m <= 8 ? kHistAdaptive : kHistPlain);
+}
+
+const void *hist_fn(int variant, int unroll) {
+    const bool deep = unroll == 8;
+    switch (variant) {
+        case kHistStreaming:
+            return deep ? (const void *)hist_kernel<true, 8, false> : (const void *)hist_kernel<true, 4, false>;
+        case kHistAdaptive:
+            return deep ? (const void *)hist_kernel<false, 8, true> : (const void *)hist_kernel<false, 4, true>;
+        default:
+            return deep ? (const void *)hist_kernel<false, 8, false> : (const void *)hist_kernel<false, 4, false>;
+    }
 }
 
 // Eight loads in flight per thread when only one CTA fits on an SM.
@@ -114,15 +184,9 @@ cudaError_t launch_hist(const HistArgs &a, int threads, size_t smem, bool stream
                         cudaStream_t s) {
     // hist_max_ctas_per_sm() has raised the shared-memory limit for this size.
     dim3 grid(a.m * a.g);
-    const bool deep = hist_unroll(smem) == 8;
-    if (streaming) {
-        if (deep) hist_kernel<true, 8><<<grid, threads, smem, s>>>(a);
-        else hist_kernel<true, 4><<<grid, threads, smem, s>>>(a);
-    } else {
-        if (deep) hist_kernel<false, 8><<<grid, threads, smem, s>>>(a);
-        else hist_kernel<false, 4><<<grid, threads, smem, s>>>(a);
-    }
-    return cudaGetLastError();
+    void *args[] = {const_cast<HistArgs *>(&a)};
+    return cudaLaunchKernel(hist_fn(hist_variant(streaming, a.m), hist_unroll(smem)), grid, dim3(threads),
+                            args, smem, s);
 }
 
 // Occupancy of the histogram kernel for a launch shape, cached per device so
@@ -141,13 +205,16 @@ cudaError_t hist_max_ctas_per_sm(int threads, size_t smem, bool streaming, int *
         *ctas = it->second;
         return cudaSuccess;
     }
-    const void *f = streaming ? hist_fn<true>(hist_unroll(smem)) : hist_fn<false>(hist_unroll(smem));
+    // The adaptive and plain multi-tile variants share the same sizes.
+    const void *f = hist_fn(streaming ? kHistStreaming : kHistAdaptive, hist_unroll(smem));
     size_t &lim = smem_limit[std::make_pair(dev, streaming)];
     if (smem > lim) {
-        for (int u : {4, 8}) {
-            const void *fu = streaming ? hist_fn<true>(u) : hist_fn<false>(u);
-            e = cudaFuncSetAttribute(fu, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-            if (e != cudaSuccess) return e;
+        for (int v : {kHistStreaming, kHistAdaptive, kHistPlain}) {
+            if ((v == kHistStreaming) != streaming) continue;
+            for (int u : {4, 8}) {
+                e = cudaFuncSetAttribute(hist_fn(v, u), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+                if (e != cudaSuccess) return e;
+            }
         }
         lim = smem;
     }

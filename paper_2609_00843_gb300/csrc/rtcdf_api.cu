@@ -100,8 +100,10 @@ rtcdf_status make_plan_with(uint64_t n, uint32_t R, uintptr_t in_addr, uintptr_t
     if (T > R) T = R;
     pl->T = T;
     pl->m = (R + T - 1) / T;
-    pl->hist_smem = (size_t)T * 4;
     pl->streaming = (pl->m == 1);
+    // Several tiles: one more word after the tile (out-of-tile keys counted
+    // into it, kept to 16 bytes).
+    pl->hist_smem = (size_t)T * 4 + (pl->streaming ? 0 : 16);
 
     // Input split: unaligned head elements, 16-byte vectors, ragged tail.
     uint32_t head_in = (uint32_t)(((16 - (in_addr & 15)) & 15) / 4);
