@@ -252,9 +252,10 @@ rtcdf_status rtcdf_sort_host(const int32_t *in, int32_t *out, uint64_t n, int64_
  * [seg_minVal[s], seg_maxVal[s]) (R_s <= 2^20), and it is written sorted to
  * the same positions of `out`.  The method per segment is Algorithms 4-7
  * unchanged; segments with fewer than 65536 keys (and R_s <= 55296) are
- * sorted entirely inside one CTA of the first launch, larger ones are split
- * into histogram items (first launch), 4096-bin scan chunks (second launch)
- * and output items (third launch).
+ * sorted entirely inside one CTA -- of the second launch when R_s is at most
+ * rtcdf_batch_params.small_scan_max_R (default 16000), else of the first --
+ * and larger ones are split into histogram items (first launch), 4096-bin
+ * scan chunks (second launch) and output items (third launch).
  *
  * rtcdf_batch_plan_create builds the work list from HOST arrays
  * (seg_offsets: S+1 entries, nondecreasing; seg_minVal / seg_maxVal: S) and
