@@ -160,8 +160,8 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
         if (!ev_pool.empty()) {
             e = ev_pool.back();
             ev_pool.pop_back();
-        } else {
-            cudaEventCreateWithFlags(&e, cudaEventDisableTiming);
+        } else if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) {
+            e = nullptr;
         }
         return e;
     };
@@ -225,7 +225,10 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
                     break;
                 }
                 req_ev[next] = take_event();
-                cudaEventRecord(req_ev[next], fill_streams[fs]);
+                if (!req_ev[next] || cudaEventRecord(req_ev[next], fill_streams[fs]) != cudaSuccess) {
+                    err = RTCDF_ERR_CUDA;
+                    break;
+                }
             }
             results[next].admit_s = secs(t0);
             pending.push_back(next);
@@ -357,8 +360,15 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
                 }
             }
             batch_cap = cfg->max_batch;
-            cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming);
-            cudaEventRecord(L.done, s);
+            if (cudaEventCreateWithFlags(&L.done, cudaEventDisableTiming) != cudaSuccess) {
+                err = RTCDF_ERR_CUDA;
+                break;
+            }
+            if (cudaEventRecord(L.done, s) != cudaSuccess) {
+                cudaEventDestroy(L.done);
+                err = RTCDF_ERR_CUDA;
+                break;
+            }
             for (int64_t i : L.reqs) results[i].launch_s = launch_t, results[i].batch_id = (int32_t)(launches_batched + launches_single);
             stream_busy[k] = true;
             if (L.large) large_inflight++;
