@@ -356,6 +356,16 @@ rtcdf_status rtcdf_sort_batched_device(const int32_t *in, int32_t *out, const in
  * rtcdf_serve_sequential serves the same trace one request at a time
  * (rtcdf_sort_ws on one stream, waiting for each) as the comparison.
  * Both allocate, synchronise and return when every request is done.
+ *
+ * Errors: RTCDF_ERR_INVALID_ARG for a null config or fill function or a null
+ * array with count > 0 (rtcdf_serve_trace also: num_streams outside 1..16,
+ * max_batch < 1); RTCDF_ERR_RANGE for a request with R outside 1..2^20 or
+ * n >= 2^32 (rtcdf_serve_sequential: R outside 1..RTCDF_MAX_R);
+ * RTCDF_ERR_NO_MEMORY when the slab, the digests or the pinned staging cannot
+ * be allocated; RTCDF_ERR_CUDA when a CUDA call fails or `fill` returns
+ * nonzero.  On an error the trace stops: requests not yet served keep status
+ * -1, and every resource the call created is released.  A request that can
+ * never fit the budget gets status RTCDF_ERR_NO_MEMORY and the trace goes on.
  */
 typedef int (*rtcdf_fill_fn)(int32_t *dev_out, uint64_t n, uint64_t first, int64_t minVal,
                              int64_t R, int dist, uint64_t seed, rtcdf_stream_t stream);
@@ -386,7 +396,7 @@ typedef struct {
 typedef struct {
     double admit_s, launch_s, done_s;
     uint64_t digest;
-    int32_t status;             /* 0 done, else an rtcdf_status */
+    int32_t status;             /* 0 done, -1 not served (the call failed), else an rtcdf_status */
     int32_t batch_id;           /* launch that served the request */
 } rtcdf_result;
 

@@ -129,9 +129,14 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
     }
     const int K = cfg->num_streams;
     const bool want_digest = cfg->digests != 0;
-    int dev = 0, sms = 0;
+    int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RTCDF_ERR_CUDA;
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    // A failed setup call is remembered and skips the trace; everything
+    // created before it is released at the end as usual.
+    rtcdf_status err = RTCDF_OK;
+    auto check = [&](cudaError_t e, rtcdf_status code) {
+        if (e != cudaSuccess && !err) err = code;
+    };
 
     // Device slab = admission budget.  Per stream, a single-array workspace
     // for the widest range is carved out of it first.
@@ -141,18 +146,19 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
     size_t ws_bytes = 0;
     rtcdf_workspace_size(maxR, &ws_bytes);
     std::vector<size_t> ws_off(K);
-    std::vector<cudaStream_t> streams(K);
+    std::vector<cudaStream_t> streams(K, nullptr);
     for (int k = 0; k < K; k++) {
         if (!alloc.alloc(ws_bytes, &ws_off[k])) { cudaFree(slab); return RTCDF_ERR_NO_MEMORY; }
-        cudaMemset(slab + ws_off[k], 0, ws_bytes);
-        cudaStreamCreateWithFlags(&streams[k], cudaStreamNonBlocking);
+        check(cudaMemset(slab + ws_off[k], 0, ws_bytes), RTCDF_ERR_CUDA);
+        check(cudaStreamCreateWithFlags(&streams[k], cudaStreamNonBlocking), RTCDF_ERR_CUDA);
     }
     // Inputs are written on their own streams (round robin), so writing the
     // next arrivals overlaps the sorts already running.  Each request's write
     // is marked by an event (from a pool, returned when the request retires):
     // a launch waits for its own requests' inputs only.
-    std::vector<cudaStream_t> fill_streams(K);
-    for (int k = 0; k < K; k++) cudaStreamCreateWithFlags(&fill_streams[k], cudaStreamNonBlocking);
+    std::vector<cudaStream_t> fill_streams(K, nullptr);
+    for (int k = 0; k < K; k++)
+        check(cudaStreamCreateWithFlags(&fill_streams[k], cudaStreamNonBlocking), RTCDF_ERR_CUDA);
     int fill_rr = 0;
     std::vector<cudaEvent_t> ev_pool, req_ev((size_t)count, nullptr);
     auto take_event = [&]() {
@@ -167,15 +173,16 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
     };
     uint64_t *d_digest = nullptr;
     if (want_digest) {
-        cudaMalloc(&d_digest, sizeof(uint64_t) * (size_t)std::max<int64_t>(1, count));
-        cudaMemset(d_digest, 0, sizeof(uint64_t) * (size_t)std::max<int64_t>(1, count));
+        const size_t db = sizeof(uint64_t) * (size_t)std::max<int64_t>(1, count);
+        check(cudaMalloc(&d_digest, db), RTCDF_ERR_NO_MEMORY);
+        if (d_digest) check(cudaMemset(d_digest, 0, db), RTCDF_ERR_CUDA);
     }
     // Pinned staging for plan uploads, one per stream (reused once that
     // stream's previous launch has completed).
     const size_t stage_bytes = 64u << 20;
     std::vector<char *> stage(K, nullptr);
-    for (int k = 0; k < K; k++) cudaMallocHost(&stage[k], stage_bytes);
-    cudaDeviceSynchronize();
+    for (int k = 0; k < K; k++) check(cudaMallocHost(&stage[k], stage_bytes), RTCDF_ERR_NO_MEMORY);
+    check(cudaDeviceSynchronize(), RTCDF_ERR_CUDA);
 
     std::vector<size_t> slot_off(count, 0), slot_bytes(count, 0);
     for (int64_t i = 0; i < count; i++) {
@@ -188,7 +195,6 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
     int64_t next = 0, done = 0;
     uint64_t launches_batched = 0, launches_single = 0, batched_requests = 0;
     int max_inflight = 0;
-    rtcdf_status err = RTCDF_OK;
     const size_t reserve = std::min<size_t>(cfg->budget_bytes / 8, (size_t)1 << 30);
     int batch_cap = cfg->max_batch;
     const int max_large = cfg->max_large_inflight > 0 ? cfg->max_large_inflight : K;
@@ -314,7 +320,10 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
                 memcpy(stage[k], hp.segs.data(), seg_b);
                 memcpy(stage[k] + seg_b, hp.items.data(), item_b);
                 memcpy(stage[k] + dig_at, dg.data(), dig_b);
-                cudaMemcpyAsync(tab, stage[k], dig_at + dig_b, cudaMemcpyHostToDevice, s);
+                if (cudaMemcpyAsync(tab, stage[k], dig_at + dig_b, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+                    err = RTCDF_ERR_CUDA;
+                    break;
+                }
             }
             if (single) {
                 const int64_t i = L.reqs[0];
@@ -326,7 +335,10 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
                 launches_single++;
             } else {
                 uint32_t *ws = reinterpret_cast<uint32_t *>(tab + tab_b);
-                cudaMemsetAsync(ws, 0, wsb, s);
+                if (cudaMemsetAsync(ws, 0, wsb, s) != cudaSuccess) {
+                    err = RTCDF_ERR_CUDA;
+                    break;
+                }
                 BatchArgs a;
                 a.in = reinterpret_cast<const int32_t *>(slab);
                 a.out = reinterpret_cast<int32_t *>(slab);
@@ -401,12 +413,14 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
         }
         if (!progressed) std::this_thread::yield();
     }
-    cudaDeviceSynchronize();
+    check(cudaDeviceSynchronize(), RTCDF_ERR_CUDA);
     const double makespan = secs(t0);
-    if (want_digest) {
+    if (want_digest && !err && count > 0) {
         std::vector<uint64_t> h((size_t)count);
-        cudaMemcpy(h.data(), d_digest, sizeof(uint64_t) * (size_t)count, cudaMemcpyDeviceToHost);
-        for (int64_t i = 0; i < count; i++) results[i].digest = h[i];
+        check(cudaMemcpy(h.data(), d_digest, sizeof(uint64_t) * (size_t)count, cudaMemcpyDeviceToHost),
+              RTCDF_ERR_CUDA);
+        if (!err)
+            for (int64_t i = 0; i < count; i++) results[i].digest = h[i];
     }
     uint64_t keys = 0;
     for (int64_t i = 0; i < count; i++) keys += reqs[i].n;
@@ -421,10 +435,10 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
         stats->peak_bytes = alloc.peak();
     }
     for (int k = 0; k < K; k++) {
-        cudaStreamDestroy(streams[k]);
+        if (streams[k]) cudaStreamDestroy(streams[k]);
+        if (fill_streams[k]) cudaStreamDestroy(fill_streams[k]);
         cudaFreeHost(stage[k]);
     }
-    for (int k = 0; k < K; k++) cudaStreamDestroy(fill_streams[k]);
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : req_ev)
         if (e) cudaEventDestroy(e);
@@ -442,7 +456,9 @@ rtcdf_status rtcdf_serve_sequential(const rtcdf_server_config *cfg, const rtcdf_
     int64_t maxR = 1;
     for (int64_t i = 0; i < count; i++) {
         const int64_t R = reqs[i].maxVal - reqs[i].minVal;
-        if (R <= 0 || R > RTCDF_MAX_R) return RTCDF_ERR_RANGE;
+        if (R <= 0 || R > RTCDF_MAX_R || reqs[i].minVal < INT32_MIN ||
+            reqs[i].maxVal > ((int64_t)1 << 31) || reqs[i].n >= (1ull << 32))
+            return RTCDF_ERR_RANGE;
         max_n = std::max<uint64_t>(max_n, reqs[i].n);
         maxR = std::max(maxR, R);
     }
@@ -451,18 +467,26 @@ rtcdf_status rtcdf_serve_sequential(const rtcdf_server_config *cfg, const rtcdf_
     char *buf = nullptr;
     if (cudaMalloc(&buf, max_n * 8 + ws_bytes + 512) != cudaSuccess) return RTCDF_ERR_NO_MEMORY;
     char *ws = buf + (max_n * 8 + 255) / 256 * 256;
-    cudaMemset(ws, 0, ws_bytes);
+    rtcdf_status err = RTCDF_OK;
+    auto check = [&](cudaError_t e, rtcdf_status code) {
+        if (e != cudaSuccess && !err) err = code;
+    };
+    check(cudaMemset(ws, 0, ws_bytes), RTCDF_ERR_CUDA);
     uint64_t *d_digest = nullptr;
     DigestSeg *d_seg = nullptr;
     if (cfg->digests) {
-        cudaMalloc(&d_digest, sizeof(uint64_t) * (size_t)std::max<int64_t>(1, count));
-        cudaMemset(d_digest, 0, sizeof(uint64_t) * (size_t)std::max<int64_t>(1, count));
-        cudaMalloc(&d_seg, sizeof(DigestSeg));
+        const size_t db = sizeof(uint64_t) * (size_t)std::max<int64_t>(1, count);
+        check(cudaMalloc(&d_digest, db), RTCDF_ERR_NO_MEMORY);
+        if (d_digest) check(cudaMemset(d_digest, 0, db), RTCDF_ERR_CUDA);
+        check(cudaMalloc(&d_seg, sizeof(DigestSeg)), RTCDF_ERR_NO_MEMORY);
     }
-    cudaStream_t s;
-    cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
-    cudaDeviceSynchronize();
-    rtcdf_status err = RTCDF_OK;
+    cudaStream_t s = nullptr;
+    check(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), RTCDF_ERR_CUDA);
+    check(cudaDeviceSynchronize(), RTCDF_ERR_CUDA);
+    for (int64_t i = 0; i < count; i++) {
+        results[i] = rtcdf_result{};
+        results[i].status = -1;
+    }
     const Clock::time_point t0 = Clock::now();
     for (int64_t i = 0; i < count && !err; i++) {
         while (secs(t0) < reqs[i].arrival_s) std::this_thread::yield();
@@ -478,21 +502,23 @@ rtcdf_status rtcdf_serve_sequential(const rtcdf_server_config *cfg, const rtcdf_
                                 (rtcdf_stream_t)s);
             if (cfg->digests && !err) {
                 DigestSeg d{(uint64_t)reqs[i].n, reqs[i].n, (uint64_t)i};
-                cudaMemcpyAsync(d_seg, &d, sizeof(d), cudaMemcpyHostToDevice, s);
+                check(cudaMemcpyAsync(d_seg, &d, sizeof(d), cudaMemcpyHostToDevice, s), RTCDF_ERR_CUDA);
                 const uint32_t chunks = (uint32_t)std::min<uint64_t>(256, (reqs[i].n + 8191) / 8192);
                 digest_kernel<<<dim3(chunks, 1), 256, 0, s>>>(reinterpret_cast<const int32_t *>(buf), d_seg, d_digest);
             }
         }
-        cudaStreamSynchronize(s);
+        check(cudaStreamSynchronize(s), RTCDF_ERR_CUDA);
         results[i].done_s = secs(t0);
         results[i].status = err ? (int32_t)err : 0;
         results[i].batch_id = (int32_t)i;
     }
     const double makespan = secs(t0);
-    if (cfg->digests) {
+    if (cfg->digests && !err && count > 0) {
         std::vector<uint64_t> h((size_t)count);
-        cudaMemcpy(h.data(), d_digest, sizeof(uint64_t) * (size_t)count, cudaMemcpyDeviceToHost);
-        for (int64_t i = 0; i < count; i++) results[i].digest = h[i];
+        check(cudaMemcpy(h.data(), d_digest, sizeof(uint64_t) * (size_t)count, cudaMemcpyDeviceToHost),
+              RTCDF_ERR_CUDA);
+        if (!err)
+            for (int64_t i = 0; i < count; i++) results[i].digest = h[i];
     }
     uint64_t keys = 0;
     for (int64_t i = 0; i < count; i++) keys += reqs[i].n;
@@ -504,7 +530,7 @@ rtcdf_status rtcdf_serve_sequential(const rtcdf_server_config *cfg, const rtcdf_
         stats->max_inflight = 1;
         stats->peak_bytes = max_n * 8 + ws_bytes;
     }
-    cudaStreamDestroy(s);
+    if (s) cudaStreamDestroy(s);
     cudaFree(d_seg);
     cudaFree(d_digest);
     cudaFree(buf);

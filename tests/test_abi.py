@@ -123,3 +123,35 @@ def test_batched_plan_rejects_bad_work_item_sizes_on_host(field, value):
                                                 b.ctypes.data_as(ctypes.c_void_p), 1, ctypes.byref(p),
                                                 ctypes.byref(h))
     assert rc == rtcdf.ERR_INVALID_ARG and not h.value
+
+
+def test_server_rejects_bad_config_and_requests_on_host():
+    import ctypes
+    lib = rtcdf.lib()
+    res = (rtcdf.Result * 2)()
+    st = rtcdf.ServeStats()
+    good = rtcdf.make_requests([10, 20], [0, -5], [128, 1000], [0, 1], [1, 2], [0.0, 0.0])
+
+    def cfg(**kw):
+        c = rtcdf.ServerConfig(budget_bytes=1 << 30, num_streams=2, max_batch=8, single_min_keys=1 << 20,
+                               fill=1, digests=0, max_large_inflight=0)
+        for k, v in kw.items():
+            setattr(c, k, v)
+        return c
+
+    for fname in ("rtcdf_serve_trace", "rtcdf_serve_sequential"):
+        f = getattr(lib, fname)
+        assert f(None, good, 2, res, ctypes.byref(st)) == rtcdf.ERR_INVALID_ARG
+        assert f(ctypes.byref(cfg(fill=None)), good, 2, res, ctypes.byref(st)) == rtcdf.ERR_INVALID_ARG
+        assert f(ctypes.byref(cfg()), None, 2, res, ctypes.byref(st)) == rtcdf.ERR_INVALID_ARG
+        assert f(ctypes.byref(cfg()), good, 2, None, ctypes.byref(st)) == rtcdf.ERR_INVALID_ARG
+        assert f(ctypes.byref(cfg()), good, -1, res, ctypes.byref(st)) == rtcdf.ERR_INVALID_ARG
+        for n, mn, mx in [(10, 5, 5), (10, 0, rtcdf.MAX_R + 1), (10, -(1 << 31) - 1, 0), (1 << 32, 0, 128)]:
+            bad = rtcdf.make_requests([10, n], [0, mn], [128, mx], [0, 0], [1, 2], [0.0, 0.0])
+            assert f(ctypes.byref(cfg()), bad, 2, res, ctypes.byref(st)) == rtcdf.ERR_RANGE
+    # the continuous-batching server also bounds streams, batch size and R (segmented launches)
+    trace = lib.rtcdf_serve_trace
+    for kw in ({"num_streams": 0}, {"num_streams": 17}, {"max_batch": 0}):
+        assert trace(ctypes.byref(cfg(**kw)), good, 2, res, ctypes.byref(st)) == rtcdf.ERR_INVALID_ARG
+    wide = rtcdf.make_requests([10], [0], [(1 << 20) + 1], [0], [1], [0.0])
+    assert trace(ctypes.byref(cfg()), wide, 1, res, ctypes.byref(st)) == rtcdf.ERR_RANGE
