@@ -240,7 +240,12 @@ rtcdf_status rtcdf_sort_ex(const int32_t *in, int32_t *out, uint64_t n, int64_t 
  * ordered after earlier work on `stream`).  When `stream` completes, `out`
  * holds the result; `in` must not be modified before then.  Device status:
  * rtcdf_status_get does not cover these calls; keys outside [minVal, maxVal)
- * leave `out` unspecified.
+ * leave `out` unspecified.  The library-owned buffers (sized for the largest
+ * n seen), streams and events live until the process exits.  Errors:
+ * RTCDF_ERR_RANGE and RTCDF_ERR_INVALID_ARG as for rtcdf_sort (checked
+ * before any CUDA call); RTCDF_ERR_NO_MEMORY when device buffers cannot be
+ * allocated; RTCDF_ERR_CUDA when creating the streams or events, a copy, an
+ * event record or a stream wait fails.
  */
 rtcdf_status rtcdf_sort_host(const int32_t *in, int32_t *out, uint64_t n, int64_t minVal,
                              int64_t maxVal, rtcdf_stream_t stream);

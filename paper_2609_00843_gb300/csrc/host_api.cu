@@ -37,6 +37,7 @@ struct BufSet {
 };
 
 struct HostCtx {
+    bool ready = false;              // streams and events below all exist
     BufSet set[2];
     int next = 0;
     void *ws = nullptr;
@@ -50,6 +51,28 @@ std::mutex g_host_mu;
 std::map<std::pair<int, cudaStream_t>, HostCtx> g_host;
 
 constexpr uint64_t kChunk = 1ull << 22;  // keys per uploaded chunk (16 MB)
+
+// Creates the context's streams and events, all or none.
+bool init_ctx(HostCtx &c) {
+    cudaStream_t *streams[3] = {&c.up, &c.down, &c.comp};
+    cudaEvent_t *events[6] = {&c.ev_done, &c.ev_chunk, &c.set[0].in_free, &c.set[0].out_free,
+                              &c.set[1].in_free, &c.set[1].out_free};
+    bool ok = true;
+    for (cudaStream_t *p : streams)
+        ok = ok && cudaStreamCreateWithFlags(p, cudaStreamNonBlocking) == cudaSuccess;
+    for (cudaEvent_t *p : events) ok = ok && cudaEventCreateWithFlags(p, cudaEventDisableTiming) == cudaSuccess;
+    // Both sets start free: their events complete with the (empty) compute stream.
+    for (BufSet &b : c.set)
+        ok = ok && cudaEventRecord(b.in_free, c.comp) == cudaSuccess &&
+             cudaEventRecord(b.out_free, c.comp) == cudaSuccess;
+    if (!ok) {
+        for (cudaEvent_t *p : events)
+            if (*p) cudaEventDestroy(*p), *p = nullptr;
+        for (cudaStream_t *p : streams)
+            if (*p) cudaStreamDestroy(*p), *p = nullptr;
+    }
+    return c.ready = ok;
+}
 
 }  // namespace
 
@@ -67,22 +90,12 @@ extern "C" rtcdf_status rtcdf_sort_host(const int32_t *h_in, int32_t *h_out, uin
     if (cudaGetDevice(&dev) != cudaSuccess) return RTCDF_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_host_mu);
     HostCtx &c = g_host[std::make_pair(dev, s)];
-    if (!c.up) {
-        if (cudaStreamCreateWithFlags(&c.up, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&c.down, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaStreamCreateWithFlags(&c.comp, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c.ev_done, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&c.ev_chunk, cudaEventDisableTiming) != cudaSuccess)
-            return RTCDF_ERR_CUDA;
-        for (BufSet &b : c.set) {
-            if (cudaEventCreateWithFlags(&b.in_free, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&b.out_free, cudaEventDisableTiming) != cudaSuccess)
-                return RTCDF_ERR_CUDA;
-            cudaEventRecord(b.in_free, c.comp);
-            cudaEventRecord(b.out_free, c.comp);
-        }
-    }
+    if (!c.ready && !init_ctx(c)) return RTCDF_ERR_CUDA;
     cudaStream_t cs = c.comp;
+    // Every record and wait below orders a buffer's reuse: one that fails
+    // ends the call with RTCDF_ERR_CUDA.
+    auto rec = [](cudaEvent_t e, cudaStream_t st) { return cudaEventRecord(e, st) == cudaSuccess; };
+    auto wait = [](cudaStream_t st, cudaEvent_t e) { return cudaStreamWaitEvent(st, e, 0) == cudaSuccess; };
     // Workspace (shared by both sets: the sorts themselves are ordered on the
     // compute stream).
     const size_t need_ws = ws_required(R);
@@ -98,8 +111,7 @@ extern "C" rtcdf_status rtcdf_sort_host(const int32_t *h_in, int32_t *h_out, uin
     c.next ^= 1;
     if (b.cap < n) {
         // Growing: wait until nothing uses the old buffers, then replace them.
-        cudaStreamWaitEvent(cs, b.in_free, 0);
-        cudaStreamWaitEvent(cs, b.out_free, 0);
+        if (!wait(cs, b.in_free) || !wait(cs, b.out_free)) return RTCDF_ERR_CUDA;
         if (b.in) cudaFreeAsync(b.in, cs);
         if (b.out) cudaFreeAsync(b.out, cs);
         b.in = b.out = nullptr;
@@ -108,33 +120,27 @@ extern "C" rtcdf_status rtcdf_sort_host(const int32_t *h_in, int32_t *h_out, uin
             cudaMallocAsync((void **)&b.out, n * 4, cs) != cudaSuccess)
             return RTCDF_ERR_NO_MEMORY;
         b.cap = n;
-        cudaEventRecord(b.in_free, cs);
-        cudaEventRecord(b.out_free, cs);
+        if (!rec(b.in_free, cs) || !rec(b.out_free, cs)) return RTCDF_ERR_CUDA;
     }
     // Upload in chunks; the histogram of chunk k waits only for chunk k (the
     // wait takes the event as last recorded, so one event serves every chunk).
-    cudaStreamWaitEvent(c.up, b.in_free, 0);
+    if (!wait(c.up, b.in_free)) return RTCDF_ERR_CUDA;
     for (uint64_t k0 = 0; k0 < n; k0 += kChunk) {
         const uint64_t k1 = std::min(n, k0 + kChunk);
         if (cudaMemcpyAsync(b.in + k0, h_in + k0, (k1 - k0) * 4, cudaMemcpyHostToDevice, c.up) != cudaSuccess)
             return RTCDF_ERR_CUDA;
-        if (cudaEventRecord(c.ev_chunk, c.up) != cudaSuccess ||
-            cudaStreamWaitEvent(cs, c.ev_chunk, 0) != cudaSuccess)
-            return RTCDF_ERR_CUDA;
+        if (!rec(c.ev_chunk, c.up) || !wait(cs, c.ev_chunk)) return RTCDF_ERR_CUDA;
         rtcdf_status st = host_pipeline_hist(b.in + k0, k1 - k0, minVal, R, c.ws, c.ws_bytes, cs);
         if (st) return st;
     }
-    cudaEventRecord(b.in_free, cs);
     // Scan and output, once the previous download from this set is done.
-    cudaStreamWaitEvent(cs, b.out_free, 0);
+    if (!rec(b.in_free, cs) || !wait(cs, b.out_free)) return RTCDF_ERR_CUDA;
     rtcdf_status st = host_pipeline_finish(b.out, n, minVal, R, c.ws, c.ws_bytes, cs);
     if (st) return st;
-    cudaEventRecord(c.ev_done, cs);
-    cudaStreamWaitEvent(c.down, c.ev_done, 0);
+    if (!rec(c.ev_done, cs) || !wait(c.down, c.ev_done)) return RTCDF_ERR_CUDA;
     if (cudaMemcpyAsync(h_out, b.out, n * 4, cudaMemcpyDeviceToHost, c.down) != cudaSuccess)
         return RTCDF_ERR_CUDA;
-    cudaEventRecord(b.out_free, c.down);
     // The caller's stream completes only when the download has.
-    cudaStreamWaitEvent(s, b.out_free, 0);
+    if (!rec(b.out_free, c.down) || !wait(s, b.out_free)) return RTCDF_ERR_CUDA;
     return RTCDF_OK;
 }
