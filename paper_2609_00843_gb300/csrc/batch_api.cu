@@ -349,10 +349,9 @@ rtcdf_status rtcdf_sort_batched(const int32_t *in, int32_t *out, const int64_t *
     if (!st) st = rtcdf_sort_batched_ws(plan, in, out, ws, bytes, stream);
     int32_t bits = 0;
     const rtcdf_status dst = rtcdf_batch_status_get(ws, stream, &bits);  // synchronises `stream`
-    cudaFreeAsync(ws, s);
-    cudaStreamSynchronize(s);
+    const bool freed = cudaFreeAsync(ws, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
     rtcdf_batch_plan_destroy(plan);
-    return st ? st : dst;
+    return st ? st : dst ? dst : freed ? RTCDF_OK : RTCDF_ERR_CUDA;
 }
 
 rtcdf_status rtcdf_sort_batched_device(const int32_t *in, int32_t *out, const int64_t *d_seg_offsets,

@@ -103,10 +103,14 @@ rtcdf_status rtcdf_autotune(const rtcdf_tune_case *cases, int32_t num_cases,
         !times_ms || !geomean || !best)
         return RTCDF_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    std::vector<cudaEvent_t> ev((size_t)reps + 1);
-    for (cudaEvent_t &e : ev)
-        if (cudaEventCreate(&e) != cudaSuccess) return RTCDF_ERR_CUDA;
+    std::vector<cudaEvent_t> ev((size_t)reps + 1, nullptr);
     rtcdf_status result = RTCDF_OK;
+    for (cudaEvent_t &e : ev)
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            e = nullptr;
+            result = RTCDF_ERR_CUDA;
+            break;
+        }
     std::vector<float> t((size_t)reps);
     for (int32_t c = 0; c < num_cases && result == RTCDF_OK; c++) {
         const rtcdf_tune_case &tc = cases[c];
@@ -118,21 +122,25 @@ rtcdf_status rtcdf_autotune(const rtcdf_tune_case *cases, int32_t num_cases,
                                             workspace, ws_bytes, nullptr, stream);
             if (st == RTCDF_ERR_INVALID_ARG) continue;
             if (st) { result = st; break; }
-            cudaEventRecord(ev[0], s);
+            if (cudaEventRecord(ev[0], s) != cudaSuccess) { result = RTCDF_ERR_CUDA; break; }
             for (int32_t r = 0; r < reps && result == RTCDF_OK; r++) {
                 st = rtcdf_sort_ex(tc.in, tc.out, tc.n, tc.minVal, tc.maxVal, &candidates[k], workspace,
                                    ws_bytes, nullptr, stream);
                 if (st) result = st;
-                cudaEventRecord(ev[(size_t)r + 1], s);
+                else if (cudaEventRecord(ev[(size_t)r + 1], s) != cudaSuccess) result = RTCDF_ERR_CUDA;
             }
             if (result) break;
             if (cudaEventSynchronize(ev[(size_t)reps]) != cudaSuccess) { result = RTCDF_ERR_CUDA; break; }
-            for (int32_t r = 0; r < reps; r++) cudaEventElapsedTime(&t[(size_t)r], ev[(size_t)r], ev[(size_t)r + 1]);
+            for (int32_t r = 0; r < reps && !result; r++)
+                if (cudaEventElapsedTime(&t[(size_t)r], ev[(size_t)r], ev[(size_t)r + 1]) != cudaSuccess)
+                    result = RTCDF_ERR_CUDA;
+            if (result) break;
             std::sort(t.begin(), t.end());
             cell = t[(size_t)reps / 2];
         }
     }
-    for (cudaEvent_t &e : ev) cudaEventDestroy(e);
+    for (cudaEvent_t &e : ev)
+        if (e) cudaEventDestroy(e);
     if (result) return result;
     int32_t dev_status = 0;
     rtcdf_status st = rtcdf_ws_status_get(workspace, stream, &dev_status);
