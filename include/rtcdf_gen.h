@@ -26,7 +26,8 @@ extern "C" {
 /*
  * Write keys first .. first + n - 1 of stream `seed` to the device buffer
  * `out` (n int32, caller-owned), asynchronously on `stream`.
- * Returns 0 on success, 1 bad argument, 2 range outside int32, 4 launch error.
+ * Returns 0 on success, 1 bad argument, 2 range outside int32, 4 CUDA error
+ * (no current device, or the launch failed).
  */
 int rtcdf_gen_keys(int32_t *out, uint64_t n, uint64_t first, int64_t minVal, int64_t R,
                    int dist, uint64_t seed, struct CUstream_st *stream);

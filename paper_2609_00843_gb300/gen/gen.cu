@@ -61,10 +61,11 @@ extern "C" int rtcdf_gen_keys(int32_t *out, uint64_t n, uint64_t first, int64_t 
     if (minVal < -(1ll << 31) || minVal + R > (1ll << 31)) return 2;
     if (dist < 0 || dist > 2) return 1;
     int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms <= 0)
+        return 4;
     uint64_t blocks = (n + 255) / 256;
-    uint64_t cap = (uint64_t)(sms > 0 ? sms : 132) * 16;
+    uint64_t cap = (uint64_t)sms * 16;
     if (blocks > cap) blocks = cap;
     gen_kernel<<<(unsigned)blocks, 256, 0, stream>>>(out, n, first, minVal, R, dist, seed);
     return cudaGetLastError() == cudaSuccess ? 0 : 4;
