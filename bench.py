@@ -792,11 +792,22 @@ def main():
         ksrc = ["paper_2609_00843_gb300/csrc/fill.cu", "paper_2609_00843_gb300/csrc/rtcdf_internal.h"]
     avg_launch_s = ktime / launches * 1e-3
     achieved = 4 * n / avg_launch_s / 1e9  # algorithmic: 4n bytes read (hist) or written (fill)
+    # The same fraction split by the number of range tiles m of the launch
+    # (one tile streams the input once; m > 1 tiles re-read it from L2).
+    j = 0 if kname == "hist_kernel" else 2
+    by_tiles = {}
+    for i, c in enumerate(cases):
+        m = -(-c["R"] // rtcdf.rtcdf_plan(n, c["R"]).tile_width)
+        by_tiles.setdefault(m, []).append(stage_ms[i][j] / nsteps)
+    by_tiles = {str(m): {"launches_per_step": len(t),
+                         "frac": round(4 * n / (sum(t) / len(t) * 1e-3) / 1e9 / hbm, 4)}
+                for m, t in sorted(by_tiles.items())}
     roofline = {"bound": "hbm", "achieved": round(achieved, 1), "peak": hbm, "unit": "GB/s",
                 "frac": round(achieved / hbm, 4),
                 "traffic": traffic_for(kname, ksrc),
                 "kernel": kname, "peak_kind": f"{peak_kind} hbm_gbs (copy)",
-                "algorithmic_bytes_per_launch": 4 * n}
+                "algorithmic_bytes_per_launch": 4 * n,
+                "by_range_tiles": by_tiles}
     whole = {"achieved_8n_GBs": round(8 * n * len(cases) / (sort_ms * 1e-3) / 1e9, 1)}
     whole["frac_8n_roofline"] = round(whole["achieved_8n_GBs"] / hbm, 4)
     whole["frac_8n_spec"] = round(whole["achieved_8n_GBs"] / SPEC_HBM_GBS, 4)

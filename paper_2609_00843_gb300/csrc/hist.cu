@@ -15,8 +15,9 @@
 //
 // On GB300 a single shared-memory copy per CTA sustains the HBM read rate for
 // uniform, normal and all-equal inputs alike, so there is no replication.
-// Bytes in flight come from unrolled 16-byte loads (bulk L2 prefetches issued
-// ahead of the loads were measured and gave nothing).
+// Bytes in flight come from unrolled 16-byte loads.  For one tile, bulk L2
+// prefetches issued ahead of the loads gave nothing; for 2 to 8 tiles they are
+// part of the adaptive form below.
 #include <map>
 #include <mutex>
 #include <tuple>
