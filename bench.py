@@ -21,6 +21,7 @@ import argparse
 import hashlib
 import json
 import os
+import re
 import statistics
 import subprocess
 import sys
@@ -145,6 +146,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def code_sha256(src_files) -> str:
+    """sha256 of the kernel sources with comments and whitespace removed, so
+    that an edit of comments alone keeps committed counters valid."""
+    h = hashlib.sha256()
+    for p in src_files:
+        with open(os.path.join(ROOT, p)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", " ", text)
+        h.update(" ".join(text.split()).encode())
+    return h.hexdigest()
+
+
 def traffic_for(kernel: str, src_files):
     """DRAM bytes per launch of `kernel` on the sweep arrays, averaged over the
     ncu captures committed in profiles/ncu_traffic.json -- only if they were
@@ -155,12 +169,9 @@ def traffic_for(kernel: str, src_files):
             table = json.load(f)
     except Exception:
         return None
-    h = hashlib.sha256()
-    for p in src_files:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+    digest = code_sha256(src_files)
     ents = [e for k, e in table.get(kernel, {}).items() if k.startswith("sweep_n1e8")]
-    if not ents or any(e.get("source_sha256") != h.hexdigest() for e in ents):
+    if not ents or any(e.get("code_sha256") != digest for e in ents):
         return None
     return round(sum(e["dram_bytes_per_launch"] for e in ents) / len(ents))
 
