@@ -102,10 +102,14 @@ extern "C" rtcdf_status rtcdf_sort_host(const int32_t *h_in, int32_t *h_out, uin
     if (c.ws_bytes < need_ws) {
         void *p = nullptr;
         if (cudaMallocAsync(&p, need_ws, cs) != cudaSuccess) return RTCDF_ERR_NO_MEMORY;
-        if (cudaMemsetAsync(p, 0, need_ws, cs) != cudaSuccess) return RTCDF_ERR_CUDA;
-        if (c.ws) cudaFreeAsync(c.ws, cs);
+        if (cudaMemsetAsync(p, 0, need_ws, cs) != cudaSuccess) {
+            cudaFreeAsync(p, cs);
+            return RTCDF_ERR_CUDA;
+        }
+        void *old = c.ws;
         c.ws = p;
         c.ws_bytes = need_ws;
+        if (old && cudaFreeAsync(old, cs) != cudaSuccess) return RTCDF_ERR_CUDA;
     }
     BufSet &b = c.set[c.next];
     c.next ^= 1;

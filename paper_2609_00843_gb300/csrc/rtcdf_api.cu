@@ -258,10 +258,14 @@ rtcdf_status cached_workspace(cudaStream_t s, size_t need, void **ptr, size_t *b
         size_t grow = std::max(need, w.bytes * 2);
         void *p = nullptr;
         if (cudaMallocAsync(&p, grow, s) != cudaSuccess) return RTCDF_ERR_NO_MEMORY;
-        if (cudaMemsetAsync(p, 0, grow, s) != cudaSuccess) return RTCDF_ERR_CUDA;
-        if (w.ptr && cudaFreeAsync(w.ptr, s) != cudaSuccess) return RTCDF_ERR_CUDA;
+        if (cudaMemsetAsync(p, 0, grow, s) != cudaSuccess) {
+            cudaFreeAsync(p, s);
+            return RTCDF_ERR_CUDA;
+        }
+        void *old = w.ptr;
         w.ptr = p;
         w.bytes = grow;
+        if (old && cudaFreeAsync(old, s) != cudaSuccess) return RTCDF_ERR_CUDA;
     }
     *ptr = w.ptr;
     *bytes = w.bytes;
