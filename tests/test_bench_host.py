@@ -1,0 +1,62 @@
+"""Host-side pieces of the benchmark (no GPU): the roofline denominator and
+the validity check of the committed DRAM-traffic records."""
+import importlib.util
+import json
+import os
+import shutil
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+HIST = ["paper_2609_00843_gb300/csrc/hist.cu", "paper_2609_00843_gb300/csrc/rtcdf_internal.h"]
+FILL = ["paper_2609_00843_gb300/csrc/fill.cu", "paper_2609_00843_gb300/csrc/rtcdf_internal.h"]
+
+
+def test_peak_is_the_measured_copy_bandwidth(bench):
+    with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+        measured = float(json.load(f)["hbm_gbs"])
+    assert bench.peaks() == (measured, "measured")
+
+
+def test_code_digest_ignores_comments_and_whitespace_only(bench, tmp_path, monkeypatch):
+    src = "// header\nint f(int x) {  /* note */\n    return x + 1;   // tail\n}\n"
+    (tmp_path / "a.cu").write_text(src)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    d0 = bench.code_sha256(["a.cu"])
+    (tmp_path / "a.cu").write_text("/* another\n header */ int f(int x) {\n\treturn x + 1;\n}\n")
+    assert bench.code_sha256(["a.cu"]) == d0
+    (tmp_path / "a.cu").write_text("int f(int x) { return x + 2; }\n")
+    assert bench.code_sha256(["a.cu"]) != d0
+
+
+def test_traffic_records_match_current_kernels(bench):
+    # Every committed capture is of the kernel code as it stands; each record
+    # is within a few percent of the kernel's algorithmic 4n bytes at n = 1e8.
+    for kernel, files in (("hist_kernel", HIST), ("fill_kernel", FILL)):
+        t = bench.traffic_for(kernel, files)
+        assert t is not None, kernel
+        assert 0.8 * 4e8 < t < 1.1 * 4e8, (kernel, t)
+
+
+def test_traffic_is_null_once_the_kernel_changes(bench, tmp_path, monkeypatch):
+    for p in HIST + ["profiles/ncu_traffic.json"]:
+        os.makedirs(tmp_path / os.path.dirname(p), exist_ok=True)
+        shutil.copy(os.path.join(ROOT, p), tmp_path / p)
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.traffic_for("hist_kernel", HIST) is not None
+    with open(tmp_path / HIST[0], "a") as f:
+        f.write("\n// a comment keeps the record\n")
+    assert bench.traffic_for("hist_kernel", HIST) is not None
+    with open(tmp_path / HIST[0], "a") as f:
+        f.write("\nstatic int changed_code = 1;\n")
+    assert bench.traffic_for("hist_kernel", HIST) is None
