@@ -52,13 +52,20 @@ __device__ __forceinline__ int next_run_after(const uint32_t *s_end, int lo, int
 template <int WIN>
 constexpr int kRunWindow = 4 * WIN;
 
+// CTAs issued first that take the LAST output chunks.  With a peaked shape
+// the chunks at both ends of the output cross by far the most runs (the
+// tails, thousands of values of a few keys each); the first ones are issued
+// first anyway, and the last ones, issued last, would end the launch.
+constexpr uint32_t kTailChunksFirst = 32;
+
 template <int WIN>
 __global__ void __launch_bounds__(WIN) fill_kernel(FillArgs a) {
     constexpr int RW = kRunWindow<WIN>;
     __shared__ uint32_t s_end[RW];
     __shared__ int32_t s_val[RW];
     const int tid = threadIdx.x;
-    const uint32_t c = blockIdx.x;
+    const uint32_t K = min(kTailChunksFirst, a.fill_ctas);
+    const uint32_t c = blockIdx.x < K ? a.fill_ctas - K + blockIdx.x : blockIdx.x - K;  // output chunk
 
     // Programmatic dependent of the scan: wait for its results.
     asm volatile("griddepcontrol.wait;" ::: "memory");
