@@ -147,9 +147,10 @@ int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P, const BatchTun
     P->n_scan = (uint32_t)Q.size() - P->n_first;
     for (uint32_t s : small2_ids) Q.push_back(BatchItem{kItemSmall, s, 0, 0, 0, 0});
     P->n_small2 = (uint32_t)small2_ids.size();
-    // Output launch, longest items first (whole chunks, then each segment's
-    // shorter last item by decreasing length), so that short items make the
-    // launch's tail.
+    // Output launch, most expensive items first, so that cheap ones make the
+    // launch's tail.  An item costs its vectors plus the runs it crosses; from
+    // the plan alone the runs are estimated as length x min(R, n) / n (every
+    // value present: exact for uniform keys, too many for peaked shapes).
     const size_t fill0 = Q.size();
     for (uint32_t s : large_ids) {
         const BatchSeg &g = segs[s];
@@ -157,8 +158,12 @@ int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P, const BatchTun
             Q.push_back(BatchItem{kItemFill, s, (uint64_t)f * g.fill_chunk,
                                   std::min<uint64_t>(g.n, (uint64_t)(f + 1) * g.fill_chunk), 0, f});
     }
-    std::stable_sort(Q.begin() + fill0, Q.end(), [](const BatchItem &x, const BatchItem &y) {
-        return x.b - x.a > y.b - y.a;
+    auto fill_cost = [&](const BatchItem &x) {
+        const BatchSeg &g = segs[x.seg];
+        return (double)(x.b - x.a) * (0.25 + (double)std::min(g.R, g.n) / (double)g.n);
+    };
+    std::stable_sort(Q.begin() + fill0, Q.end(), [&](const BatchItem &x, const BatchItem &y) {
+        return fill_cost(x) > fill_cost(y);
     });
     P->n_fill = (uint32_t)Q.size() - P->n_first - P->n_scan - P->n_small2;
     return 0;
