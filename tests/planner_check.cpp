@@ -4,8 +4,10 @@
 // come in ascending order (a chunk's lookback only reaches earlier chunks of
 // its segment, handed out before it), the items of every segment cover its
 // keys and positions exactly once, and the per-segment workspace regions are
-// disjoint.  Usage: planner_check <seed> <segments>; prints "OK" or the first
-// violation.
+// disjoint; the output launch issues its items by non-increasing estimated
+// cost (length x (1/4 + min(R, n) / n): vectors plus the runs crossed when
+// every value is present).  Usage: planner_check <seed> <segments>; prints
+// "OK" or the first violation.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -28,6 +30,7 @@ static int check(const std::vector<SegSpec> &spec, const BatchTuning &tun) {
     const uint32_t S = (uint32_t)spec.size();
     if ((size_t)P.n_first + P.n_scan + P.n_small2 + P.n_fill != P.items.size()) return fail("launch sizes", 0, 0);
     std::vector<uint32_t> small_seen(S, 0), next_chunk(S, 0);
+    double prev_cost = HUGE_VAL;
     std::vector<std::vector<std::pair<uint64_t, uint64_t>>> hist_rng(S), fill_rng(S);
     for (size_t q = 0; q < P.items.size(); q++) {
         const BatchItem &it = P.items[q];
@@ -57,6 +60,11 @@ static int check(const std::vector<SegSpec> &spec, const BatchTuning &tun) {
                 fill_rng[it.seg].push_back({it.a, it.b});
                 if (it.aux >= g.fill_items || it.a != (uint64_t)it.aux * g.fill_chunk)
                     return fail("fill index", (long)q, it.aux);
+                {
+                    const double cost = (double)(it.b - it.a) * (0.25 + (double)std::min(g.R, g.n) / (double)g.n);
+                    if (cost > prev_cost) return fail("output item order", (long)q, (long)cost);
+                    prev_cost = cost;
+                }
                 break;
             default: return fail("item kind", (long)q, it.kind);
         }

@@ -2,7 +2,8 @@
 library, builds plans for random segment shapes under every schedule and
 checks the invariants the three launches rely on (kinds in the right launch,
 scan chunks of a segment in ascending ticket order, exact coverage of keys
-and positions, disjoint workspace regions)."""
+and positions, disjoint workspace regions, output items by non-increasing
+estimated cost)."""
 import os
 import shutil
 import subprocess
