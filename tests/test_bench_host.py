@@ -1,5 +1,6 @@
-"""Host-side pieces of the benchmark (no GPU): the roofline denominator and
-the validity check of the committed DRAM-traffic records."""
+"""Host-side pieces of the benchmark (no GPU): the roofline denominator, the
+validity check of the committed DRAM-traffic records, and the reference arm's
+JSON line (the CPU oracle on a sample of the sweep)."""
 import importlib.util
 import json
 import os
@@ -60,3 +61,21 @@ def test_traffic_is_null_once_the_kernel_changes(bench, tmp_path, monkeypatch):
     with open(tmp_path / HIST[0], "a") as f:
         f.write("\nstatic int changed_code = 1;\n")
     assert bench.traffic_for("hist_kernel", HIST) is None
+
+
+def test_reference_arm_prints_the_contract_line(bench, monkeypatch, capsys):
+    # The reference arm (the CPU oracle) on a small sample of the sweep.
+    import types
+    monkeypatch.setattr(bench, "N_SWEEP", 1_000_000)
+    args = types.SimpleNamespace(steps=1, warmup=0)
+    assert bench.run_reference(args, 0, 1) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["unit"] == "GKeys/s" and line["value"] > 0 and line["higher_is_better"] is True
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"] == {"value": line["value"], "unit": "GKeys/s",
+                           "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+    assert line["config"]["arrays"] == 12 and line["config"]["n_per_array"] == 1_000_000
+    # Other ranks of a multi-process launch do no work and print nothing.
+    assert bench.run_reference(args, 1, 2) == 0
+    assert capsys.readouterr().out == ""
