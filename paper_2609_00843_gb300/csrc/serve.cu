@@ -442,6 +442,7 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
     for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
     for (cudaEvent_t e : req_ev)
         if (e) cudaEventDestroy(e);
+    for (Launch &L : inflight) cudaEventDestroy(L.done);  // launches left by an error
     cudaFree(d_digest);
     cudaFree(slab);
     if (err) return err;
