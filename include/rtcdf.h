@@ -30,6 +30,8 @@
  *  - No entry point synchronizes the device except rtcdf_status_get /
  *    rtcdf_ws_status_get and first-use workspace growth outside stream
  *    capture (which only orders on `stream`).
+ *  - No C++ exception leaves the library: a failed host allocation is
+ *    returned as RTCDF_ERR_NO_MEMORY.
  */
 #ifndef RTCDF_H
 #define RTCDF_H
@@ -49,7 +51,7 @@ typedef enum {
     RTCDF_ERR_RANGE = 2,            /* R <= 0, R > RTCDF_MAX_R, or range outside int32 */
     RTCDF_ERR_KEY_OUT_OF_RANGE = 3, /* device status: a key outside [minVal, maxVal) */
     RTCDF_ERR_CUDA = 4,             /* a CUDA runtime call failed */
-    RTCDF_ERR_NO_MEMORY = 5,        /* workspace allocation failed or too small */
+    RTCDF_ERR_NO_MEMORY = 5,        /* device or host allocation failed, or workspace too small */
     RTCDF_ERR_TIMEOUT = 6           /* device status: a bounded wait gave up */
 } rtcdf_status;
 

@@ -183,7 +183,7 @@ rtcdf_status rtcdf_batch_plan_create(const int64_t *seg_offsets, const int64_t *
 rtcdf_status rtcdf_batch_plan_create_ex(const int64_t *seg_offsets, const int64_t *seg_minVal,
                                         const int64_t *seg_maxVal, int32_t num_segments,
                                         const rtcdf_batch_params *params,
-                                        rtcdf_batch_plan **plan_out) {
+                                        rtcdf_batch_plan **plan_out) try {
     if (!plan_out || num_segments < 0) return RTCDF_ERR_INVALID_ARG;
     BatchTuning tun;
     if (params) {
@@ -251,6 +251,8 @@ rtcdf_status rtcdf_batch_plan_create_ex(const int64_t *seg_offsets, const int64_
     }
     *plan_out = p;
     return RTCDF_OK;
+} catch (...) {  // an allocation failed (std::bad_alloc and the like)
+    return RTCDF_ERR_NO_MEMORY;
 }
 
 rtcdf_status rtcdf_batch_plan_destroy(rtcdf_batch_plan *plan) {
@@ -361,7 +363,7 @@ rtcdf_status rtcdf_sort_batched(const int32_t *in, int32_t *out, const int64_t *
 
 rtcdf_status rtcdf_sort_batched_device(const int32_t *in, int32_t *out, const int64_t *d_seg_offsets,
                                        const int64_t *d_seg_minVal, const int64_t *d_seg_maxVal,
-                                       int32_t num_segments, rtcdf_stream_t stream) {
+                                       int32_t num_segments, rtcdf_stream_t stream) try {
     if (num_segments < 0) return RTCDF_ERR_INVALID_ARG;
     if (num_segments > 0 && (!d_seg_offsets || !d_seg_minVal || !d_seg_maxVal)) return RTCDF_ERR_INVALID_ARG;
     const size_t S = (size_t)num_segments;
@@ -376,6 +378,8 @@ rtcdf_status rtcdf_sort_batched_device(const int32_t *in, int32_t *out, const in
          cudaStreamSynchronize(s) != cudaSuccess))
         return RTCDF_ERR_CUDA;
     return rtcdf_sort_batched(in, out, offs.data(), mn.data(), mx.data(), num_segments, stream);
+} catch (...) {  // an allocation failed (std::bad_alloc and the like)
+    return RTCDF_ERR_NO_MEMORY;
 }
 
 }  // extern "C"

@@ -89,7 +89,13 @@ extern "C" rtcdf_status rtcdf_sort_host(const int32_t *h_in, int32_t *h_out, uin
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RTCDF_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_host_mu);
-    HostCtx &c = g_host[std::make_pair(dev, s)];
+    HostCtx *cp = nullptr;
+    try {
+        cp = &g_host[std::make_pair(dev, s)];
+    } catch (...) {
+        return RTCDF_ERR_NO_MEMORY;
+    }
+    HostCtx &c = *cp;
     if (!c.ready && !init_ctx(c)) return RTCDF_ERR_CUDA;
     cudaStream_t cs = c.comp;
     // Every record and wait below orders a buffer's reuse: one that fails

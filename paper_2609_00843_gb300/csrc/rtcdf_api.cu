@@ -44,7 +44,11 @@ rtcdf_status device_info(DeviceInfo *out) {
         if (cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
             return RTCDF_ERR_CUDA;
         d.smem_optin = (size_t)v;
-        it = g_dev.emplace(dev, d).first;
+        try {
+            it = g_dev.emplace(dev, d).first;
+        } catch (...) {
+            return RTCDF_ERR_NO_MEMORY;
+        }
     }
     *out = it->second;
     return RTCDF_OK;
@@ -112,8 +116,12 @@ rtcdf_status make_plan_with(uint64_t n, uint32_t R, uintptr_t in_addr, uintptr_t
     pl->nvec = (n - head_in) / 4;
 
     int occ = 0;
-    if (hist_max_ctas_per_sm(pl->hist_threads, pl->hist_smem, pl->streaming, &occ) != cudaSuccess)
-        return RTCDF_ERR_CUDA;
+    try {  // the occupancy cache may need memory for a new entry
+        if (hist_max_ctas_per_sm(pl->hist_threads, pl->hist_smem, pl->streaming, &occ) != cudaSuccess)
+            return RTCDF_ERR_CUDA;
+    } catch (...) {
+        return RTCDF_ERR_NO_MEMORY;
+    }
     if (occ < 1) return RTCDF_ERR_INVALID_ARG;
     // g_hist = min(max(1, floor(a_hist * S / m)), ceil(n / (16 * threads)))
     uint64_t g = std::max<uint64_t>(1, (uint64_t)occ * dev.sms / pl->m);
@@ -250,7 +258,13 @@ rtcdf_status cached_workspace(cudaStream_t s, size_t need, void **ptr, size_t *b
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess) return RTCDF_ERR_CUDA;
     std::lock_guard<std::mutex> lk(g_mu);
-    CachedWs &w = g_ws[std::make_pair(dev, s)];
+    CachedWs *wp = nullptr;
+    try {
+        wp = &g_ws[std::make_pair(dev, s)];
+    } catch (...) {
+        return RTCDF_ERR_NO_MEMORY;
+    }
+    CachedWs &w = *wp;
     if (w.bytes < need) {
         cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
         if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return RTCDF_ERR_CUDA;

@@ -115,7 +115,7 @@ double secs(Clock::time_point t0) {
 extern "C" {
 
 rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_request *reqs,
-                               int64_t count, rtcdf_result *results, rtcdf_serve_stats *stats) {
+                               int64_t count, rtcdf_result *results, rtcdf_serve_stats *stats) try {
     if (!cfg || (count > 0 && (!reqs || !results)) || count < 0) return RTCDF_ERR_INVALID_ARG;
     if (!cfg->fill || cfg->num_streams < 1 || cfg->num_streams > 16 || cfg->max_batch < 1)
         return RTCDF_ERR_INVALID_ARG;
@@ -447,10 +447,12 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
     cudaFree(slab);
     if (err) return err;
     return cudaGetLastError() == cudaSuccess ? RTCDF_OK : RTCDF_ERR_CUDA;
+} catch (...) {  // an allocation failed (std::bad_alloc and the like)
+    return RTCDF_ERR_NO_MEMORY;
 }
 
 rtcdf_status rtcdf_serve_sequential(const rtcdf_server_config *cfg, const rtcdf_request *reqs,
-                                    int64_t count, rtcdf_result *results, rtcdf_serve_stats *stats) {
+                                    int64_t count, rtcdf_result *results, rtcdf_serve_stats *stats) try {
     if (!cfg || (count > 0 && (!reqs || !results)) || count < 0 || !cfg->fill)
         return RTCDF_ERR_INVALID_ARG;
     uint64_t max_n = 1;
@@ -536,6 +538,8 @@ rtcdf_status rtcdf_serve_sequential(const rtcdf_server_config *cfg, const rtcdf_
     cudaFree(d_digest);
     cudaFree(buf);
     return err;
+} catch (...) {  // an allocation failed (std::bad_alloc and the like)
+    return RTCDF_ERR_NO_MEMORY;
 }
 
 }  // extern "C"

@@ -43,7 +43,14 @@ namespace rtcdf {
 bool tune_lookup(uint64_t n, uint32_t R, rtcdf_params *out) {
     const int32_t lr = log2_ceil(R), nc = rtcdf_tune_n_class(n);
     std::lock_guard<std::mutex> lk(g_tune_mu);
-    if (!g_loaded) load_builtin_locked();
+    if (!g_loaded) {
+        try {
+            load_builtin_locked();
+        } catch (...) {  // no memory for the table: the built-in rules apply
+            g_table.clear();
+            return false;
+        }
+    }
     // The last entry with the key wins.
     for (auto it = g_table.rbegin(); it != g_table.rend(); ++it) {
         if (it->log2_R == lr && it->n_class == nc) {
@@ -64,7 +71,7 @@ int32_t rtcdf_tune_n_class(uint64_t n) {
     return RTCDF_TUNE_N_LARGE;
 }
 
-rtcdf_status rtcdf_tune_set(const rtcdf_tune_entry *entries, int32_t count) {
+rtcdf_status rtcdf_tune_set(const rtcdf_tune_entry *entries, int32_t count) try {
     if (count < 0 || (count > 0 && !entries)) return RTCDF_ERR_INVALID_ARG;
     for (int32_t i = 0; i < count; i++) {
         const rtcdf_tune_entry &e = entries[i];
@@ -78,12 +85,16 @@ rtcdf_status rtcdf_tune_set(const rtcdf_tune_entry *entries, int32_t count) {
     g_table.assign(entries, entries + count);
     g_loaded = true;
     return RTCDF_OK;
+} catch (...) {  // an allocation failed (std::bad_alloc and the like)
+    return RTCDF_ERR_NO_MEMORY;
 }
 
-rtcdf_status rtcdf_tune_reset(void) {
+rtcdf_status rtcdf_tune_reset(void) try {
     std::lock_guard<std::mutex> lk(g_tune_mu);
     load_builtin_locked();
     return RTCDF_OK;
+} catch (...) {  // an allocation failed (std::bad_alloc and the like)
+    return RTCDF_ERR_NO_MEMORY;
 }
 
 rtcdf_status rtcdf_tune_get(rtcdf_tune_entry *entries, int32_t capacity, int32_t *count) {
@@ -98,7 +109,7 @@ rtcdf_status rtcdf_tune_get(rtcdf_tune_entry *entries, int32_t capacity, int32_t
 rtcdf_status rtcdf_autotune(const rtcdf_tune_case *cases, int32_t num_cases,
                             const rtcdf_params *candidates, int32_t num_candidates, int32_t reps,
                             void *workspace, size_t ws_bytes, float *times_ms, double *geomean,
-                            int32_t *best, rtcdf_stream_t stream) {
+                            int32_t *best, rtcdf_stream_t stream) try {
     if (!cases || num_cases <= 0 || !candidates || num_candidates <= 0 || reps <= 0 || !workspace ||
         !times_ms || !geomean || !best)
         return RTCDF_ERR_INVALID_ARG;
@@ -167,6 +178,8 @@ rtcdf_status rtcdf_autotune(const rtcdf_tune_case *cases, int32_t num_cases,
     }
     *best = b;
     return b < 0 ? RTCDF_ERR_INVALID_ARG : RTCDF_OK;
+} catch (...) {  // an allocation failed (std::bad_alloc and the like)
+    return RTCDF_ERR_NO_MEMORY;
 }
 
 }  // extern "C"
