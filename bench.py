@@ -220,18 +220,52 @@ def run_reference(args, rank, world):
     return 0
 
 
+# Arm core part numbers (MIDR_EL1 bits 4..15) of the implementer Arm (0x41)
+# and NVIDIA (0x4e) cores a GPU host is likely to have.
+_ARM_PARTS = {(0x41, 0xd4f): "Arm Neoverse V2", (0x41, 0xd84): "Arm Neoverse V3",
+              (0x41, 0xd40): "Arm Neoverse V1", (0x41, 0xd0c): "Arm Neoverse N1",
+              (0x41, 0xd49): "Arm Neoverse N2", (0x4e, 0x004): "NVIDIA Carmel"}
+
+
+def _lscpu_model() -> str:
+    import subprocess
+    try:
+        r = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10)
+    except (OSError, subprocess.SubprocessError):
+        return ""
+    for ln in r.stdout.splitlines():
+        if ln.split(":")[0].strip().lower() == "model name" and ":" in ln:
+            name = ln.split(":", 1)[1].strip()
+            if name and name != "-":
+                return name
+    return ""
+
+
+def _midr_model() -> str:
+    try:
+        with open("/sys/devices/system/cpu/cpu0/regs/identification/midr_el1") as f:
+            midr = int(f.read().strip(), 16)
+    except (OSError, ValueError):
+        return ""
+    impl, part = (midr >> 24) & 0xFF, (midr >> 4) & 0xFFF
+    return _ARM_PARTS.get((impl, part), f"Arm core implementer 0x{impl:02x} part 0x{part:03x}")
+
+
 def cpu_info() -> dict:
-    """Host CPU model and core count, for the CPU baseline's record."""
+    """Host CPU model and core count, for the CPU baseline's record: the model
+    name of /proc/cpuinfo (x86), else lscpu's (Arm hosts, whose /proc/cpuinfo
+    has none), else the core named by MIDR_EL1, else the architecture."""
     model = ""
     try:
         with open("/proc/cpuinfo") as f:
             for ln in f:
                 k = ln.split(":")[0].strip().lower()
-                if k in ("model name", "cpu model", "hardware") and ":" in ln:
+                if k in ("model name", "cpu model") and ":" in ln:
                     model = ln.split(":", 1)[1].strip()
                     break
     except OSError:
         pass
+    model = model or _lscpu_model() or _midr_model()
     if not model:
         import platform
         model = platform.processor() or platform.machine()

@@ -25,6 +25,8 @@
  *    nothing.  Errors found by the device (a key outside [minVal, maxVal), a
  *    bounded wait that ran out) are recorded in a device status word that
  *    rtcdf_status_get / rtcdf_ws_status_get read; `out` is then unspecified.
+ *    The status word is sticky: once a bounded wait has run out, sorts on
+ *    that workspace write no output until the status has been read.
  *  - minVal >= INT32_MIN and maxVal <= 2^31 (the range lies in the int32 key
  *    space), 1 <= R <= RTCDF_MAX_R, n < 2^32.  n == 0 returns RTCDF_OK.
  *  - No entry point synchronizes the device except rtcdf_status_get /
@@ -389,6 +391,12 @@ typedef struct {
                                    sorts are bandwidth-bound, so running them one
                                    after another keeps their latency while small
                                    batches still overlap them */
+    int32_t *const *outputs;    /* NULL, or `count` HOST pointers (entries may be
+                                   NULL): request i's sorted keys are copied to
+                                   outputs[i] (n int32) once its launch has
+                                   completed, before its memory is released.  The
+                                   copy is synchronous and holds up the serving
+                                   loop: leave this NULL when timing. */
 } rtcdf_server_config;
 
 typedef struct {
@@ -439,9 +447,12 @@ rtcdf_status rtcdf_serve_sequential(const rtcdf_server_config *cfg, const rtcdf_
  * device, on the current device); make that first call before any CUDA graph
  * capture.  All calls on a device share the array and it keeps what the last
  * call left, so each call clears the part that must start at zero; calls that
- * overlap on the GPU (unordered streams) race and must not be issued.  Device-
- * detected errors (a key outside [minVal, maxVal)) are not reported by this
- * entry point: the caller guarantees the range, as Section 2.1 assumes.
+ * overlap on the GPU (unordered streams) race and must not be issued.  This
+ * entry point reports no device-detected error: neither a key outside
+ * [minVal, maxVal) nor a bounded wait that ran out (which only overlapping
+ * calls can cause) reaches the caller, and `out` is then unspecified.  The
+ * caller guarantees that every key lies in [minVal, maxVal) and that calls on
+ * one device are ordered.
  */
 #define RTCDF_STATIC_MAX_R (1LL << 16)
 #define RTCDF_STATIC_WS_BYTES (1u << 20)

@@ -33,7 +33,7 @@
 #define OR_ERR_KEY_OUT_OF_RANGE 3
 #define OR_ERR_NO_MEMORY 5
 
-/* Largest range the oracle accepts: 2^31 values (an int32 key space). */
+/* Largest range the oracle accepts: 2^32 values (the whole int32 key space). */
 #define OR_MAX_R (((int64_t)1) << 32)
 
 static int range_size(int64_t minVal, int64_t maxVal, int64_t *R) {

@@ -417,7 +417,13 @@ __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs 
     // plan's first launch began.)
     if (tid == 0) s_ticket = atomicAdd(&a.ctl->scan_ticket, 1u);
     __syncthreads();
-    if (s_ticket >= a.n_scan) return;  // only with a workspace whose ticket was not zero
+    if (s_ticket >= a.n_scan) {
+        // Only with a workspace whose ticket was not zero: the chunk this
+        // ticket stood for is never published, so the output launch must not
+        // trust the run tables.
+        if (tid == 0) atomicOr(&a.ctl->status, kDevTimeout);
+        return;
+    }
     const BatchItem it = a.items[a.n_first + s_ticket];
     const BatchSeg g = a.segs[it.seg];
     asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -572,11 +578,17 @@ __global__ void __launch_bounds__(kFillCtaThreads) seg_fill_kernel(BatchArgs a) 
         uint64_t *state = reinterpret_cast<uint64_t *>(a.ws_u32 + g.state_off);
         for (uint32_t i = tid; i < g.scan_chunks; i += nt) state[i] = 0;
     }
-    const uint32_t D = a.seg_ctl[it.seg].num_runs;
+    // A wait that ran out (or a stray scan ticket) leaves run tables
+    // incomplete: write nothing (the status word reports it).
+    if (a.ctl->status & kDevTimeout) return;
+    // Indices into the segment's run table stay below its R entries whatever
+    // the scan left behind.
+    const uint32_t D = min(a.seg_ctl[it.seg].num_runs, g.R);
+    if (D == 0) return;
     const uint32_t *run_end = a.ws_u32 + g.run_end_off;
     const int32_t *run_val = reinterpret_cast<const int32_t *>(a.ws_u32 + g.run_val_off);
     const uint32_t *start_run = a.ws_u32 + g.start_run_off;
-    uint32_t k_cur = start_run[it.aux];
+    uint32_t k_cur = min(start_run[it.aux], D - 1);
     // Last run this item can need: the one holding the next item's first position.
     const uint32_t k_last = (it.aux + 1 < g.fill_items) ? min(start_run[it.aux + 1], D - 1) : D - 1;
     int32_t *out = a.out + g.out_off;

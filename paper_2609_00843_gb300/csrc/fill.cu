@@ -72,11 +72,20 @@ __global__ void __launch_bounds__(WIN) fill_kernel(FillArgs a) {
     for (uint32_t i = c * WIN + tid; i < a.scan_chunks; i += a.fill_ctas * WIN) a.scan_state[i] = 0;
     if (c == 0 && tid == 0) a.ctl->scan_ticket = 0;
 
+    // A wait that ran out (or a stray scan ticket) leaves the run table and the
+    // start runs incomplete: write nothing (the output is unspecified then and
+    // the status word says so).  The status is sticky until read, so once it
+    // is set later sorts on the workspace write nothing either.
+    if (a.ctl->status & kDevTimeout) return;
+
     const uint32_t n = (uint32_t)a.n, head = a.head, fc = (uint32_t)a.fill_chunk;
     const uint32_t P0 = (c == 0) ? 0u : head + c * fc;
     const uint32_t P1 = (c + 1 == a.fill_ctas) ? n : head + (c + 1) * fc;
-    const uint32_t D = a.ctl->num_runs;
-    uint32_t k_cur = a.start_run[c];
+    // Every index into the run table stays below the R entries it holds, even
+    // if the scan's results were not what this sort expects.
+    const uint32_t D = min(a.ctl->num_runs, a.R);
+    if (D == 0) return;
+    uint32_t k_cur = min(a.start_run[c], D - 1);
     // Last run this CTA can need: the one holding the next CTA's first position.
     const uint32_t k_last = (c + 1 < a.fill_ctas) ? min(a.start_run[c + 1], D - 1) : D - 1;
     int4 *vout = reinterpret_cast<int4 *>(a.out + head);  // 16-byte aligned frame

@@ -145,6 +145,9 @@ extern "C" rtcdf_status rtcdf_sort_host(const int32_t *h_in, int32_t *h_out, uin
     }
     // Scan and output, once the previous download from this set is done.
     if (!rec(b.in_free, cs) || !wait(cs, b.out_free)) return RTCDF_ERR_CUDA;
+    // Nobody reads this workspace's status word; clear it so that a wait that
+    // ran out in an earlier call does not stop this call's output kernel.
+    if (cudaMemsetAsync(c.ws, 0, 4, cs) != cudaSuccess) return RTCDF_ERR_CUDA;
     rtcdf_status st = host_pipeline_finish(b.out, n, minVal, R, c.ws, c.ws_bytes, cs);
     if (st) return st;
     if (!rec(c.ev_done, cs) || !wait(c.down, c.ev_done)) return RTCDF_ERR_CUDA;

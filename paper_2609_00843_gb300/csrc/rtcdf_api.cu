@@ -227,6 +227,7 @@ rtcdf_status finish_phase(int32_t *out, uint64_t n, int64_t minVal, uint32_t R, 
     f.out = out; f.n = n; f.fill_chunk = pl.fill_chunk; f.head = head_out;
     f.fill_ctas = pl.fill_ctas; f.run_end = run_end; f.run_val = run_val;
     f.start_run = start_run; f.ctl = ctl; f.scan_state = state; f.scan_chunks = L.scan_chunks;
+    f.R = R;
     if (launch_fill(f, pl.fill_threads, s) != cudaSuccess) return RTCDF_ERR_CUDA;
     if (ev_fill && cudaEventRecord(ev_fill, s) != cudaSuccess) return RTCDF_ERR_CUDA;
     return RTCDF_OK;

@@ -132,6 +132,7 @@ struct FillArgs {
     Ctl *ctl;
     uint64_t *scan_state;  // reset here for the next call
     uint32_t scan_chunks;
+    uint32_t R;            // entries of run_end / run_val
 };
 cudaError_t launch_fill(const FillArgs &a, int threads, cudaStream_t s);
 

@@ -115,10 +115,14 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs a) {
     asm volatile("griddepcontrol.launch_dependents;");
     const uint32_t chunk = single ? 0u : s_chunk;
     // A ticket past the last chunk only happens with a workspace whose ticket
-    // was not zero (not cleared, or shared by unordered calls): take no chunk.
-    // The chunk that ticket stood for is then never published, and the
-    // lookback of its successor runs out and records kDevTimeout.
-    if (chunk >= a.chunks) return;
+    // was not zero (not cleared, or shared by unordered calls): take no chunk
+    // and record kDevTimeout, since the chunk that ticket stood for is never
+    // published (its successor's lookback would run out too) and the output
+    // kernel must not trust this sort's run table.
+    if (chunk >= a.chunks) {
+        if (tid == 0) atomicOr(&a.ctl->status, kDevTimeout);
+        return;
+    }
     const uint32_t cbase = chunk * kScanChunk;
     const uint32_t base = cbase + tid * kScanItems;
 

@@ -110,6 +110,33 @@ double secs(Clock::time_point t0) {
     return std::chrono::duration<double>(Clock::now() - t0).count();
 }
 
+// Everything rtcdf_serve_trace creates, released by the destructor on every
+// way out -- a normal return, an error, or an exception (a failed host
+// allocation) -- after the device has finished with it.
+struct ServeResources {
+    char *slab = nullptr;
+    uint64_t *d_digest = nullptr;
+    std::vector<cudaStream_t> streams, fill_streams;
+    std::vector<char *> stage;
+    std::vector<cudaEvent_t> ev_pool, req_ev;
+    std::vector<Launch> inflight;
+    ~ServeResources() {
+        cudaDeviceSynchronize();  // nothing in flight still uses the slab or the staging
+        for (cudaStream_t s : streams)
+            if (s) cudaStreamDestroy(s);
+        for (cudaStream_t s : fill_streams)
+            if (s) cudaStreamDestroy(s);
+        for (char *p : stage)
+            if (p) cudaFreeHost(p);
+        for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+        for (cudaEvent_t e : req_ev)
+            if (e) cudaEventDestroy(e);
+        for (Launch &L : inflight) cudaEventDestroy(L.done);  // launches left by an error
+        cudaFree(d_digest);
+        cudaFree(slab);
+    }
+};
+
 }  // namespace
 
 extern "C" {
@@ -138,17 +165,19 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
         if (e != cudaSuccess && !err) err = code;
     };
 
+    ServeResources res;
     // Device slab = admission budget.  Per stream, a single-array workspace
     // for the widest range is carved out of it first.
-    char *slab = nullptr;
+    char *&slab = res.slab;
     if (cudaMalloc(&slab, cfg->budget_bytes) != cudaSuccess) return RTCDF_ERR_NO_MEMORY;
     Slab alloc(cfg->budget_bytes);
     size_t ws_bytes = 0;
     rtcdf_workspace_size(maxR, &ws_bytes);
     std::vector<size_t> ws_off(K);
-    std::vector<cudaStream_t> streams(K, nullptr);
+    std::vector<cudaStream_t> &streams = res.streams;
+    streams.assign(K, nullptr);
     for (int k = 0; k < K; k++) {
-        if (!alloc.alloc(ws_bytes, &ws_off[k])) { cudaFree(slab); return RTCDF_ERR_NO_MEMORY; }
+        if (!alloc.alloc(ws_bytes, &ws_off[k])) return RTCDF_ERR_NO_MEMORY;
         check(cudaMemset(slab + ws_off[k], 0, ws_bytes), RTCDF_ERR_CUDA);
         check(cudaStreamCreateWithFlags(&streams[k], cudaStreamNonBlocking), RTCDF_ERR_CUDA);
     }
@@ -156,11 +185,13 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
     // next arrivals overlaps the sorts already running.  Each request's write
     // is marked by an event (from a pool, returned when the request retires):
     // a launch waits for its own requests' inputs only.
-    std::vector<cudaStream_t> fill_streams(K, nullptr);
+    std::vector<cudaStream_t> &fill_streams = res.fill_streams;
+    fill_streams.assign(K, nullptr);
     for (int k = 0; k < K; k++)
         check(cudaStreamCreateWithFlags(&fill_streams[k], cudaStreamNonBlocking), RTCDF_ERR_CUDA);
     int fill_rr = 0;
-    std::vector<cudaEvent_t> ev_pool, req_ev((size_t)count, nullptr);
+    std::vector<cudaEvent_t> &ev_pool = res.ev_pool, &req_ev = res.req_ev;
+    req_ev.assign((size_t)count, nullptr);
     auto take_event = [&]() {
         cudaEvent_t e = nullptr;
         if (!ev_pool.empty()) {
@@ -171,7 +202,7 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
         }
         return e;
     };
-    uint64_t *d_digest = nullptr;
+    uint64_t *&d_digest = res.d_digest;
     if (want_digest) {
         const size_t db = sizeof(uint64_t) * (size_t)std::max<int64_t>(1, count);
         check(cudaMalloc(&d_digest, db), RTCDF_ERR_NO_MEMORY);
@@ -180,7 +211,8 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
     // Pinned staging for plan uploads, one per stream (reused once that
     // stream's previous launch has completed).
     const size_t stage_bytes = 64u << 20;
-    std::vector<char *> stage(K, nullptr);
+    std::vector<char *> &stage = res.stage;
+    stage.assign(K, nullptr);
     for (int k = 0; k < K; k++) check(cudaMallocHost(&stage[k], stage_bytes), RTCDF_ERR_NO_MEMORY);
     check(cudaDeviceSynchronize(), RTCDF_ERR_CUDA);
 
@@ -190,7 +222,7 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
         results[i].status = -1;
     }
     std::deque<int64_t> pending;            // admitted, input enqueued
-    std::vector<Launch> inflight;
+    std::vector<Launch> &inflight = res.inflight;
     std::vector<bool> stream_busy(K, false);
     int64_t next = 0, done = 0;
     uint64_t launches_batched = 0, launches_single = 0, batched_requests = 0;
@@ -396,6 +428,13 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
                 for (int64_t i : L.reqs) {
                     results[i].done_s = t;
                     results[i].status = 0;
+                    // The result is complete: copy it out if the caller asked.
+                    if (cfg->outputs && cfg->outputs[i] && reqs[i].n &&
+                        cudaMemcpy(cfg->outputs[i], slab + slot_off[i] + 4 * reqs[i].n, 4 * reqs[i].n,
+                                   cudaMemcpyDeviceToHost) != cudaSuccess) {
+                        results[i].status = RTCDF_ERR_CUDA;
+                        if (!err) err = RTCDF_ERR_CUDA;
+                    }
                     alloc.release(slot_off[i], slot_bytes[i]);
                     if (req_ev[i]) ev_pool.push_back(req_ev[i]);  // complete: the launch waited for it
                     req_ev[i] = nullptr;
@@ -434,18 +473,7 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
         stats->max_inflight = max_inflight;
         stats->peak_bytes = alloc.peak();
     }
-    for (int k = 0; k < K; k++) {
-        if (streams[k]) cudaStreamDestroy(streams[k]);
-        if (fill_streams[k]) cudaStreamDestroy(fill_streams[k]);
-        cudaFreeHost(stage[k]);
-    }
-    for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
-    for (cudaEvent_t e : req_ev)
-        if (e) cudaEventDestroy(e);
-    for (Launch &L : inflight) cudaEventDestroy(L.done);  // launches left by an error
-    cudaFree(d_digest);
-    cudaFree(slab);
-    if (err) return err;
+    if (err) return err;  // `res` releases everything the call created
     return cudaGetLastError() == cudaSuccess ? RTCDF_OK : RTCDF_ERR_CUDA;
 } catch (...) {  // an allocation failed (std::bad_alloc and the like)
     return RTCDF_ERR_NO_MEMORY;
@@ -467,7 +495,21 @@ rtcdf_status rtcdf_serve_sequential(const rtcdf_server_config *cfg, const rtcdf_
     }
     size_t ws_bytes = 0;
     rtcdf_workspace_size(maxR, &ws_bytes);
-    char *buf = nullptr;
+    // Released on every way out, after the device has finished with them.
+    struct SeqResources {
+        char *buf = nullptr;
+        uint64_t *d_digest = nullptr;
+        DigestSeg *d_seg = nullptr;
+        cudaStream_t s = nullptr;
+        ~SeqResources() {
+            cudaDeviceSynchronize();
+            if (s) cudaStreamDestroy(s);
+            cudaFree(d_seg);
+            cudaFree(d_digest);
+            cudaFree(buf);
+        }
+    } res;
+    char *&buf = res.buf;
     if (cudaMalloc(&buf, max_n * 8 + ws_bytes + 512) != cudaSuccess) return RTCDF_ERR_NO_MEMORY;
     char *ws = buf + (max_n * 8 + 255) / 256 * 256;
     rtcdf_status err = RTCDF_OK;
@@ -475,15 +517,15 @@ rtcdf_status rtcdf_serve_sequential(const rtcdf_server_config *cfg, const rtcdf_
         if (e != cudaSuccess && !err) err = code;
     };
     check(cudaMemset(ws, 0, ws_bytes), RTCDF_ERR_CUDA);
-    uint64_t *d_digest = nullptr;
-    DigestSeg *d_seg = nullptr;
+    uint64_t *&d_digest = res.d_digest;
+    DigestSeg *&d_seg = res.d_seg;
     if (cfg->digests) {
         const size_t db = sizeof(uint64_t) * (size_t)std::max<int64_t>(1, count);
         check(cudaMalloc(&d_digest, db), RTCDF_ERR_NO_MEMORY);
         if (d_digest) check(cudaMemset(d_digest, 0, db), RTCDF_ERR_CUDA);
         check(cudaMalloc(&d_seg, sizeof(DigestSeg)), RTCDF_ERR_NO_MEMORY);
     }
-    cudaStream_t s = nullptr;
+    cudaStream_t &s = res.s;
     check(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking), RTCDF_ERR_CUDA);
     check(cudaDeviceSynchronize(), RTCDF_ERR_CUDA);
     for (int64_t i = 0; i < count; i++) {
@@ -512,6 +554,9 @@ rtcdf_status rtcdf_serve_sequential(const rtcdf_server_config *cfg, const rtcdf_
         }
         check(cudaStreamSynchronize(s), RTCDF_ERR_CUDA);
         results[i].done_s = secs(t0);
+        if (!err && cfg->outputs && cfg->outputs[i] && reqs[i].n)
+            check(cudaMemcpy(cfg->outputs[i], buf + 4 * reqs[i].n, 4 * reqs[i].n, cudaMemcpyDeviceToHost),
+                  RTCDF_ERR_CUDA);
         results[i].status = err ? (int32_t)err : 0;
         results[i].batch_id = (int32_t)i;
     }
@@ -533,11 +578,7 @@ rtcdf_status rtcdf_serve_sequential(const rtcdf_server_config *cfg, const rtcdf_
         stats->max_inflight = 1;
         stats->peak_bytes = max_n * 8 + ws_bytes;
     }
-    if (s) cudaStreamDestroy(s);
-    cudaFree(d_seg);
-    cudaFree(d_digest);
-    cudaFree(buf);
-    return err;
+    return err;  // `res` releases the buffers and the stream
 } catch (...) {  // an allocation failed (std::bad_alloc and the like)
     return RTCDF_ERR_NO_MEMORY;
 }

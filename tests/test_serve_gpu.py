@@ -1,7 +1,11 @@
 """Continuous-batching server: every request's result is the same alone (served
 one at a time) and in the mix (admitted while others run, batched with them),
-and matches the CPU oracle -- bit-exact, compared through order-dependent
-digests of the sorted outputs."""
+and matches the CPU oracle -- bit-exact.  Whole traces are compared through
+order-dependent digests of the sorted outputs; selected requests' outputs are
+copied back from the server and compared with the oracle element by element.
+"""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -28,6 +32,25 @@ def config(budget, digests=True, streams=4, max_batch=64, single_min=1 << 21, ma
     return rtcdf.ServerConfig(budget_bytes=budget, num_streams=streams, max_batch=max_batch,
                               single_min_keys=single_min, fill=gen.fill_function_address(),
                               digests=1 if digests else 0, max_large_inflight=max_large)
+
+
+def output_buffers(n, chosen):
+    """Host buffers for the requests in `chosen` and the pointer array the
+    server copies their sorted outputs to (NULL for the others)."""
+    bufs = {int(i): np.full(int(n[i]), 0x7FFFFFFF, dtype=np.int32) for i in chosen}
+    ptrs = (ctypes.c_void_p * len(n))()
+    for i, b in bufs.items():
+        ptrs[i] = b.ctypes.data
+    return bufs, ptrs
+
+
+def assert_outputs_match_oracle(bufs, n, mn, R, dist, seeds):
+    for i, got in bufs.items():
+        a = gen.keys_host(int(n[i]), int(mn[i]), int(R[i]), int(dist[i]), int(seeds[i]))
+        want = oracle.counting_sort(a, int(mn[i]), int(mn[i]) + int(R[i]))
+        bad = np.nonzero(got != want)[0]
+        assert bad.size == 0, (f"request {i} (n={n[i]}, R={R[i]}): {bad.size} positions differ "
+                               f"from the oracle, first {bad[:8].tolist()}")
 
 
 def oracle_digest(n, mn, R, dist, seed):
@@ -60,6 +83,27 @@ def test_results_alone_equal_results_in_the_mix():
     # and against the oracle on a sample
     for i in range(0, count, 23):
         assert mix[i].digest == oracle_digest(n[i], mn[i], R[i], dist[i], seeds[i]), i
+
+
+def test_served_outputs_equal_oracle_element_by_element():
+    """Requests admitted while others run and batched with them: every output
+    of n <= 1e6 keys, and a seeded sample of the larger ones, copied back from
+    the server and compared with the oracle position by position."""
+    count = 300
+    n, mn, R, dist, seeds, arr = trace(count, gen.derive_seed(54), n_hi=3e6, rate=20000.0)
+    reqs = rtcdf.make_requests(n, mn, mn + R, dist, seeds, arr)
+    rng = np.random.default_rng(54)
+    big = np.nonzero(n > 1_000_000)[0]
+    chosen = list(np.nonzero(n <= 1_000_000)[0]) + list(rng.choice(big, size=min(12, big.size),
+                                                                    replace=False))
+    bufs, ptrs = output_buffers(n, chosen)
+    cfg = config(4 << 30)
+    cfg.outputs = ctypes.cast(ptrs, ctypes.c_void_p)
+    res, st = rtcdf.rtcdf_serve_trace(cfg, reqs, count)
+    assert st.launches_batched > 0 and st.max_inflight > 1
+    for i in range(count):
+        assert res[i].status == 0, i
+    assert_outputs_match_oracle(bufs, n, mn, R, dist, seeds)
 
 
 def test_small_budget_admission_waits_for_memory():
@@ -118,3 +162,27 @@ def test_benchmark_serving_trace_all_requests():
     small = np.nonzero(n <= 2_000_000)[0]
     for i in rng.choice(small, size=min(40, small.size), replace=False):
         assert mix[i].digest == oracle_digest(n[i], mn[i], R[i], dist[i], seeds[i]), i
+
+
+def test_benchmark_serving_trace_outputs_element_by_element():
+    """The benchmark's serving trace again, with the outputs of every request
+    of n <= 1e6 keys (about half of the 20000) and of a seeded sample of the
+    larger ones copied back and compared with the oracle position by
+    position."""
+    count = 20000
+    seed = gen.derive_seed(5)
+    n, mn, R, dist, seeds = gen.serving_requests(seed, count)
+    arr = gen.poisson_arrivals(seed, count, 13000.0)
+    reqs = rtcdf.make_requests(n, mn, mn + R, dist, seeds, arr)
+    rng = np.random.default_rng(8)
+    big = np.nonzero(n > 1_000_000)[0]
+    chosen = list(np.nonzero(n <= 1_000_000)[0]) + list(rng.choice(big, size=min(16, big.size),
+                                                                    replace=False))
+    bufs, ptrs = output_buffers(n, chosen)
+    cfg = rtcdf.ServerConfig(budget_bytes=32 << 30, num_streams=4, max_batch=256,
+                             single_min_keys=1 << 22, fill=gen.fill_function_address(), digests=0,
+                             outputs=ctypes.cast(ptrs, ctypes.c_void_p))
+    res, st = rtcdf.rtcdf_serve_trace(cfg, reqs, count)
+    assert st.launches_batched > 0 and st.launches_single > 0
+    assert all(res[i].status == 0 for i in range(count))
+    assert_outputs_match_oracle(bufs, n, mn, R, dist, seeds)
