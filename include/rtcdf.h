@@ -232,6 +232,52 @@ rtcdf_status rtcdf_sort_ex(const int32_t *in, int32_t *out, uint64_t n, int64_t 
                            rtcdf_stream_t stream);
 
 /*
+ * Sharded sort of one array over several GPUs (or several slices on one).
+ * The sorted output depends on the global histogram alone (Section 3.1,
+ * Algorithms 4 and 7; Section 3.2, Lemma 3: value v occupies positions
+ * [sum_{u<v} c_u, sum_{u<=v} c_u)), so P ranks that each hold a contiguous
+ * slice of the input run:
+ *   1. rtcdf_hist_accumulate on their slice into a counts array zeroed
+ *      beforehand (Algorithm 5 for every tile);
+ *   2. one sum all-reduce of the R counts over the ranks (the caller's
+ *      collective, e.g. NCCL on uint32/int32: sums wrap identically);
+ *   3. rtcdf_fill_from_counts for their own window [pos_begin, pos_end) of
+ *      the sorted array (Algorithm 6's offsets and Algorithm 7's output for
+ *      those positions only).
+ * No keys cross ranks.  Both calls are asynchronous and stream-ordered, and
+ * allocate nothing.
+ *
+ * rtcdf_hist_accumulate -- counts[x] += #{i : in[i] - minVal == x} for the n
+ * keys of `in` (device), x in [0, R).  `counts` is a DEVICE array of R uint32
+ * (4-byte aligned) that the caller zeroes before the first slice; calls on
+ * several slices add up.  Keys outside [minVal, maxVal) are counted nowhere
+ * (the shortfall is found by rtcdf_fill_from_counts).  Errors:
+ * RTCDF_ERR_RANGE as for rtcdf_sort; RTCDF_ERR_INVALID_ARG for a null or
+ * misaligned pointer, n >= 2^32, or `in` overlapping `counts`.
+ */
+rtcdf_status rtcdf_hist_accumulate(const int32_t *in, uint64_t n, int64_t minVal, int64_t maxVal,
+                                   uint32_t *counts, rtcdf_stream_t stream);
+
+/*
+ * rtcdf_fill_from_counts -- write positions [pos_begin, pos_end) of the sorted
+ * array whose global counts are `counts` (device, R uint32 adding up to
+ * total_n): out[p - pos_begin] = minVal + min{v : sum_{u<=v} c_u > p}.
+ * `counts` is only read.  `workspace` is as for rtcdf_sort_ws (at least
+ * rtcdf_workspace_size(R) bytes, 256-byte aligned, zero-filled before its
+ * first use, left ready for the next call; calls sharing it must be
+ * ordered).  Counts that do not add up to total_n (a key outside the range
+ * on some rank) set RTCDF_DEV_KEY_OUT_OF_RANGE in the workspace's status word
+ * (rtcdf_ws_status_get), and `out` is then unspecified.  Errors:
+ * RTCDF_ERR_RANGE as for rtcdf_sort; RTCDF_ERR_INVALID_ARG for total_n >=
+ * 2^32, pos_begin > pos_end, pos_end > total_n, a null or misaligned pointer,
+ * or `out` overlapping `counts` or the workspace; RTCDF_ERR_NO_MEMORY for a
+ * workspace that is too small.  An empty window returns RTCDF_OK at once.
+ */
+rtcdf_status rtcdf_fill_from_counts(const uint32_t *counts, uint64_t total_n, int64_t minVal,
+                                    int64_t maxVal, uint64_t pos_begin, uint64_t pos_end, int32_t *out,
+                                    void *workspace, size_t ws_bytes, rtcdf_stream_t stream);
+
+/*
  * rtcdf_sort_host -- rtcdf_sort with HOST buffers: `in` and `out` point to
  * host memory (page-locked for the transfers to overlap anything; pageable
  * works but copies synchronously).  The keys are uploaded in 16 MB chunks on

@@ -78,9 +78,13 @@ __global__ void __launch_bounds__(WIN) fill_kernel(FillArgs a) {
     // is set later sorts on the workspace write nothing either.
     if (a.ctl->status & kDevTimeout) return;
 
+    // Positions are those of the whole sorted array; this launch writes
+    // [pos_base, n) of them, position p to out[p - pos_base].  hb is the
+    // position of the first 16-byte aligned element of `out`.
     const uint32_t n = (uint32_t)a.n, head = a.head, fc = (uint32_t)a.fill_chunk;
-    const uint32_t P0 = (c == 0) ? 0u : head + c * fc;
-    const uint32_t P1 = (c + 1 == a.fill_ctas) ? n : head + (c + 1) * fc;
+    const uint32_t pb = a.pos_base, hb = pb + head;
+    const uint32_t P0 = (c == 0) ? pb : hb + c * fc;
+    const uint32_t P1 = (c + 1 == a.fill_ctas) ? n : hb + (c + 1) * fc;
     // Every index into the run table stays below the R entries it holds, even
     // if the scan's results were not what this sort expects.
     const uint32_t D = min(a.ctl->num_runs, a.R);
@@ -100,9 +104,9 @@ __global__ void __launch_bounds__(WIN) fill_kernel(FillArgs a) {
         }
         __syncthreads();
         const uint32_t hi = min(P1, s_end[nw - 1]);
-        // Whole vectors w cover [head + 4w, head + 4w + 4) inside [pos, hi).
-        const uint32_t w_lo = pos >= head ? (pos - head + 3) >> 2 : 0u;
-        const uint32_t w_hi = hi >= head ? (hi - head) >> 2 : 0u;
+        // Whole vectors w cover [hb + 4w, hb + 4w + 4) inside [pos, hi).
+        const uint32_t w_lo = pos >= hb ? (pos - hb + 3) >> 2 : 0u;
+        const uint32_t w_hi = hi >= hb ? (hi - hb) >> 2 : 0u;
 
         if (s_end[0] >= hi) {
             // One run covers the whole round: constant stores.
@@ -134,7 +138,7 @@ __global__ void __launch_bounds__(WIN) fill_kernel(FillArgs a) {
             uint32_t ej = s_end[0];
             int32_t vj = s_val[0];
             for (uint32_t w = wb + lane; w < we; w += 32) {
-                const uint32_t q = head + 4 * w;
+                const uint32_t q = hb + 4 * w;
                 if (ej <= q) {
                     // s_end[nw - 1] > q, so j + 1 <= nw - 1.
                     j = next_run_after(s_end, j + 1, nw - 1, q);
@@ -164,7 +168,7 @@ __global__ void __launch_bounds__(WIN) fill_kernel(FillArgs a) {
         // Positions of [pos, hi) outside whole vectors: at most three before
         // the first vector and three after the last.
         if (tid < 8) {
-            const uint32_t q_lo = head + 4 * w_lo, q_hi = head + 4 * w_hi;
+            const uint32_t q_lo = hb + 4 * w_lo, q_hi = hb + 4 * w_hi;
             uint32_t p;
             if (w_lo >= w_hi) {
                 p = pos + tid;  // no whole vector: hi - pos < 8
@@ -173,7 +177,7 @@ __global__ void __launch_bounds__(WIN) fill_kernel(FillArgs a) {
                 p = (uint32_t)tid < n_front ? pos + tid : q_hi + (tid - n_front);
             }
             if (p >= pos && p < hi && (w_lo >= w_hi || p < q_lo || p >= q_hi))
-                a.out[p] = s_val[first_run_after(s_end, 0, nw - 1, p)];
+                a.out[p - pb] = s_val[first_run_after(s_end, 0, nw - 1, p)];
         }
         pos = hi;
         k_cur += nw;

@@ -202,10 +202,13 @@ rtcdf_status hist_phase(const int32_t *in, uint64_t n, int64_t minVal, uint32_t 
 }
 
 // Local CDFs + offsets (Algorithm 6) and output generation (Algorithm 7)
-// for an n-key array whose histogram is in H.
+// for an n-key array whose histogram is in H: positions [pos_base, pos_end)
+// of the sorted array are written, position p to out[p - pos_base] (the
+// plan's output CTAs are sized for pos_end - pos_base positions).
 rtcdf_status finish_phase(int32_t *out, uint64_t n, int64_t minVal, uint32_t R, const Plan &pl,
                           const WsLayout &L, char *base, const rtcdf_debug *dbg,
-                          cudaEvent_t ev_scan, cudaEvent_t ev_fill, cudaStream_t s) {
+                          cudaEvent_t ev_scan, cudaEvent_t ev_fill, cudaStream_t s,
+                          uint64_t pos_base, uint64_t pos_end) {
     Ctl *ctl = (Ctl *)(base + L.ctl);
     uint64_t *state = (uint64_t *)(base + L.scan_state);
     uint32_t *run_end = (uint32_t *)(base + L.run_end);
@@ -216,6 +219,7 @@ rtcdf_status finish_phase(int32_t *out, uint64_t n, int64_t minVal, uint32_t R, 
     sc.H = (uint32_t *)(base + L.hist); sc.state = state; sc.ctl = ctl; sc.run_end = run_end;
     sc.run_val = run_val; sc.start_run = start_run; sc.n = n; sc.fill_chunk = pl.fill_chunk;
     sc.head = head_out; sc.fill_ctas = pl.fill_ctas; sc.R = R; sc.T = pl.T; sc.chunks = L.scan_chunks;
+    sc.pos_base = (uint32_t)pos_base; sc.pos_end = (uint32_t)pos_end;
     sc.minVal = (int32_t)minVal;
     sc.dbg_hist = dbg ? dbg->tile_hist : nullptr;
     sc.dbg_cdf = dbg ? dbg->cdf : nullptr;
@@ -224,7 +228,8 @@ rtcdf_status finish_phase(int32_t *out, uint64_t n, int64_t minVal, uint32_t R, 
     if (ev_scan && cudaEventRecord(ev_scan, s) != cudaSuccess) return RTCDF_ERR_CUDA;
 
     FillArgs f;
-    f.out = out; f.n = n; f.fill_chunk = pl.fill_chunk; f.head = head_out;
+    f.out = out; f.n = pos_end; f.pos_base = (uint32_t)pos_base; f.fill_chunk = pl.fill_chunk;
+    f.head = head_out;
     f.fill_ctas = pl.fill_ctas; f.run_end = run_end; f.run_val = run_val;
     f.start_run = start_run; f.ctl = ctl; f.scan_state = state; f.scan_chunks = L.scan_chunks;
     f.R = R;
@@ -245,7 +250,7 @@ rtcdf_status run_pipeline(const int32_t *in, int32_t *out, uint64_t n, int64_t m
     rtcdf_status st = hist_phase(in, n, minVal, R, pl, L, base, s);
     if (st) return st;
     if (ev[1] && cudaEventRecord(ev[1], s) != cudaSuccess) return RTCDF_ERR_CUDA;
-    return finish_phase(out, n, minVal, R, pl, L, base, dbg, ev[2], ev[3], s);
+    return finish_phase(out, n, minVal, R, pl, L, base, dbg, ev[2], ev[3], s, 0, n);
 }
 
 // ---------------------------------------------------------------- workspace cache
@@ -341,7 +346,7 @@ rtcdf_status host_pipeline_finish(int32_t *out, uint64_t n, int64_t minVal, uint
     rtcdf_status st = make_plan(n, R, 0, (uintptr_t)out, nullptr, &pl);
     if (st) return st;
     return finish_phase(out, n, minVal, R, pl, ws_layout(R, ws_bytes), (char *)ws, nullptr,
-                        nullptr, nullptr, s);
+                        nullptr, nullptr, s, 0, n);
 }
 
 }  // namespace rtcdf
@@ -433,6 +438,64 @@ rtcdf_status rtcdf_sort(const int32_t *in, int32_t *out, uint64_t n, int64_t min
     st = make_plan(n, R, (uintptr_t)in, (uintptr_t)out, nullptr, &pl);
     if (st) return st;
     return run_pipeline(in, out, n, minVal, R, pl, ws, ws_bytes, nullptr, (cudaStream_t)stream);
+}
+
+rtcdf_status rtcdf_hist_accumulate(const int32_t *in, uint64_t n, int64_t minVal, int64_t maxVal,
+                                   uint32_t *counts, rtcdf_stream_t stream) {
+    uint32_t R = 0;
+    rtcdf_status st = check_range(minVal, maxVal, &R);
+    if (st) return st;
+    if (!counts || ((uintptr_t)counts & 3)) return RTCDF_ERR_INVALID_ARG;
+    if (n == 0) return RTCDF_OK;
+    if (n >= (1ull << 32) || !in || ((uintptr_t)in & 3)) return RTCDF_ERR_INVALID_ARG;
+    {
+        const uintptr_t x = (uintptr_t)in, y = (uintptr_t)counts;
+        if (x < y + (uint64_t)R * 4 && y < x + n * 4) return RTCDF_ERR_INVALID_ARG;
+    }
+    Plan pl;
+    st = make_plan(n, R, (uintptr_t)in, 0, nullptr, &pl);
+    if (st) return st;
+    // Algorithm 5 for every tile, added straight into the caller's counts.
+    HistArgs h;
+    h.in = in; h.n = n; h.nvec = pl.nvec; h.head = pl.head;
+    h.min_u = (uint32_t)(int32_t)minVal; h.R = R; h.T = pl.T; h.m = pl.m; h.g = pl.g;
+    h.H = counts;
+    h.ctl = nullptr;
+    if (launch_hist(h, pl.hist_threads, pl.hist_smem, pl.streaming, (cudaStream_t)stream) != cudaSuccess)
+        return RTCDF_ERR_CUDA;
+    return RTCDF_OK;
+}
+
+rtcdf_status rtcdf_fill_from_counts(const uint32_t *counts, uint64_t total_n, int64_t minVal,
+                                    int64_t maxVal, uint64_t pos_begin, uint64_t pos_end, int32_t *out,
+                                    void *workspace, size_t ws_bytes, rtcdf_stream_t stream) {
+    uint32_t R = 0;
+    rtcdf_status st = check_range(minVal, maxVal, &R);
+    if (st) return st;
+    if (total_n >= (1ull << 32) || pos_begin > pos_end || pos_end > total_n) return RTCDF_ERR_INVALID_ARG;
+    if (!counts || ((uintptr_t)counts & 3)) return RTCDF_ERR_INVALID_ARG;
+    if (pos_end == pos_begin) return RTCDF_OK;
+    if (!out || ((uintptr_t)out & 3)) return RTCDF_ERR_INVALID_ARG;
+    if (!workspace || ((uintptr_t)workspace & 255)) return RTCDF_ERR_INVALID_ARG;
+    if (ws_bytes < ws_required(R)) return RTCDF_ERR_NO_MEMORY;
+    const uint64_t len = pos_end - pos_begin;
+    {
+        const uintptr_t x = (uintptr_t)out, y = (uintptr_t)counts, w = (uintptr_t)workspace;
+        if (x < y + (uint64_t)R * 4 && y < x + len * 4) return RTCDF_ERR_INVALID_ARG;
+        if (x < w + ws_bytes && w < x + len * 4) return RTCDF_ERR_INVALID_ARG;
+    }
+    Plan pl;
+    st = make_plan(len, R, 0, (uintptr_t)out, nullptr, &pl);
+    if (st) return st;
+    cudaStream_t s = (cudaStream_t)stream;
+    const WsLayout L = ws_layout(R, ws_bytes);
+    // The global counts become the workspace's H (zero between sorts; the scan
+    // zeroes it again as it reads it).
+    if (cudaMemcpyAsync((char *)workspace + L.hist, counts, (size_t)R * 4, cudaMemcpyDeviceToDevice, s) !=
+        cudaSuccess)
+        return RTCDF_ERR_CUDA;
+    return finish_phase(out, total_n, minVal, R, pl, L, (char *)workspace, nullptr, nullptr, nullptr, s,
+                        pos_begin, pos_end);
 }
 
 rtcdf_status rtcdf_status_get(rtcdf_stream_t stream, int32_t *device_status) {

@@ -109,10 +109,12 @@ struct ScanArgs {
     uint32_t *run_end;     // inclusive CDF at each non-empty value (exclusive end of its run)
     int32_t *run_val;      // the key of each non-empty value
     uint32_t *start_run;   // per output CTA: run containing its first position
-    uint64_t n;
+    uint64_t n;            // keys of the whole array (the counts must add up to it)
     uint64_t fill_chunk;   // positions per output CTA (multiple of 4)
-    uint32_t head;         // first output CTA boundary is head + fill_chunk
+    uint32_t head;         // first output CTA boundary is pos_base + head + fill_chunk
     uint32_t fill_ctas;
+    uint32_t pos_base;     // the output CTAs cover positions [pos_base, pos_end) of
+    uint32_t pos_end;      // the sorted array (0 and n for a whole sort)
     uint32_t R, T, chunks;
     int32_t minVal;
     uint32_t *dbg_hist, *dbg_cdf, *dbg_offset;  // optional exports
@@ -121,8 +123,9 @@ cudaError_t launch_scan(const ScanArgs &a, cudaStream_t s);
 
 // ---------------------------------------------------------------- output
 struct FillArgs {
-    int32_t *out;
-    uint64_t n;
+    int32_t *out;          // out[0] holds position pos_base of the sorted array
+    uint64_t n;            // end of the positions written (pos_end)
+    uint32_t pos_base;     // first position written (0 for a whole sort)
     uint64_t fill_chunk;
     uint32_t head;
     uint32_t fill_ctas;

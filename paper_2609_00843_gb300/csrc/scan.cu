@@ -183,22 +183,24 @@ __global__ void __launch_bounds__(kScanThreads) scan_kernel(ScanArgs a) {
     }
     __syncthreads();
 
-    // Output CTA j starts at P0(j): P0(0) = 0, P0(j) = head + j * fill_chunk.
-    // The chunk's values cover positions [pos_lo, pos_hi).
-    const uint32_t pos_lo = (uint32_t)chunk_prefix;
-    const uint32_t pos_hi = s_cdf[kScanChunk - 1];
+    // Output CTA j starts at P0(j): P0(0) = pos_base, P0(j) = pos_base + head
+    // + j * fill_chunk, all inside [pos_base, pos_end).  The chunk's values
+    // cover positions [pos_lo, pos_hi); only the part inside the written
+    // window can hold a CTA's first position.
+    const uint32_t pos_lo = max((uint32_t)chunk_prefix, a.pos_base);
+    const uint32_t pos_hi = min(s_cdf[kScanChunk - 1], a.pos_end);
     if (pos_hi > pos_lo) {
-        const uint32_t fc = (uint32_t)a.fill_chunk, head = a.head;
-        // First CTA j with P0(j) >= pos (P0 is increasing in j).
-        auto first_cta_at_or_after = [&](uint32_t pos) -> uint32_t {
-            if (pos == 0) return 0u;
-            if ((uint64_t)pos <= (uint64_t)head + fc) return 1u;
-            return (uint32_t)(((uint64_t)pos - head + fc - 1) / fc);
+        const uint32_t fc = (uint32_t)a.fill_chunk, head = a.head, pb = a.pos_base;
+        // First CTA j with P0(j) >= pb + l (P0 is increasing in j).
+        auto first_cta_at_or_after = [&](uint32_t l) -> uint32_t {
+            if (l == 0) return 0u;
+            if ((uint64_t)l <= (uint64_t)head + fc) return 1u;
+            return (uint32_t)(((uint64_t)l - head + fc - 1) / fc);
         };
-        const uint32_t j_lo = first_cta_at_or_after(pos_lo);
-        const uint32_t j_hi = min(first_cta_at_or_after(pos_hi), a.fill_ctas);
+        const uint32_t j_lo = first_cta_at_or_after(pos_lo - pb);
+        const uint32_t j_hi = min(first_cta_at_or_after(pos_hi - pb), a.fill_ctas);
         for (uint32_t j = j_lo + tid; j < j_hi; j += kScanThreads) {
-            const uint32_t p0 = (j == 0) ? 0u : head + j * fc;
+            const uint32_t p0 = pb + ((j == 0) ? 0u : head + j * fc);
             // Smallest value of the chunk whose CDF exceeds p0 (Algorithm 7's rule).
             int lo = 0, hi = kScanChunk - 1;
             while (lo < hi) {

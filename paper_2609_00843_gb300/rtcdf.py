@@ -129,6 +129,8 @@ def lib():
             L.rtcdf_ws_status_get.argtypes = [vp, vp, ctypes.POINTER(i32)]
             L.rtcdf_plan.argtypes = [u64, i64, ctypes.POINTER(Params)]
             L.rtcdf_sort_static.argtypes = [vp, vp, u64, i64, i64, vp]
+            L.rtcdf_hist_accumulate.argtypes = [vp, u64, i64, i64, vp, vp]
+            L.rtcdf_fill_from_counts.argtypes = [vp, u64, i64, i64, u64, u64, vp, vp, sz, vp]
             L.rtcdf_sort_host.argtypes = [vp, vp, u64, i64, i64, vp]
             L.rtcdf_batch_plan_create.argtypes = [vp, vp, vp, i32, ctypes.POINTER(vp)]
             L.rtcdf_batch_plan_create_ex.argtypes = [vp, vp, vp, i32, ctypes.POINTER(BatchParams),
@@ -163,7 +165,7 @@ def lib():
                       "rtcdf_plan", "rtcdf_sort_static", "rtcdf_sort_host", "rtcdf_batch_plan_create",
                       "rtcdf_batch_plan_destroy", "rtcdf_batch_workspace_size",
                       "rtcdf_batch_plan_info", "rtcdf_sort_batched_ws", "rtcdf_batch_status_get",
-                      "rtcdf_sort_batched"):
+                      "rtcdf_sort_batched", "rtcdf_hist_accumulate", "rtcdf_fill_from_counts"):
                 getattr(L, f).restype = ctypes.c_int
             L.rtcdf_status_str.argtypes = [ctypes.c_int]
             L.rtcdf_status_str.restype = ctypes.c_char_p
@@ -191,6 +193,21 @@ def rtcdf_sort_ex(in_ptr, out_ptr, n, minVal, maxVal, params: Params | None, ws_
 def rtcdf_sort_static(in_ptr: int, out_ptr: int, n: int, minVal: int, maxVal: int,
                       stream: int = 0) -> int:
     return lib().rtcdf_sort_static(in_ptr, out_ptr, n, minVal, maxVal, stream)
+
+
+def rtcdf_hist_accumulate(in_ptr: int, n: int, minVal: int, maxVal: int, counts_ptr: int,
+                          stream: int = 0) -> int:
+    """Add the counts of n device keys into a device uint32[R] array."""
+    return lib().rtcdf_hist_accumulate(in_ptr, n, minVal, maxVal, counts_ptr, stream)
+
+
+def rtcdf_fill_from_counts(counts_ptr: int, total_n: int, minVal: int, maxVal: int, pos_begin: int,
+                           pos_end: int, out_ptr: int, ws_ptr: int, ws_bytes: int,
+                           stream: int = 0) -> int:
+    """Write positions [pos_begin, pos_end) of the sorted array with the given
+    global counts into out (out[0] = position pos_begin)."""
+    return lib().rtcdf_fill_from_counts(counts_ptr, total_n, minVal, maxVal, pos_begin, pos_end,
+                                        out_ptr, ws_ptr, ws_bytes, stream)
 
 
 def _i64_array(xs):

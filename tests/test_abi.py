@@ -155,3 +155,31 @@ def test_server_rejects_bad_config_and_requests_on_host():
         assert trace(ctypes.byref(cfg(**kw)), good, 2, res, ctypes.byref(st)) == rtcdf.ERR_INVALID_ARG
     wide = rtcdf.make_requests([10], [0], [(1 << 20) + 1], [0], [1], [0.0])
     assert trace(ctypes.byref(cfg()), wide, 1, res, ctypes.byref(st)) == rtcdf.ERR_RANGE
+
+
+def test_sharded_entry_points_reject_bad_arguments_on_host():
+    # Every case returns before any CUDA call, so it runs without a GPU.
+    h, f = rtcdf.rtcdf_hist_accumulate, rtcdf.rtcdf_fill_from_counts
+    assert h(4096, 10, 5, 5, 1 << 20, 0) == rtcdf.ERR_RANGE                  # R = 0
+    assert h(4096, 10, 0, rtcdf.MAX_R + 1, 1 << 20, 0) == rtcdf.ERR_RANGE
+    assert h(4096, 10, 0, 128, 0, 0) == rtcdf.ERR_INVALID_ARG                # null counts
+    assert h(4096, 10, 0, 128, (1 << 20) + 2, 0) == rtcdf.ERR_INVALID_ARG    # misaligned counts
+    assert h(0, 10, 0, 128, 1 << 20, 0) == rtcdf.ERR_INVALID_ARG             # null input
+    assert h(4098, 10, 0, 128, 1 << 20, 0) == rtcdf.ERR_INVALID_ARG          # misaligned input
+    assert h(4096, 1 << 32, 0, 128, 1 << 30, 0) == rtcdf.ERR_INVALID_ARG     # n >= 2^32
+    assert h(4096, 1000, 0, 128, 4096 + 400, 0) == rtcdf.ERR_INVALID_ARG     # input overlaps counts
+    assert h(0, 0, 0, 128, 1 << 20, 0) == rtcdf.OK                           # empty slice
+    ws = 1 << 24
+    wsb = rtcdf.rtcdf_workspace_size(128)
+    assert f(1 << 20, 100, 3, 3, 0, 100, 1 << 22, ws, wsb, 0) == rtcdf.ERR_RANGE
+    assert f(1 << 20, 1 << 32, 0, 128, 0, 100, 1 << 22, ws, wsb, 0) == rtcdf.ERR_INVALID_ARG
+    assert f(1 << 20, 100, 0, 128, 60, 50, 1 << 22, ws, wsb, 0) == rtcdf.ERR_INVALID_ARG   # begin > end
+    assert f(1 << 20, 100, 0, 128, 0, 101, 1 << 22, ws, wsb, 0) == rtcdf.ERR_INVALID_ARG   # end > n
+    assert f(0, 100, 0, 128, 0, 100, 1 << 22, ws, wsb, 0) == rtcdf.ERR_INVALID_ARG         # null counts
+    assert f(1 << 20, 100, 0, 128, 0, 100, 0, ws, wsb, 0) == rtcdf.ERR_INVALID_ARG         # null out
+    assert f(1 << 20, 100, 0, 128, 0, 100, (1 << 22) + 1, ws, wsb, 0) == rtcdf.ERR_INVALID_ARG
+    assert f(1 << 20, 100, 0, 128, 0, 100, 1 << 22, ws + 16, wsb, 0) == rtcdf.ERR_INVALID_ARG
+    assert f(1 << 20, 100, 0, 128, 0, 100, 1 << 22, ws, 64, 0) == rtcdf.ERR_NO_MEMORY
+    assert f(1 << 20, 100, 0, 128, 0, 100, (1 << 20) + 64, ws, wsb, 0) == rtcdf.ERR_INVALID_ARG  # out on counts
+    assert f(1 << 20, 100, 0, 128, 0, 100, ws + 256, ws, wsb, 0) == rtcdf.ERR_INVALID_ARG  # out on workspace
+    assert f(1 << 20, 100, 0, 128, 40, 40, 0, 0, 0, 0) == rtcdf.OK           # empty window
