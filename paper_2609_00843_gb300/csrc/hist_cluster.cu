@@ -295,10 +295,6 @@ size_t hist_cluster_smem(uint32_t R, int C) {
 cudaError_t hist_cluster_max_clusters(int C, size_t smem, int *clusters) {
     static std::mutex mu;
     static std::map<std::tuple<int, int, size_t>, int> cache;
-    // Largest dynamic shared memory requested so far per (device, C): the
-    // kernel attribute only ever grows, so a size cached earlier stays
-    // launchable after a smaller one was planned.
-    static std::map<std::pair<int, int>, size_t> limit;
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
@@ -311,12 +307,8 @@ cudaError_t hist_cluster_max_clusters(int C, size_t smem, int *clusters) {
         *clusters = it->second;
         return cudaSuccess;
     }
-    size_t &lim = limit[std::make_pair(dev, C)];
-    if (smem > lim) {
-        e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        lim = smem;
-    }
+    e = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
     int sms = 0;
     e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
