@@ -136,25 +136,8 @@ typedef struct {
     int32_t fill_threads;    /* 256, 512 or 1024 */
     int32_t fill_chunk;      /* output positions per output CTA; when > 0 it
                                 replaces fill_ctas (the count then follows n) */
-    int32_t hist_method;     /* ranges wider than one tile: RTCDF_HIST_AUTO,
-                                RTCDF_HIST_TILES or RTCDF_HIST_CLUSTER */
-    int32_t reserved;
+    int32_t reserved[2];
 } rtcdf_params;
-
-/* Histogram of a range wider than one shared-memory tile (m > 1):
- *  RTCDF_HIST_TILES    the paper's form (Section 3.3): each tile's CTAs read
- *                      the whole input and count the keys inside their tile;
- *  RTCDF_HIST_CLUSTER  the m tiles spread over the 2, 4 or 8 CTAs of a
- *                      thread-block cluster, every key read once and sent to
- *                      the CTA that owns its bin through distributed shared
- *                      memory (ranges up to RTCDF_HIST_CLUSTER_MAX_R; used
- *                      only with an automatic tile width);
- *  RTCDF_HIST_AUTO     the cluster form where it applies, else tiles.
- * The counts, and so the sorted output, are the same either way. */
-#define RTCDF_HIST_AUTO 0
-#define RTCDF_HIST_TILES 1
-#define RTCDF_HIST_CLUSTER 2
-#define RTCDF_HIST_CLUSTER_MAX_R 395264
 
 /* The parameters rtcdf_sort would use for (n, R) on the current device
  * (tuning table first, then the built-in rules). */

@@ -59,8 +59,6 @@ struct Plan {
     int hist_threads;
     size_t hist_smem;
     bool streaming;
-    int cluster;            // > 0: cluster histogram with this many CTAs per cluster
-    uint32_t clusters;      // clusters launched
     uint32_t head;
     uint64_t nvec;
     int fill_threads;
@@ -132,35 +130,6 @@ rtcdf_status make_plan_with(uint64_t n, uint32_t R, uintptr_t in_addr, uintptr_t
     if (q.hist_ctas_per_tile > 0) g = (uint64_t)q.hist_ctas_per_tile;
     pl->g = (uint32_t)g;
 
-    // Several tiles with an automatic tile width: the cluster form (every key
-    // read once) with the smallest cluster whose CTAs hold the range.
-    pl->cluster = 0;
-    pl->clusters = 0;
-    if (q.hist_method < RTCDF_HIST_AUTO || q.hist_method > RTCDF_HIST_CLUSTER) return RTCDF_ERR_INVALID_ARG;
-    const bool want_cluster = q.hist_method == RTCDF_HIST_CLUSTER ||
-                              (q.hist_method == RTCDF_HIST_AUTO && q.tile_width <= 0 && pl->m > 1);
-    if (want_cluster && R > 1 && R <= (uint32_t)RTCDF_HIST_CLUSTER_MAX_R) {
-        for (int C : {2, 4, 8}) {
-            const size_t sm = hist_cluster_smem(R, C);
-            if (sm > dev.smem_optin) continue;
-            int ncl = 0;
-            try {
-                if (hist_cluster_max_clusters(C, sm, &ncl) != cudaSuccess) return RTCDF_ERR_CUDA;
-            } catch (...) {
-                return RTCDF_ERR_NO_MEMORY;
-            }
-            if (ncl < 1) continue;
-            const uint64_t per_round = (uint64_t)C * 2 * kClThreads;  // vectors per cluster round
-            const uint64_t rounds = std::max<uint64_t>(1, (pl->nvec + per_round - 1) / per_round);
-            pl->cluster = C;
-            pl->clusters = (uint32_t)std::min<uint64_t>((uint64_t)ncl, rounds);
-            pl->hist_smem = sm;
-            pl->hist_threads = kClThreads;
-            break;
-        }
-    }
-    if (q.hist_method == RTCDF_HIST_CLUSTER && pl->cluster == 0) return RTCDF_ERR_INVALID_ARG;
-
     // Output: contiguous position ranges, CTA boundaries on 16-byte vectors of `out`.
     // Not clamped to n: positions below head_out are written one by one, and
     // the vector frame must stay 16-byte aligned.
@@ -218,12 +187,6 @@ rtcdf_status check_args(const int32_t *in, int32_t *out, uint64_t n) {
     return RTCDF_OK;
 }
 
-rtcdf_status launch_hist_plan(const HistArgs &h, const Plan &pl, cudaStream_t s) {
-    const cudaError_t e = pl.cluster ? launch_hist_cluster(h, pl.cluster, pl.clusters, pl.hist_smem, s)
-                                     : launch_hist(h, pl.hist_threads, pl.hist_smem, pl.streaming, s);
-    return e == cudaSuccess ? RTCDF_OK : RTCDF_ERR_CUDA;
-}
-
 // Algorithm 5 (all tiles) into the workspace's H.  H accumulates, so several
 // calls over slices of one array add up to the array's histogram.
 rtcdf_status hist_phase(const int32_t *in, uint64_t n, int64_t minVal, uint32_t R, const Plan &pl,
@@ -233,7 +196,9 @@ rtcdf_status hist_phase(const int32_t *in, uint64_t n, int64_t minVal, uint32_t 
     h.min_u = (uint32_t)(int32_t)minVal; h.R = R; h.T = pl.T; h.m = pl.m; h.g = pl.g;
     h.H = (uint32_t *)(base + L.hist);
     h.ctl = (Ctl *)(base + L.ctl);
-    return launch_hist_plan(h, pl, s);
+    if (launch_hist(h, pl.hist_threads, pl.hist_smem, pl.streaming, s) != cudaSuccess)
+        return RTCDF_ERR_CUDA;
+    return RTCDF_OK;
 }
 
 // Local CDFs + offsets (Algorithm 6) and output generation (Algorithm 7)
@@ -423,7 +388,6 @@ rtcdf_status rtcdf_plan(uint64_t n, int64_t R, rtcdf_params *params) {
     params->fill_ctas = (int32_t)pl.fill_ctas;
     params->fill_threads = pl.fill_threads;
     params->fill_chunk = (int32_t)std::min<uint64_t>(pl.fill_chunk, INT32_MAX);
-    params->hist_method = pl.cluster ? RTCDF_HIST_CLUSTER : RTCDF_HIST_TILES;
     return RTCDF_OK;
 }
 
@@ -497,7 +461,9 @@ rtcdf_status rtcdf_hist_accumulate(const int32_t *in, uint64_t n, int64_t minVal
     h.min_u = (uint32_t)(int32_t)minVal; h.R = R; h.T = pl.T; h.m = pl.m; h.g = pl.g;
     h.H = counts;
     h.ctl = nullptr;
-    return launch_hist_plan(h, pl, (cudaStream_t)stream);
+    if (launch_hist(h, pl.hist_threads, pl.hist_smem, pl.streaming, (cudaStream_t)stream) != cudaSuccess)
+        return RTCDF_ERR_CUDA;
+    return RTCDF_OK;
 }
 
 rtcdf_status rtcdf_fill_from_counts(const uint32_t *counts, uint64_t total_n, int64_t minVal,

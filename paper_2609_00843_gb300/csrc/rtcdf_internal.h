@@ -101,16 +101,6 @@ cudaError_t launch_hist(const HistArgs &a, int threads, size_t smem, bool stream
                         cudaStream_t s);
 cudaError_t hist_max_ctas_per_sm(int threads, size_t smem, bool streaming, int *ctas);
 
-// Several tiles held by the C CTAs of a thread-block cluster, keys routed to
-// the CTA that owns their bin (hist_cluster.cu).  Uses a.in, n, nvec, head,
-// min_u, R and H.
-constexpr int kClThreads = 1024;
-// Shared memory of one cluster CTA for range size R and cluster size C.
-size_t hist_cluster_smem(uint32_t R, int C);
-cudaError_t hist_cluster_max_clusters(int C, size_t smem, int *clusters);
-cudaError_t launch_hist_cluster(const HistArgs &a, int C, uint32_t clusters, size_t smem,
-                                cudaStream_t s);
-
 // ---------------------------------------------------------------- scan
 struct ScanArgs {
     uint32_t *H;           // histogram, zeroed as it is consumed

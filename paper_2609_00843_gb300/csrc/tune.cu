@@ -16,7 +16,7 @@ namespace {
 // from measurements on GB300).
 const rtcdf_tune_entry kBuiltin[] = {
 #include "tune_table.inc"
-    {-1, -1, {0, 0, 0, 0, 0, 0, 0, 0}}  // terminator, never matched
+    {-1, -1, {0, 0, 0, 0, 0, 0, {0, 0}}}  // terminator, never matched
 };
 
 std::mutex g_tune_mu;

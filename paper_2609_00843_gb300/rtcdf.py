@@ -43,11 +43,7 @@ class Params(ctypes.Structure):
     _fields_ = [("tile_width", ctypes.c_int32), ("hist_ctas_per_tile", ctypes.c_int32),
                 ("hist_threads", ctypes.c_int32), ("fill_ctas", ctypes.c_int32),
                 ("fill_threads", ctypes.c_int32), ("fill_chunk", ctypes.c_int32),
-                ("hist_method", ctypes.c_int32), ("reserved", ctypes.c_int32)]
-
-
-HIST_AUTO, HIST_TILES, HIST_CLUSTER = 0, 1, 2
-HIST_CLUSTER_MAX_R = 395264
+                ("reserved", ctypes.c_int32 * 2)]
 
 
 class BatchParams(ctypes.Structure):

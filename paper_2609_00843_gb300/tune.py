@@ -272,13 +272,13 @@ def _geomean(times):
 
 def write_inc(entries, path: str) -> None:
     lines = ["// Built-in tuning table: {ceil(log2 R), n class, {T, hist CTAs per tile,",
-             "// hist threads, output CTAs, output threads, output chunk, hist method, 0}}.",
+             "// hist threads, output CTAs, output threads, output chunk, {0, 0}}}.",
              "// Zero = built-in rule.  Written by paper_2609_00843_gb300.tune from",
              "// measurements on GB300."]
     for e in entries:
-        lines.append("{%d, %d, {%d, 0, %d, 0, %d, %d, %d, 0}}," % (
+        lines.append("{%d, %d, {%d, 0, %d, 0, %d, %d, {0, 0}}}," % (
             e["log2_R"], e["n_class"], e["tile_width"], e["hist_threads"], e["fill_threads"],
-            e["fill_chunk"], e.get("hist_method", 0)))
+            e["fill_chunk"]))
     with open(path, "w") as f:
         f.write("\n".join(lines) + "\n")
 

@@ -142,86 +142,16 @@ def test_forced_tiles_intermediates_match_algorithms_5_to_7(R, T):
 @pytest.mark.parametrize("ht,hg,ft,fc", [(256, 1, 256, 1), (512, 3, 1024, 7), (1024, 1000, 512, 4096),
                                         (1024, 0, 256, 3000)])
 def test_launch_parameters_do_not_change_result(ht, hg, ft, fc):
-    for R, method in ((130, rtcdf.HIST_AUTO), (1 << 16, rtcdf.HIST_TILES), (1 << 16, rtcdf.HIST_AUTO)):
+    for R in (130, 1 << 16):
         x = dev_keys(777_777, 0, R, gen.UNIFORM, gen.derive_seed(11, R))
         out = torch.empty_like(x)
         ws_bytes = rtcdf.rtcdf_workspace_size(R)
         ws = torch.zeros(ws_bytes // 4 + 64, dtype=torch.int32, device="cuda")
-        p = rtcdf.Params(hist_threads=ht, hist_ctas_per_tile=hg, fill_threads=ft, fill_ctas=fc,
-                         hist_method=method)
+        p = rtcdf.Params(hist_threads=ht, hist_ctas_per_tile=hg, fill_threads=ft, fill_ctas=fc)
         rc = rtcdf.rtcdf_sort_ex(x.data_ptr(), out.data_ptr(), x.numel(), 0, R, p, ws.data_ptr(),
                                  ws_bytes, None, stream_handle())
         assert rc == rtcdf.OK
         assert_matches_oracle(x, out, 0, R)
-
-
-def _sort_with_method(x, mn, R, method, ws, wsb, dbg=None):
-    out = torch.full_like(x, 0x7FFFFFFF)
-    rc = rtcdf.rtcdf_sort_ex(x.data_ptr() if x.numel() else 0, out.data_ptr() if x.numel() else 0,
-                             x.numel(), mn, mn + R, rtcdf.Params(hist_method=method), ws.data_ptr(),
-                             wsb, dbg, stream_handle())
-    assert rc == rtcdf.OK, rtcdf.rtcdf_status_str(rc)
-    return out
-
-
-# Ranges around the cluster sizes' limits: 2 CTAs up to 98816 values, 4 up to
-# 197632, 8 up to 395264 (and one tile's 57344).
-CLUSTER_RS = [3, 1000, 57345, 65536, 98816, 98817, 131071, 197632, 197633, 1 << 18, 300_001,
-              rtcdf.HIST_CLUSTER_MAX_R]
-
-
-@pytest.mark.parametrize("R", CLUSTER_RS)
-def test_cluster_histogram_equals_tiles_and_oracle(R):
-    """The cluster histogram (keys routed to the CTA owning their bin) against
-    the paper's per-tile histogram and the oracle: sorted outputs and the
-    exported histogram H, on sizes from one key to several rounds of every
-    cluster, for each shape."""
-    mn = -31
-    wsb = rtcdf.rtcdf_workspace_size(R)
-    ws = torch.zeros(wsb // 4 + 64, dtype=torch.int32, device="cuda")
-    for dist in DISTS:
-        for n in (1, 3, 5, 8195, 1_000_003, 6_000_001):
-            x = dev_keys(n, mn, R, dist, gen.derive_seed(12, R, dist, n))
-            a = x.cpu().numpy()
-            want = oracle.counting_sort(a, mn, mn + R)
-            h = torch.zeros(R, dtype=torch.int32, device="cuda")
-            dbg = rtcdf.Debug(tile_hist=h.data_ptr())
-            for method in (rtcdf.HIST_CLUSTER, rtcdf.HIST_TILES):
-                out = _sort_with_method(x, mn, R, method, ws, wsb, dbg)
-                got = out.cpu().numpy()
-                bad = np.nonzero(got != want)[0]
-                assert bad.size == 0, (f"method {method} R={R} dist={dist} n={n}: {bad.size} "
-                                       f"positions differ, first {bad[:8].tolist()}")
-                assert np.array_equal(h.cpu().numpy().astype(np.uint64),
-                                      oracle.histogram(a, mn, mn + R)), f"H, method {method}"
-            assert rtcdf.rtcdf_ws_status_get(ws.data_ptr(), stream_handle()) == (rtcdf.OK, 0)
-
-
-def test_cluster_histogram_runs_misalignment_and_out_of_range_keys():
-    """Inputs the cluster histogram treats specially: long runs of one key
-    (warp slots of 32 equal keys skip the staging), runs that change value
-    inside a warp, every input alignment (head and tail keys), and keys
-    outside the range (counted nowhere; the status reports them)."""
-    R, mn = 1 << 18, 100
-    wsb = rtcdf.rtcdf_workspace_size(R)
-    ws = torch.zeros(wsb // 4 + 64, dtype=torch.int32, device="cuda")
-    rng = np.random.default_rng(13)
-    # sorted input: runs of every length
-    a = np.sort(rng.integers(mn, mn + R, 3_000_011)).astype(np.int32)
-    # blocks of 32 and 256 equal keys, with lengths that cross warp slots
-    b = np.repeat(rng.integers(mn, mn + R, 20_000).astype(np.int32), rng.integers(1, 300, 20_000))
-    for arr in (a, b):
-        base = torch.from_numpy(np.concatenate([arr, np.full(8, mn, np.int32)])).cuda()
-        for off in range(4):
-            x = base[off:off + arr.size - 3]
-            out = _sort_with_method(x, mn, R, rtcdf.HIST_CLUSTER, ws, wsb)
-            assert_matches_oracle(x, out, mn, mn + R)
-    x = dev_keys(500_000, mn, R, gen.UNIFORM, gen.derive_seed(14))
-    x[12345] = mn + R          # just above the range
-    x[400_000] = mn - 1        # just below
-    _sort_with_method(x, mn, R, rtcdf.HIST_CLUSTER, ws, wsb)
-    rc, bits = rtcdf.rtcdf_ws_status_get(ws.data_ptr(), stream_handle())
-    assert rc == rtcdf.ERR_KEY_OUT_OF_RANGE and bits & rtcdf.DEV_KEY_OUT_OF_RANGE
 
 
 def test_caller_workspace_reused_across_ranges():

@@ -23,7 +23,7 @@ def built():
 
 def _inc_entries():
     text = open(INC).read()
-    return re.findall(r"^\{(-?\d+), (-?\d+), \{(-?\d+), 0, (-?\d+), 0, (-?\d+), (-?\d+), (-?\d+), 0\}\},$",
+    return re.findall(r"^\{(-?\d+), (-?\d+), \{(-?\d+), 0, (-?\d+), 0, (-?\d+), (-?\d+), \{0, 0\}\}\},$",
                       text, re.M)
 
 
@@ -107,6 +107,6 @@ def test_write_inc_format_is_what_the_library_parses(tmp_path):
     tune.write_inc([{"log2_R": 18, "n_class": 2, "tile_width": 53248, "hist_threads": 1024,
                      "fill_threads": 256, "fill_chunk": 65536}], path)
     text = open(path).read()
-    assert "{18, 2, {53248, 0, 1024, 0, 256, 65536, 0, 0}}," in text
+    assert "{18, 2, {53248, 0, 1024, 0, 256, 65536, {0, 0}}}," in text
     for line in text.splitlines():
         assert line.startswith("//") or line.startswith("{")
