@@ -527,6 +527,35 @@ def batched_comparison(args, stream, num_segments=4096):
     info = plan.info()
     phases = rtcdf.batch_profile_summary(words, info["workers"])
     plan.close()
+    del ws
+    # The same segments with the metadata in device memory, planned on the
+    # device each run (rtcdf_sort_batched_device_ws), replayed from a graph.
+    d_o = torch.from_numpy(offs).cuda()
+    d_mn = torch.from_numpy(mn.astype(np.int64)).cuda()
+    d_mx = torch.from_numpy(mx.astype(np.int64)).cuda()
+    max_R = int(R.max())
+    dwsb = rtcdf.rtcdf_batch_device_workspace_size(num_segments, total, max_R)
+    dws = torch.zeros(dwsb // 4 + 64, dtype=torch.int32, device="cuda")
+
+    def device_planned():
+        rc = rtcdf.rtcdf_sort_batched_device_ws(x.data_ptr(), out.data_ptr(), d_o.data_ptr(), d_mn.data_ptr(),
+                                                d_mx.data_ptr(), num_segments, total, max_R, dws.data_ptr(),
+                                                dwsb, sh)
+        if rc != rtcdf.OK:
+            raise rtcdf.RtcdfError(rc, "rtcdf_sort_batched_device_ws")
+    out.fill_(-1)
+    device_planned()
+    stream.synchronize()
+    same = same and bool(torch.equal(out, ref))
+    g3 = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g3, stream=stream):
+        device_planned()
+    ms_dev_graph = timed(g3.replay, steps)
+    rc, bits = rtcdf.rtcdf_batch_status_get(dws.data_ptr(), sh)
+    if rc != rtcdf.OK:
+        raise rtcdf.RtcdfError(rc, "device-planned status")
+    same = same and bool(torch.equal(out, ref))
+    del dws, g3
     res = {
         "workload": f"{num_segments} segments: n log-uniform [1e3,1e6], R log-uniform [2^7,2^16], "
                     "minVal uniform [-2^20,2^20], mixed uniform/normal/all-equal",
@@ -538,10 +567,13 @@ def batched_comparison(args, stream, num_segments=4096):
         "batched_graph_ms": round(ms_batched_graph, 4), "batched_ms": round(ms_batched, 4),
         "looped_ms": round(ms_looped, 4), "looped_graph_ms": round(ms_looped_graph, 4),
         "speedup_vs_looped_graph": round(ms_looped_graph / ms_batched_graph, 2),
+        "device_planned_graph_GKeys_s": round(total / (ms_dev_graph * 1e-3) / 1e9, 2),
+        "device_planned_graph_ms": round(ms_dev_graph, 4),
+        "device_planned_workspace_GB": round(dwsb / 1e9, 3),
         "frac_8n_roofline": round(8 * total / (ms_batched_graph * 1e-3) / 1e9 / peaks()[0], 4),
         "outputs_equal": same, "plan": info, "phases": phases,
     }
-    del x, out, ws, ref
+    del x, out, ref
     torch.cuda.empty_cache()
     return res
 

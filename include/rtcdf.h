@@ -57,7 +57,9 @@ typedef enum {
     RTCDF_ERR_TIMEOUT = 6           /* device status: a bounded wait gave up */
 } rtcdf_status;
 
-/* Device status bits reported by rtcdf_status_get / rtcdf_ws_status_get. */
+/* Device status bits reported by rtcdf_status_get / rtcdf_ws_status_get
+ * (and RTCDF_DEV_BAD_SEGMENT, below, for segmented sorts planned on the
+ * device). */
 #define RTCDF_DEV_KEY_OUT_OF_RANGE 0x1
 #define RTCDF_DEV_TIMEOUT 0x2
 
@@ -107,11 +109,12 @@ rtcdf_status rtcdf_sort_ws(const int32_t *in, int32_t *out, uint64_t n, int64_t 
 
 /*
  * rtcdf_status_get -- wait for `stream`, then return in *device_status the
- * RTCDF_DEV_* bits recorded by sorts on the library-owned workspace of
- * `stream` since the last read, and clear them.  Returns RTCDF_ERR_TIMEOUT
- * when a bounded wait ran out (checked first: the other findings of that sort
- * are then unreliable), else RTCDF_ERR_KEY_OUT_OF_RANGE when a key lay
- * outside its range.
+ * RTCDF_DEV_* bits recorded by sorts on the library-owned workspaces of
+ * `stream` (rtcdf_sort's and rtcdf_sort_batched's) since the last read, and
+ * clear them.  Returns RTCDF_ERR_TIMEOUT when a bounded wait ran out (checked
+ * first: the other findings of that sort are then unreliable), else
+ * RTCDF_ERR_INVALID_ARG for segment metadata that broke its bounds, else
+ * RTCDF_ERR_KEY_OUT_OF_RANGE when a key lay outside its range.
  */
 rtcdf_status rtcdf_status_get(rtcdf_stream_t stream, int32_t *device_status);
 
@@ -322,8 +325,13 @@ rtcdf_status rtcdf_sort_host(const int32_t *in, int32_t *out, uint64_t n, int64_
  * the parts that must start at zero (histograms, lookback state, control
  * block) zeroed again, so the plan can be replayed on it, but its other parts
  * hold per-run tables, so zero-fill it again before using it with another
- * plan.  The status word is sticky until read with rtcdf_batch_status_get.  rtcdf_sort_batched is the one-shot
- * form: plan, allocate, run, read the status, free -- it synchronises.
+ * plan.  The status word is sticky until read with rtcdf_batch_status_get.
+ * rtcdf_sort_batched_host is the one-shot form over host arrays: plan,
+ * allocate, run, read the status, free -- it synchronises.
+ *
+ * rtcdf_sort_batched (below the plan API) takes the metadata in DEVICE memory
+ * and plans on the device: asynchronous and stream-ordered, no host
+ * synchronisation.
  */
 typedef struct rtcdf_batch_plan rtcdf_batch_plan;
 
@@ -383,16 +391,59 @@ rtcdf_status rtcdf_batch_status_get(void *workspace, rtcdf_stream_t stream,
 rtcdf_status rtcdf_sort_batched_profiled(const rtcdf_batch_plan *plan, const int32_t *in,
                                          int32_t *out, void *workspace, size_t ws_bytes,
                                          uint64_t *profile, rtcdf_stream_t stream);
+/* One-shot segmented sort over HOST metadata (the plan API's arrays):
+ * plans on the host, allocates, runs, reads the status and frees; it
+ * synchronises `stream` and returns the device status. */
+rtcdf_status rtcdf_sort_batched_host(const int32_t *in, int32_t *out, const int64_t *seg_offsets,
+                                     const int64_t *seg_minVal, const int64_t *seg_maxVal,
+                                     int32_t num_segments, rtcdf_stream_t stream);
+
+/*
+ * rtcdf_sort_batched -- segmented sort with the segment metadata in DEVICE
+ * memory (e.g. written by earlier kernels on `stream`): int64 seg_offsets
+ * (S+1 entries, nondecreasing, seg_offsets[0] >= 0), seg_minVal and
+ * seg_maxVal (S entries), 8-byte aligned.  Each segment s is sorted as in the
+ * plan API (Section 2.1's problem per segment, Algorithms 4-7).  The work
+ * lists are built on the device by two planner kernels, so the call enqueues
+ * five launches and returns: asynchronous, stream-ordered, no host
+ * synchronisation.
+ *
+ * The caller states bounds the metadata must keep: num_segments (S),
+ * max_total_keys (>= seg_offsets[S]; also the length checked for in/out
+ * overlap) and max_R (every R_s <= max_R <= 2^20).  The workspace is sized
+ * from them (rtcdf_batch_device_workspace_size): about 12 bytes x max_R per
+ * segment plus O(S + max_total_keys / 65536) -- every segment owns a slot for
+ * a range of max_R.  Metadata that breaks a bound (or a limit of the
+ * segmented sort) sets RTCDF_DEV_BAD_SEGMENT in the device status word and
+ * nothing is written; the status calls then return RTCDF_ERR_INVALID_ARG.
+ *
+ * rtcdf_sort_batched uses a library-owned workspace per (device, stream),
+ * grown on demand by stream-ordered allocation (inside CUDA graph capture it
+ * must already be large enough: rtcdf_batch_reserve); rtcdf_status_get reads
+ * its status.  rtcdf_sort_batched_device_ws takes a caller workspace
+ * (256-byte aligned, zero-filled before its first use, left ready for the
+ * next call of any layout within the same bounds; calls sharing it must be
+ * ordered): no allocation, so it can be captured in a CUDA graph and replayed
+ * with new keys AND new segment metadata.  Its status: rtcdf_batch_status_get.
+ * Host-side errors (returned at once, nothing enqueued): RTCDF_ERR_INVALID_ARG
+ * for S < 0, max_total_keys >= 2^40, null or misaligned pointers, in/out
+ * partial overlap; RTCDF_ERR_RANGE for max_R outside 1..2^20;
+ * RTCDF_ERR_NO_MEMORY for a workspace that is too small (or cannot grow).
+ */
+#define RTCDF_DEV_BAD_SEGMENT 0x4
+rtcdf_status rtcdf_batch_device_workspace_size(int32_t num_segments, uint64_t max_total_keys, int64_t max_R,
+                                               size_t *bytes);
+rtcdf_status rtcdf_sort_batched_device_ws(const int32_t *in, int32_t *out, const int64_t *seg_offsets,
+                                          const int64_t *seg_minVal, const int64_t *seg_maxVal,
+                                          int32_t num_segments, uint64_t max_total_keys, int64_t max_R,
+                                          void *workspace, size_t ws_bytes, rtcdf_stream_t stream);
 rtcdf_status rtcdf_sort_batched(const int32_t *in, int32_t *out, const int64_t *seg_offsets,
-                                const int64_t *seg_minVal, const int64_t *seg_maxVal,
-                                int32_t num_segments, rtcdf_stream_t stream);
-/* rtcdf_sort_batched with the segment metadata (the same three arrays) in
- * DEVICE memory, e.g. produced by earlier kernels on `stream`: they are copied
- * to the host after that work (the plan is built on the host), then the call
- * proceeds as rtcdf_sort_batched.  Synchronises `stream`. */
-rtcdf_status rtcdf_sort_batched_device(const int32_t *in, int32_t *out, const int64_t *d_seg_offsets,
-                                       const int64_t *d_seg_minVal, const int64_t *d_seg_maxVal,
-                                       int32_t num_segments, rtcdf_stream_t stream);
+                                const int64_t *seg_minVal, const int64_t *seg_maxVal, int32_t num_segments,
+                                uint64_t max_total_keys, int64_t max_R, rtcdf_stream_t stream);
+/* Grow the library-owned workspace of `stream` for these bounds (needed
+ * before capturing rtcdf_sort_batched in a CUDA graph). */
+rtcdf_status rtcdf_batch_reserve(int32_t num_segments, uint64_t max_total_keys, int64_t max_R,
+                                 rtcdf_stream_t stream);
 
 /*
  * Continuous-batching server.  A trace of sort requests (arrival times

@@ -334,13 +334,14 @@ rtcdf_status rtcdf_batch_status_get(void *workspace, rtcdf_stream_t stream, int3
     if (device_status) *device_status = (int32_t)v;
     // A wait that ran out makes every other finding unreliable: report it first.
     if (v & kDevTimeout) return RTCDF_ERR_TIMEOUT;
+    if (v & kDevBadSegment) return RTCDF_ERR_INVALID_ARG;
     if (v & kDevKeyOutOfRange) return RTCDF_ERR_KEY_OUT_OF_RANGE;
     return RTCDF_OK;
 }
 
-rtcdf_status rtcdf_sort_batched(const int32_t *in, int32_t *out, const int64_t *seg_offsets,
-                                const int64_t *seg_minVal, const int64_t *seg_maxVal,
-                                int32_t num_segments, rtcdf_stream_t stream) {
+rtcdf_status rtcdf_sort_batched_host(const int32_t *in, int32_t *out, const int64_t *seg_offsets,
+                                     const int64_t *seg_minVal, const int64_t *seg_maxVal,
+                                     int32_t num_segments, rtcdf_stream_t stream) {
     rtcdf_batch_plan *plan = nullptr;
     rtcdf_status st = rtcdf_batch_plan_create(seg_offsets, seg_minVal, seg_maxVal, num_segments, &plan);
     if (st) return st;
@@ -359,27 +360,6 @@ rtcdf_status rtcdf_sort_batched(const int32_t *in, int32_t *out, const int64_t *
     const bool freed = cudaFreeAsync(ws, s) == cudaSuccess && cudaStreamSynchronize(s) == cudaSuccess;
     rtcdf_batch_plan_destroy(plan);
     return st ? st : dst ? dst : freed ? RTCDF_OK : RTCDF_ERR_CUDA;
-}
-
-rtcdf_status rtcdf_sort_batched_device(const int32_t *in, int32_t *out, const int64_t *d_seg_offsets,
-                                       const int64_t *d_seg_minVal, const int64_t *d_seg_maxVal,
-                                       int32_t num_segments, rtcdf_stream_t stream) try {
-    if (num_segments < 0) return RTCDF_ERR_INVALID_ARG;
-    if (num_segments > 0 && (!d_seg_offsets || !d_seg_minVal || !d_seg_maxVal)) return RTCDF_ERR_INVALID_ARG;
-    const size_t S = (size_t)num_segments;
-    std::vector<int64_t> offs(S + 1, 0), mn(S), mx(S);
-    cudaStream_t s = (cudaStream_t)stream;
-    // The plan is built on the host: bring the metadata over (ordered after
-    // the work on `stream` that produced it).
-    if (S > 0 &&
-        (cudaMemcpyAsync(offs.data(), d_seg_offsets, (S + 1) * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-         cudaMemcpyAsync(mn.data(), d_seg_minVal, S * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-         cudaMemcpyAsync(mx.data(), d_seg_maxVal, S * 8, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
-         cudaStreamSynchronize(s) != cudaSuccess))
-        return RTCDF_ERR_CUDA;
-    return rtcdf_sort_batched(in, out, offs.data(), mn.data(), mx.data(), num_segments, stream);
-} catch (...) {  // an allocation failed (std::bad_alloc and the like)
-    return RTCDF_ERR_NO_MEMORY;
 }
 
 }  // extern "C"

@@ -358,19 +358,40 @@ __device__ __forceinline__ uint32_t next_after(const uint32_t *e, uint32_t lo, u
 
 }  // namespace
 
-__global__ void __launch_bounds__(kSegThreads, 2) seg_first_kernel(BatchArgs a) {
-    extern __shared__ uint32_t sm[];
-    // The scan launch may be scheduled as soon as every CTA here has started;
-    // it waits for this grid to finish before reading anything.
-    asm volatile("griddepcontrol.launch_dependents;");
+__device__ __forceinline__ void first_item(const BatchArgs &a, uint32_t idx, uint32_t *sm) {
     const unsigned long long t0 = (a.prof && threadIdx.x == 0) ? global_ns() : 0ull;
-    const BatchItem it = a.items[blockIdx.x];
+    const BatchItem it = a.items[idx];
     const BatchSeg g = a.segs[it.seg];
     if (it.kind == kItemSmall) do_small(a, g, sm, kBatchSmallMaxR / 2, sm + kBatchSmallMaxR / 2);
     else do_hist(a, g, it, sm);
     if (a.prof) {
         __syncthreads();
         if (threadIdx.x == 0) prof_item(a, it.kind, t0, 0);
+    }
+}
+
+// DEV: the lists were built on the device (their lengths are in
+// a.dev_counts) and the grid is a fixed number of CTAs that take items by
+// ticket; otherwise one CTA per item of the host-built plan.
+template <bool DEV>
+__global__ void __launch_bounds__(kSegThreads, 2) seg_first_kernel(BatchArgs a) {
+    extern __shared__ uint32_t sm[];
+    // The scan launch may be scheduled as soon as every CTA here has started;
+    // it waits for this grid to finish before reading anything.
+    asm volatile("griddepcontrol.launch_dependents;");
+    if (!DEV) {
+        first_item(a, blockIdx.x, sm);
+        return;
+    }
+    __shared__ uint32_t s_idx;
+    const uint32_t n_first = a.dev_counts[0];
+    for (;;) {
+        if (threadIdx.x == 0) s_idx = atomicAdd(&a.ctl->first_ticket, 1u);
+        __syncthreads();
+        const uint32_t idx = s_idx;
+        __syncthreads();  // every thread has read s_idx (and the previous item's shared memory is free)
+        if (idx >= n_first) break;
+        first_item(a, idx, sm);
     }
 }
 
@@ -386,49 +407,27 @@ constexpr int kScanPerThread = kBatchScanChunk / kScanCtaThreads;  // 16
 // in 32 distinct banks.
 __device__ __forceinline__ uint32_t run_slot(uint32_t r) { return r + (r >> 5); }
 
-__global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs a) {
-    __shared__ uint32_t s_ticket;
-    __shared__ uint64_t s_warp[kScanCtaThreads / 32];
-    __shared__ uint64_t s_prefix, s_total;
-    __shared__ unsigned long long s_wait;
-    __shared__ uint32_t s_buf[kScanSmemWords];
-    uint32_t *s_end = s_buf;
-    int32_t *s_val = reinterpret_cast<int32_t *>(s_buf + kScanStageWords);
+// Shared memory of a scan-launch CTA.
+struct ScanShared {
+    uint64_t warp[kScanCtaThreads / 32];
+    uint64_t prefix, total;
+    unsigned long long wait;
+    uint32_t buf[kScanSmemWords];
+};
+
+// One 4096-bin chunk of a large segment's histogram: local CDF and offsets
+// (Algorithm 6) by the segment's decoupled lookback, the chunk's runs and the
+// first run of every output item that starts inside it.
+__device__ __forceinline__ void scan_chunk(const BatchArgs &a, const BatchItem &it, const BatchSeg &g, ScanShared &sh,
+                                           unsigned long long t0) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int kWarps = kScanCtaThreads / 32;
-    // The in-CTA segments come first in the grid (dispatched first; spreading
-    // them among the scan chunks was measured slower).
-    if (blockIdx.x < a.n_small2) {
-        // An in-CTA segment: independent of the first launch, so no wait.
-        asm volatile("griddepcontrol.launch_dependents;");
-        const unsigned long long ts = (a.prof && tid == 0) ? global_ns() : 0ull;
-        const BatchItem it = a.items[a.n_first + a.n_scan + blockIdx.x];
-        const BatchSeg g = a.segs[it.seg];
-        do_small(a, g, s_buf, kScanSmemWords - 64, s_buf + kScanSmemWords - 64);
-        if (a.prof) {
-            __syncthreads();
-            if (tid == 0) prof_item(a, kItemSmall, ts, 0);
-        }
-        return;
-    }
-    // The ticket and the chunk's descriptors come from plan data, not from the
-    // first launch: fetched before waiting for it.  (The ticket counter was
-    // reset by the previous run's output launch, which finished before this
-    // plan's first launch began.)
-    if (tid == 0) s_ticket = atomicAdd(&a.ctl->scan_ticket, 1u);
-    __syncthreads();
-    if (s_ticket >= a.n_scan) {
-        // Only with a workspace whose ticket was not zero: the chunk this
-        // ticket stood for is never published, so the output launch must not
-        // trust the run tables.
-        if (tid == 0) atomicOr(&a.ctl->status, kDevTimeout);
-        return;
-    }
-    const BatchItem it = a.items[a.n_first + s_ticket];
-    const BatchSeg g = a.segs[it.seg];
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    asm volatile("griddepcontrol.launch_dependents;");
-    const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
+    uint64_t *s_warp = sh.warp;
+    uint64_t &s_prefix = sh.prefix, &s_total = sh.total;
+    unsigned long long &s_wait = sh.wait;
+    uint32_t *s_buf = sh.buf;
+    uint32_t *s_end = s_buf;
+    int32_t *s_val = reinterpret_cast<int32_t *>(s_buf + kScanStageWords);
     const uint32_t chunk = (uint32_t)it.a;
     uint32_t *H = a.ws_u32 + g.hist_off;
     uint64_t *state = reinterpret_cast<uint64_t *>(a.ws_u32 + g.state_off);
@@ -558,21 +557,88 @@ __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs 
     }
 }
 
+
+template <bool DEV>
+__global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs a) {
+    __shared__ uint32_t s_ticket;
+    __shared__ ScanShared sh;
+    const int tid = threadIdx.x;
+    const uint32_t n_first = DEV ? a.dev_counts[0] : a.n_first;
+    const uint32_t n_scan = DEV ? a.dev_counts[1] : a.n_scan;
+    const uint32_t n_small2 = DEV ? a.dev_counts[2] : a.n_small2;
+    auto small_item = [&](uint32_t i) {
+        const unsigned long long ts = (a.prof && tid == 0) ? global_ns() : 0ull;
+        const BatchItem it = a.items[n_first + n_scan + i];
+        const BatchSeg g = a.segs[it.seg];
+        do_small(a, g, sh.buf, kScanSmemWords - 64, sh.buf + kScanSmemWords - 64);
+        if (a.prof) {
+            __syncthreads();
+            if (tid == 0) prof_item(a, kItemSmall, ts, 0);
+        }
+    };
+    if (!DEV) {
+        // The in-CTA segments come first in the grid (dispatched first;
+        // spreading them among the scan chunks was measured slower).
+        if (blockIdx.x < n_small2) {
+            // An in-CTA segment: independent of the first launch, so no wait.
+            asm volatile("griddepcontrol.launch_dependents;");
+            small_item(blockIdx.x);
+            return;
+        }
+        // The ticket and the chunk's descriptors come from plan data, not from
+        // the first launch: fetched before waiting for it.  (The ticket counter
+        // was reset by the previous run's output launch, which finished before
+        // this plan's first launch began.)
+        if (tid == 0) s_ticket = atomicAdd(&a.ctl->scan_ticket, 1u);
+        __syncthreads();
+        if (s_ticket >= n_scan) {
+            // Only with a workspace whose ticket was not zero: the chunk this
+            // ticket stood for is never published, so the output launch must
+            // not trust the run tables.
+            if (tid == 0) atomicOr(&a.ctl->status, kDevTimeout);
+            return;
+        }
+        const BatchItem it = a.items[n_first + s_ticket];
+        const BatchSeg g = a.segs[it.seg];
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        asm volatile("griddepcontrol.launch_dependents;");
+        const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
+        scan_chunk(a, it, g, sh, t0);
+        return;
+    }
+    // Device-built lists: a fixed grid takes the in-CTA segments (grid-stride,
+    // no wait), then the chunks by ticket.  A CTA takes its next ticket only
+    // after finishing its chunk, so every chunk a lookback waits for belongs
+    // to a running CTA.
+    asm volatile("griddepcontrol.launch_dependents;");
+    for (uint32_t i = blockIdx.x; i < n_small2; i += gridDim.x) {
+        small_item(i);
+        __syncthreads();
+    }
+    for (;;) {
+        if (tid == 0) s_ticket = atomicAdd(&a.ctl->scan_ticket, 1u);
+        __syncthreads();
+        const uint32_t tk = s_ticket;
+        __syncthreads();
+        if (tk >= n_scan) break;
+        const BatchItem it = a.items[n_first + tk];
+        const BatchSeg g = a.segs[it.seg];
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
+        scan_chunk(a, it, g, sh, t0);
+        __syncthreads();
+    }
+}
+
 // Output CTAs of 512 threads: four resident per SM, so that one CTA's
 // descriptor loads and window round trip overlap the others' stores.
 constexpr int kFillCtaThreads = 512;
 
-__global__ void __launch_bounds__(kFillCtaThreads) seg_fill_kernel(BatchArgs a) {
-    __shared__ uint32_t s_end[kSegFillRuns];
-    __shared__ int32_t s_val[kSegFillRuns];
+// One output item: positions [it.a, it.b) of its segment from the run table
+// (Algorithm 7's rule).
+__device__ __forceinline__ void fill_item(const BatchArgs &a, const BatchItem &it, const BatchSeg &g, uint32_t *s_end,
+                                          int32_t *s_val, unsigned long long t0) {
     const uint32_t tid = threadIdx.x, nt = blockDim.x;
-    // The item and its segment are plan data: fetched before waiting for the
-    // scan launch.
-    const BatchItem it = a.items[a.n_first + a.n_scan + a.n_small2 + blockIdx.x];
-    const BatchSeg g = a.segs[it.seg];
-    asm volatile("griddepcontrol.wait;" ::: "memory");
-    const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
-    if (blockIdx.x == 0 && tid == 0) a.ctl->scan_ticket = 0;
     if (it.aux == 0 && g.scan_chunks > 1) {
         // The segment's first output item leaves its lookback state zeroed.
         uint64_t *state = reinterpret_cast<uint64_t *>(a.ws_u32 + g.state_off);
@@ -671,6 +737,35 @@ __global__ void __launch_bounds__(kFillCtaThreads) seg_fill_kernel(BatchArgs a) 
     }
 }
 
+
+template <bool DEV>
+__global__ void __launch_bounds__(kFillCtaThreads) seg_fill_kernel(BatchArgs a) {
+    __shared__ uint32_t s_end[kSegFillRuns];
+    __shared__ int32_t s_val[kSegFillRuns];
+    const uint32_t tid = threadIdx.x;
+    if (!DEV) {
+        // The item and its segment are plan data: fetched before waiting for
+        // the scan launch.
+        const BatchItem it = a.items[a.n_first + a.n_scan + a.n_small2 + blockIdx.x];
+        const BatchSeg g = a.segs[it.seg];
+        asm volatile("griddepcontrol.wait;" ::: "memory");
+        const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
+        if (blockIdx.x == 0 && tid == 0) a.ctl->scan_ticket = 0;
+        fill_item(a, it, g, s_end, s_val, t0);
+        return;
+    }
+    const uint32_t base = a.dev_counts[0] + a.dev_counts[1] + a.dev_counts[2], n_fill = a.dev_counts[3];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
+    if (blockIdx.x == 0 && tid == 0) a.ctl->scan_ticket = 0;
+    for (uint32_t i = blockIdx.x; i < n_fill; i += gridDim.x) {
+        const BatchItem it = a.items[base + i];
+        const BatchSeg g = a.segs[it.seg];
+        const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
+        fill_item(a, it, g, s_end, s_val, t0);
+        __syncthreads();
+    }
+}
+
 namespace {
 
 cudaError_t launch_dep(const void *fn, uint32_t grid, int threads, const BatchArgs &a, bool programmatic,
@@ -692,7 +787,7 @@ cudaError_t launch_dep(const void *fn, uint32_t grid, int threads, const BatchAr
 }  // namespace
 
 cudaError_t launch_batched(const BatchArgs &a, cudaStream_t s) {
-    cudaError_t e = cudaFuncSetAttribute(seg_first_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(seg_first_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)kSegSmemBytes);
     if (e != cudaSuccess) return e;
     // A launch is a programmatic dependent only of the plan's own launch
@@ -700,19 +795,33 @@ cudaError_t launch_batched(const BatchArgs &a, cudaStream_t s) {
     // the first launch issued waits for all earlier work in the stream.
     bool chained = false;
     if (a.n_first) {
-        seg_first_kernel<<<a.n_first, kSegThreads, kSegSmemBytes, s>>>(a);
+        seg_first_kernel<false><<<a.n_first, kSegThreads, kSegSmemBytes, s>>>(a);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
         chained = true;
     }
     if (a.n_scan + a.n_small2) {
-        e = launch_dep((const void *)seg_scan_kernel, a.n_scan + a.n_small2, kScanCtaThreads, a, chained, s);
+        e = launch_dep((const void *)seg_scan_kernel<false>, a.n_scan + a.n_small2, kScanCtaThreads, a, chained, s);
         if (e != cudaSuccess) return e;
         chained = true;
     }
     if (a.n_fill &&
-        (e = launch_dep((const void *)seg_fill_kernel, a.n_fill, kFillCtaThreads, a, chained, s)) != cudaSuccess)
+        (e = launch_dep((const void *)seg_fill_kernel<false>, a.n_fill, kFillCtaThreads, a, chained, s)) != cudaSuccess)
         return e;
     return cudaSuccess;
+}
+
+cudaError_t launch_batched_dev(const BatchArgs &a, uint32_t first_ctas, uint32_t scan_ctas, uint32_t fill_ctas,
+                               cudaStream_t s) {
+    cudaError_t e = cudaFuncSetAttribute(seg_first_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)kSegSmemBytes);
+    if (e != cudaSuccess) return e;
+    // The first launch waits for the planner; every launch runs (the lists
+    // may be empty), so that the tickets are consumed and reset in order.
+    seg_first_kernel<true><<<first_ctas, kSegThreads, kSegSmemBytes, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    e = launch_dep((const void *)seg_scan_kernel<true>, scan_ctas, kScanCtaThreads, a, true, s);
+    if (e != cudaSuccess) return e;
+    return launch_dep((const void *)seg_fill_kernel<true>, fill_ctas, kFillCtaThreads, a, true, s);
 }
 
 }  // namespace rtcdf

@@ -1,6 +1,7 @@
 // Internal declarations of the segmented (batched) RT-CDF pipeline.
 #pragma once
 
+#include <climits>
 #include <vector>
 
 #include "rtcdf_internal.h"
@@ -62,8 +63,10 @@ struct BatchSegCtl {
 
 struct BatchCtl {
     uint32_t status;
-    uint32_t scan_ticket;  // dynamic order of the scan CTAs (reset by the output launch)
-    uint32_t pad[62];
+    uint32_t scan_ticket;   // dynamic order of the scan CTAs (reset by the output launch)
+    uint32_t first_ticket;  // device-built lists: items of the first launch taken so far
+                            // (reset by the planner before the first launch)
+    uint32_t pad[61];
 };
 
 struct BatchArgs {
@@ -80,9 +83,15 @@ struct BatchArgs {
     // Optional phase profile (device, RTCDF_BATCH_PROFILE_WORDS u64), or null:
     // per item kind busy ns, items, first start, last end, dependency-wait ns.
     unsigned long long *prof = nullptr;
+    // Lists built on the device: their lengths (n_first, n_scan, n_small2,
+    // n_fill) in device memory; null for a host-built plan.
+    const uint32_t *dev_counts = nullptr;
 };
 
 cudaError_t launch_batched(const BatchArgs &a, cudaStream_t s);
+// The three launches over device-built lists with fixed grids.
+cudaError_t launch_batched_dev(const BatchArgs &a, uint32_t first_ctas, uint32_t scan_ctas, uint32_t fill_ctas,
+                               cudaStream_t s);
 
 // Host planner shared by the plan API and the server: segment s reads
 // n[s] keys at in_off[s] and writes them sorted at out_off[s].
@@ -113,5 +122,125 @@ struct BatchTuning {
 int check_specs(const SegSpec *segs, uint32_t S);
 int build_host_plan(const SegSpec *segs, uint32_t S, HostPlan *plan,
                     const BatchTuning &tuning = BatchTuning());
+
+// ---------------------------------------------------------------- device planner
+// A segmented sort whose segment metadata lives in device memory is planned
+// on the device (devplan.cu) into a workspace sized from host-known bounds.
+// The per-segment and per-item rules below are shared by the planner kernels
+// and a host emulation of them (for checks on the CPU).
+struct DevBounds {
+    uint32_t S;                 // segments
+    uint32_t max_R;             // every R_s <= max_R <= kBatchMaxR
+    uint64_t max_total_keys;    // seg_offsets[S] <= max_total_keys
+};
+
+// Items of one segment in each list.
+struct DevSegCount {
+    uint32_t hist, small1, scan, small2, fill;
+};
+
+// Exclusive prefixes of DevSegCount over the segments before s (8 words).
+struct DevPfx {
+    uint32_t hist, small1, scan, small2, fill, pad[3];
+};
+
+// Lengths of the lists (the first four are BatchArgs::dev_counts).
+struct DevPlanHdr {
+    uint32_t n_first, n_scan, n_small2, n_fill, n_hist, n_small1;
+    uint32_t pad[58];
+};
+
+enum : uint32_t { kListHist = 0, kListSmall1 = 1, kListScan = 2, kListSmall2 = 3, kListFill = 4 };
+
+// Workspace layout of the device-planned sort (32-bit word offsets).  Every
+// segment owns a fixed slot [H | lookback state | run ends | run keys] sized
+// for max_R, so H and the state, zero between runs, stay where the next run
+// of any layout expects them.
+struct DevLayout {
+    size_t ctl, hdr, segctl, segs, pfx, items, start, slots, slot_words, total_words;
+    size_t slot_state, slot_run_end, slot_run_val;  // offsets inside a slot
+    uint64_t first_bound, scan_bound, small2_bound, fill_bound, item_bound;
+};
+// 0, or RTCDF_ERR_RANGE / RTCDF_ERR_INVALID_ARG for bounds out of range.
+int devplan_layout(const DevBounds &b, const BatchTuning &t, DevLayout *L);
+
+__host__ __device__ inline uint32_t devplan_field(const DevPfx &p, uint32_t list) {
+    return list == kListHist ? p.hist : list == kListSmall1 ? p.small1 : list == kListScan ? p.scan
+           : list == kListSmall2 ? p.small2 : p.fill;
+}
+
+// Segment s from its metadata: its descriptor (workspace offsets left to the
+// caller) and its items per list, as build_host_plan classifies it; false
+// when it breaks the bounds or the limits of a segmented sort.
+__host__ __device__ inline bool devplan_segment(int64_t o0, int64_t o1, int64_t mn, int64_t mx, const DevBounds &b,
+                                                const BatchTuning &t, BatchSeg *g, DevSegCount *c) {
+    *c = DevSegCount{0, 0, 0, 0, 0};
+    *g = BatchSeg{};
+    if (o0 < 0 || o1 < o0 || (uint64_t)o1 > b.max_total_keys) return false;
+    const uint64_t n = (uint64_t)(o1 - o0);
+    if (n >= (1ull << 32)) return false;
+    if (mn < INT32_MIN || mx > ((int64_t)1 << 31) || mx <= mn || mx - mn > (int64_t)b.max_R) return false;
+    g->off = g->out_off = (uint64_t)o0;
+    g->n = (uint32_t)n;
+    g->R = (uint32_t)(mx - mn);
+    g->minVal = (int32_t)mn;
+    if (n == 0) return true;
+    if (g->n <= t.small_max_n && g->R <= kBatchSmallMaxR) {
+        if (g->R <= t.small_scan_max_R) c->small2 = 1;
+        else c->small1 = 1;
+        return true;
+    }
+    g->m = (g->R + kBatchTileMax - 1) / kBatchTileMax;
+    g->T = (g->R + g->m - 1) / g->m;
+    const uint64_t chunks = (n + t.hist_chunk - 1) / t.hist_chunk;
+    g->hist_items = (uint32_t)(chunks * g->m);
+    g->single_hist = chunks == 1 ? 1u : 0u;
+    g->scan_chunks = (g->R + kBatchScanChunk - 1) / kBatchScanChunk;
+    g->fill_chunk = t.fill_chunk;
+    g->fill_items = (uint32_t)((n + t.fill_chunk - 1) / t.fill_chunk);
+    c->hist = g->hist_items;
+    c->scan = g->scan_chunks;
+    c->fill = g->fill_items;
+    return true;
+}
+
+// The k-th item of list `list` that belongs to segment s (k counted within the
+// segment), as build_host_plan lays it out.
+__host__ __device__ inline BatchItem devplan_item(uint32_t list, uint32_t s, uint32_t k, const BatchSeg &g,
+                                                  const BatchTuning &t) {
+    BatchItem it{};
+    it.seg = s;
+    switch (list) {
+        case kListHist: {
+            const uint32_t c = k / g.m;
+            it.kind = kItemHist;
+            it.a = (uint64_t)c * t.hist_chunk;
+            it.b = ((uint64_t)c + 1) * t.hist_chunk < g.n ? ((uint64_t)c + 1) * t.hist_chunk : g.n;
+            it.tile = k % g.m;
+            break;
+        }
+        case kListScan:
+            it.kind = kItemScan;
+            it.a = k;
+            break;
+        case kListFill:
+            it.kind = kItemFill;
+            it.a = (uint64_t)k * g.fill_chunk;
+            it.b = ((uint64_t)k + 1) * g.fill_chunk < g.n ? ((uint64_t)k + 1) * g.fill_chunk : g.n;
+            it.aux = k;
+            break;
+        default:
+            it.kind = kItemSmall;
+            break;
+    }
+    return it;
+}
+
+// Host emulation of the device planner: the descriptors, prefixes, list
+// lengths and items the planner kernels write (workspace offsets per the
+// layout), or a nonzero rtcdf_status for metadata that breaks the bounds.
+int devplan_host(const int64_t *offs, const int64_t *mn, const int64_t *mx, const DevBounds &b,
+                 const BatchTuning &t, const DevLayout &L, std::vector<BatchSeg> *segs,
+                 std::vector<DevPfx> *pfx, DevPlanHdr *hdr, std::vector<BatchItem> *items);
 
 }  // namespace rtcdf

@@ -1,0 +1,404 @@
+// Segmented sort with the segment metadata in device memory, planned on the
+// device: asynchronous, stream-ordered, no host synchronisation and no
+// allocation, so a caller whose segment layout is produced by earlier kernels
+// can enqueue the sort -- or capture it in a CUDA graph and replay it with new
+// layouts -- without a round trip through the host.
+//
+// Each segment is still sorted by Algorithms 4-7 (Section 3); the plan is the
+// same three work lists as the host planner's (batch_api.cu), built by two
+// kernels:
+//   1. devplan_segments_kernel (one CTA): every segment's descriptor and its
+//      item counts per list (the rules of devplan_segment, batched.h), and
+//      their exclusive prefixes -- a block-wide scan per 1024 segments;
+//   2. devplan_items_kernel (one thread per item): the list and the segment
+//      of an item index (a binary search in the prefixes), then the item.
+// The three launches then run over these lists with fixed grids whose CTAs
+// take items by ticket or by grid stride (seg_*_kernel<true>), since the list
+// lengths are known only on the device.
+//
+// The workspace is sized from host-known bounds (segment count, total keys,
+// widest range).  Every segment owns a fixed slot for its histogram, lookback
+// state and run tables, so the regions that must be zero when a run starts
+// (histogram, lookback state) are where the next run expects them whatever
+// its layout.  Metadata that breaks the bounds sets RTCDF_DEV_BAD_SEGMENT and
+// the lists are left empty: nothing is written.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <utility>
+
+#include "../../include/rtcdf.h"
+#include "batched.h"
+
+namespace rtcdf {
+
+namespace {
+
+size_t align64(uint64_t words) { return (size_t)((words + 63) / 64 * 64); }
+
+struct DevPlanArgs {
+    const int64_t *offs, *mn, *mx;
+    DevBounds b;
+    BatchTuning t;
+    uint32_t *ws;
+    DevLayout L;
+};
+
+__global__ void __launch_bounds__(1024) devplan_segments_kernel(DevPlanArgs p) {
+    __shared__ uint32_t s_warp[5][32];
+    __shared__ uint32_t s_tot[5], s_run[5];
+    __shared__ int s_bad;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    BatchCtl *ctl = reinterpret_cast<BatchCtl *>(p.ws + p.L.ctl);
+    BatchSeg *segs = reinterpret_cast<BatchSeg *>(p.ws + p.L.segs);
+    DevPfx *pfx = reinterpret_cast<DevPfx *>(p.ws + p.L.pfx);
+    if (tid == 0) {
+        s_bad = 0;
+        ctl->first_ticket = 0;  // the previous run has finished (stream order)
+    }
+    if (tid < 5) s_run[tid] = 0;
+    __syncthreads();
+    const uint32_t S = p.b.S;
+    for (uint32_t c0 = 0; c0 < S; c0 += 1024) {
+        const uint32_t s = c0 + tid;
+        DevSegCount c{0, 0, 0, 0, 0};
+        BatchSeg g{};
+        if (s < S && !devplan_segment(p.offs[s], p.offs[s + 1], p.mn[s], p.mx[s], p.b, p.t, &g, &c)) s_bad = 1;
+        const uint32_t v[5] = {c.hist, c.small1, c.scan, c.small2, c.fill};
+        uint32_t inc[5];
+#pragma unroll
+        for (int f = 0; f < 5; f++) {
+            inc[f] = v[f];
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc[f], d);
+                if (lane >= d) inc[f] += y;
+            }
+            if (lane == 31) s_warp[f][warp] = inc[f];
+        }
+        __syncthreads();
+        if (warp < 5) {
+            const uint32_t x = s_warp[warp][lane];
+            uint32_t xi = x;
+#pragma unroll
+            for (int d = 1; d < 32; d <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, xi, d);
+                if (lane >= d) xi += y;
+            }
+            s_warp[warp][lane] = xi - x;  // exclusive prefix of each warp
+            if (lane == 31) s_tot[warp] = xi;
+        }
+        __syncthreads();
+        if (s < S) {
+            uint32_t q[5];
+#pragma unroll
+            for (int f = 0; f < 5; f++) q[f] = s_run[f] + s_warp[f][warp] + inc[f] - v[f];
+            pfx[s] = DevPfx{q[0], q[1], q[2], q[3], q[4], {0, 0, 0}};
+            if (g.m > 0) {
+                const size_t slot = p.L.slots + (size_t)s * p.L.slot_words;
+                g.hist_off = slot;
+                g.state_off = slot + p.L.slot_state;
+                g.run_end_off = slot + p.L.slot_run_end;
+                g.run_val_off = slot + p.L.slot_run_val;
+                g.start_run_off = p.L.start + q[kListFill];
+            }
+            segs[s] = g;
+        }
+        __syncthreads();
+        if (tid < 5) s_run[tid] += s_tot[tid];
+        __syncthreads();
+    }
+    if (tid == 0) {
+        pfx[S] = DevPfx{s_run[0], s_run[1], s_run[2], s_run[3], s_run[4], {0, 0, 0}};
+        DevPlanHdr *h = reinterpret_cast<DevPlanHdr *>(p.ws + p.L.hdr);
+        const uint64_t nf = (uint64_t)s_run[kListHist] + s_run[kListSmall1];
+        // The bounds hold by construction; checked anyway, so that a list
+        // never outgrows its region.
+        const bool bad = s_bad || nf > p.L.first_bound || s_run[kListScan] > p.L.scan_bound ||
+                         s_run[kListSmall2] > p.L.small2_bound || s_run[kListFill] > p.L.fill_bound;
+        h->n_hist = bad ? 0 : s_run[kListHist];
+        h->n_small1 = bad ? 0 : s_run[kListSmall1];
+        h->n_first = bad ? 0 : (uint32_t)nf;
+        h->n_scan = bad ? 0 : s_run[kListScan];
+        h->n_small2 = bad ? 0 : s_run[kListSmall2];
+        h->n_fill = bad ? 0 : s_run[kListFill];
+        if (bad) atomicOr(&ctl->status, kDevBadSegment);
+    }
+}
+
+__global__ void __launch_bounds__(256) devplan_items_kernel(DevPlanArgs p) {
+    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
+    const DevPlanHdr *h = reinterpret_cast<const DevPlanHdr *>(p.ws + p.L.hdr);
+    const uint32_t nh = h->n_hist, nf = h->n_first, ns = h->n_scan, n2 = h->n_small2, nl = h->n_fill;
+    if (i >= (uint64_t)nf + ns + n2 + nl) return;
+    uint32_t list, k;
+    if (i < nh) {
+        list = kListHist, k = (uint32_t)i;
+    } else if (i < nf) {
+        list = kListSmall1, k = (uint32_t)(i - nh);
+    } else if (i < (uint64_t)nf + ns) {
+        list = kListScan, k = (uint32_t)(i - nf);
+    } else if (i < (uint64_t)nf + ns + n2) {
+        list = kListSmall2, k = (uint32_t)(i - nf - ns);
+    } else {
+        list = kListFill, k = (uint32_t)(i - nf - ns - n2);
+    }
+    // The segment whose items of this list include the k-th: the last s with
+    // prefix(s) <= k (prefix(0) = 0 <= k < prefix(S)).
+    const DevPfx *pfx = reinterpret_cast<const DevPfx *>(p.ws + p.L.pfx);
+    uint32_t lo = 0, hi = p.b.S;
+    while (hi - lo > 1) {
+        const uint32_t mid = lo + (hi - lo) / 2;
+        if (devplan_field(pfx[mid], list) <= k) lo = mid;
+        else hi = mid;
+    }
+    const BatchSeg *segs = reinterpret_cast<const BatchSeg *>(p.ws + p.L.segs);
+    BatchItem *items = reinterpret_cast<BatchItem *>(p.ws + p.L.items);
+    items[i] = devplan_item(list, lo, k - devplan_field(pfx[lo], list), segs[lo], p.t);
+}
+
+// Library-owned workspaces of rtcdf_sort_batched, per (device, stream).
+struct BatchCache {
+    void *ptr = nullptr;
+    size_t bytes = 0;
+};
+std::mutex g_bmu;
+std::map<std::pair<int, cudaStream_t>, BatchCache> g_bws;
+
+rtcdf_status check_bounds(int32_t S, uint64_t N, int64_t max_R, DevBounds *b) {
+    if (S < 0) return RTCDF_ERR_INVALID_ARG;
+    if (max_R < 1 || max_R > (int64_t)kBatchMaxR) return RTCDF_ERR_RANGE;
+    if (N >= (1ull << 40)) return RTCDF_ERR_INVALID_ARG;
+    *b = DevBounds{(uint32_t)S, (uint32_t)max_R, N};
+    return RTCDF_OK;
+}
+
+rtcdf_status grow_cache(cudaStream_t s, size_t need, void **ptr, size_t *bytes) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return RTCDF_ERR_CUDA;
+    std::lock_guard<std::mutex> lk(g_bmu);
+    BatchCache *c = nullptr;
+    try {
+        c = &g_bws[std::make_pair(dev, s)];
+    } catch (...) {
+        return RTCDF_ERR_NO_MEMORY;
+    }
+    if (c->bytes < need) {
+        cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+        if (cudaStreamIsCapturing(s, &cap) != cudaSuccess) return RTCDF_ERR_CUDA;
+        if (cap != cudaStreamCaptureStatusNone) return RTCDF_ERR_NO_MEMORY;
+        void *p = nullptr;
+        if (cudaMallocAsync(&p, need, s) != cudaSuccess) return RTCDF_ERR_NO_MEMORY;
+        if (cudaMemsetAsync(p, 0, need, s) != cudaSuccess) {
+            cudaFreeAsync(p, s);
+            return RTCDF_ERR_CUDA;
+        }
+        void *old = c->ptr;
+        c->ptr = p;
+        c->bytes = need;
+        if (old && cudaFreeAsync(old, s) != cudaSuccess) return RTCDF_ERR_CUDA;
+    }
+    *ptr = c->ptr;
+    *bytes = c->bytes;
+    return RTCDF_OK;
+}
+
+}  // namespace
+
+int devplan_layout(const DevBounds &b, const BatchTuning &t, DevLayout *L) {
+    if (b.max_R < 1 || b.max_R > kBatchMaxR) return RTCDF_ERR_RANGE;
+    const uint64_t S = b.S, N = b.max_total_keys;
+    const uint64_t cpr = (b.max_R + kBatchScanChunk - 1) / kBatchScanChunk;  // scan chunks per segment
+    const uint64_t m_max = (b.max_R + kBatchTileMax - 1) / kBatchTileMax;
+    L->first_bound = (N / t.hist_chunk + S) * m_max + S;
+    L->scan_bound = S * cpr;
+    L->small2_bound = S;
+    L->fill_bound = N / t.fill_chunk + S;
+    L->item_bound = L->first_bound + L->scan_bound + L->small2_bound + L->fill_bound;
+    size_t w = 0;
+    L->ctl = w;      w += 64;
+    L->hdr = w;      w += 64;
+    L->segctl = w;   w += align64(S * sizeof(BatchSegCtl) / 4);
+    L->segs = w;     w += align64(S * sizeof(BatchSeg) / 4);
+    L->pfx = w;      w += align64((S + 1) * sizeof(DevPfx) / 4);
+    L->items = w;    w += align64(L->item_bound * sizeof(BatchItem) / 4);
+    L->start = w;    w += align64(L->fill_bound);
+    L->slots = w;
+    L->slot_state = align64(cpr * kBatchScanChunk);
+    L->slot_run_end = L->slot_state + align64(2 * cpr);
+    L->slot_run_val = L->slot_run_end + align64(b.max_R);
+    L->slot_words = L->slot_run_val + align64(b.max_R);
+    w += S * L->slot_words;
+    L->total_words = w;
+    return 0;
+}
+
+int devplan_host(const int64_t *offs, const int64_t *mn, const int64_t *mx, const DevBounds &b,
+                 const BatchTuning &t, const DevLayout &L, std::vector<BatchSeg> *segs,
+                 std::vector<DevPfx> *pfx, DevPlanHdr *hdr, std::vector<BatchItem> *items) {
+    const uint32_t S = b.S;
+    segs->assign(S, BatchSeg{});
+    pfx->assign((size_t)S + 1, DevPfx{});
+    memset(hdr, 0, sizeof(*hdr));
+    items->clear();
+    uint32_t run[5] = {0, 0, 0, 0, 0};
+    for (uint32_t s = 0; s < S; s++) {
+        DevSegCount c;
+        BatchSeg g;
+        if (!devplan_segment(offs[s], offs[s + 1], mn[s], mx[s], b, t, &g, &c)) return RTCDF_ERR_INVALID_ARG;
+        (*pfx)[s] = DevPfx{run[0], run[1], run[2], run[3], run[4], {0, 0, 0}};
+        if (g.m > 0) {
+            const size_t slot = L.slots + (size_t)s * L.slot_words;
+            g.hist_off = slot;
+            g.state_off = slot + L.slot_state;
+            g.run_end_off = slot + L.slot_run_end;
+            g.run_val_off = slot + L.slot_run_val;
+            g.start_run_off = L.start + run[kListFill];
+        }
+        (*segs)[s] = g;
+        run[0] += c.hist, run[1] += c.small1, run[2] += c.scan, run[3] += c.small2, run[4] += c.fill;
+    }
+    (*pfx)[S] = DevPfx{run[0], run[1], run[2], run[3], run[4], {0, 0, 0}};
+    hdr->n_hist = run[0];
+    hdr->n_small1 = run[1];
+    hdr->n_first = run[0] + run[1];
+    hdr->n_scan = run[2];
+    hdr->n_small2 = run[3];
+    hdr->n_fill = run[4];
+    if (hdr->n_first > L.first_bound || hdr->n_scan > L.scan_bound || hdr->n_small2 > L.small2_bound ||
+        hdr->n_fill > L.fill_bound)
+        return RTCDF_ERR_INVALID_ARG;
+    // The items in the order the items kernel writes them: [hist | small1 |
+    // scan | small2 | fill], each list in segment order.
+    const uint32_t lists[5] = {kListHist, kListSmall1, kListScan, kListSmall2, kListFill};
+    for (uint32_t list : lists)
+        for (uint32_t s = 0; s < S; s++)
+            for (uint32_t k = devplan_field((*pfx)[s], list); k < devplan_field((*pfx)[s + 1], list); k++)
+                items->push_back(devplan_item(list, s, k - devplan_field((*pfx)[s], list), (*segs)[s], t));
+    return 0;
+}
+
+// The batch workspace of `stream` on the current device, if rtcdf_sort_batched
+// made one (for rtcdf_status_get).
+void *batch_stream_workspace(cudaStream_t s) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return nullptr;
+    std::lock_guard<std::mutex> lk(g_bmu);
+    auto it = g_bws.find(std::make_pair(dev, s));
+    return it == g_bws.end() ? nullptr : it->second.ptr;
+}
+
+}  // namespace rtcdf
+
+using namespace rtcdf;
+
+extern "C" {
+
+rtcdf_status rtcdf_batch_device_workspace_size(int32_t num_segments, uint64_t max_total_keys, int64_t max_R,
+                                               size_t *bytes) {
+    if (!bytes) return RTCDF_ERR_INVALID_ARG;
+    DevBounds b;
+    rtcdf_status st = check_bounds(num_segments, max_total_keys, max_R, &b);
+    if (st) return st;
+    DevLayout L;
+    if (const int rc = devplan_layout(b, BatchTuning(), &L)) return (rtcdf_status)rc;
+    *bytes = L.total_words * 4;
+    return RTCDF_OK;
+}
+
+rtcdf_status rtcdf_sort_batched_device_ws(const int32_t *in, int32_t *out, const int64_t *seg_offsets,
+                                          const int64_t *seg_minVal, const int64_t *seg_maxVal,
+                                          int32_t num_segments, uint64_t max_total_keys, int64_t max_R,
+                                          void *workspace, size_t ws_bytes, rtcdf_stream_t stream) {
+    DevBounds b;
+    rtcdf_status st = check_bounds(num_segments, max_total_keys, max_R, &b);
+    if (st) return st;
+    if (num_segments == 0 || max_total_keys == 0) return RTCDF_OK;
+    if (!in || !out || !seg_offsets || !seg_minVal || !seg_maxVal || !workspace) return RTCDF_ERR_INVALID_ARG;
+    if (((uintptr_t)in & 3) || ((uintptr_t)out & 3) || ((uintptr_t)workspace & 255) ||
+        ((uintptr_t)seg_offsets & 7) || ((uintptr_t)seg_minVal & 7) || ((uintptr_t)seg_maxVal & 7))
+        return RTCDF_ERR_INVALID_ARG;
+    if ((const void *)in != (const void *)out) {
+        const uintptr_t x = (uintptr_t)in, y = (uintptr_t)out, n = max_total_keys * 4;
+        if (x < y + n && y < x + n) return RTCDF_ERR_INVALID_ARG;
+    }
+    const BatchTuning tun;
+    DevLayout L;
+    if (const int rc = devplan_layout(b, tun, &L)) return (rtcdf_status)rc;
+    if (ws_bytes < L.total_words * 4) return RTCDF_ERR_NO_MEMORY;
+    int dev = 0, sms = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return RTCDF_ERR_CUDA;
+    cudaStream_t s = (cudaStream_t)stream;
+    uint32_t *ws = (uint32_t *)workspace;
+    DevPlanArgs p;
+    p.offs = seg_offsets;
+    p.mn = seg_minVal;
+    p.mx = seg_maxVal;
+    p.b = b;
+    p.t = tun;
+    p.ws = ws;
+    p.L = L;
+    devplan_segments_kernel<<<1, 1024, 0, s>>>(p);
+    if (cudaGetLastError() != cudaSuccess) return RTCDF_ERR_CUDA;
+    const uint64_t blocks = (L.item_bound + 255) / 256;
+    if (blocks > 0x7fffffffull) return RTCDF_ERR_INVALID_ARG;
+    devplan_items_kernel<<<(unsigned)blocks, 256, 0, s>>>(p);
+    if (cudaGetLastError() != cudaSuccess) return RTCDF_ERR_CUDA;
+    BatchArgs a;
+    a.in = in;
+    a.out = out;
+    a.segs = reinterpret_cast<const BatchSeg *>(ws + L.segs);
+    a.items = reinterpret_cast<const BatchItem *>(ws + L.items);
+    a.n_first = (uint32_t)std::min<uint64_t>(L.first_bound, UINT32_MAX);
+    a.n_scan = (uint32_t)std::min<uint64_t>(L.scan_bound, UINT32_MAX);
+    a.n_small2 = (uint32_t)std::min<uint64_t>(L.small2_bound, UINT32_MAX);
+    a.n_fill = (uint32_t)std::min<uint64_t>(L.fill_bound, UINT32_MAX);
+    a.num_segs = b.S;
+    a.ws_u32 = ws;
+    a.ctl = reinterpret_cast<BatchCtl *>(ws + L.ctl);
+    a.seg_ctl = reinterpret_cast<BatchSegCtl *>(ws + L.segctl);
+    a.dev_counts = ws + L.hdr;  // n_first, n_scan, n_small2, n_fill
+    // Resident CTAs per launch: two first-launch CTAs, six scan CTAs and four
+    // output CTAs per SM.
+    const uint32_t first = (uint32_t)std::min<uint64_t>(L.first_bound, 2ull * sms);
+    const uint32_t scan = (uint32_t)std::min<uint64_t>(L.scan_bound + L.small2_bound, 6ull * sms);
+    const uint32_t fill = (uint32_t)std::min<uint64_t>(L.fill_bound, 4ull * sms);
+    if (launch_batched_dev(a, std::max(first, 1u), std::max(scan, 1u), std::max(fill, 1u), s) != cudaSuccess)
+        return RTCDF_ERR_CUDA;
+    return RTCDF_OK;
+}
+
+rtcdf_status rtcdf_batch_reserve(int32_t num_segments, uint64_t max_total_keys, int64_t max_R,
+                                 rtcdf_stream_t stream) try {
+    size_t need = 0;
+    rtcdf_status st = rtcdf_batch_device_workspace_size(num_segments, max_total_keys, max_R, &need);
+    if (st) return st;
+    void *ws = nullptr;
+    size_t bytes = 0;
+    return grow_cache((cudaStream_t)stream, std::max<size_t>(need, 256), &ws, &bytes);
+} catch (...) {
+    return RTCDF_ERR_NO_MEMORY;
+}
+
+rtcdf_status rtcdf_sort_batched(const int32_t *in, int32_t *out, const int64_t *seg_offsets,
+                                const int64_t *seg_minVal, const int64_t *seg_maxVal, int32_t num_segments,
+                                uint64_t max_total_keys, int64_t max_R, rtcdf_stream_t stream) try {
+    size_t need = 0;
+    rtcdf_status st = rtcdf_batch_device_workspace_size(num_segments, max_total_keys, max_R, &need);
+    if (st) return st;
+    if (num_segments == 0 || max_total_keys == 0) return RTCDF_OK;
+    if (!in || !out || !seg_offsets || !seg_minVal || !seg_maxVal) return RTCDF_ERR_INVALID_ARG;
+    void *ws = nullptr;
+    size_t bytes = 0;
+    st = grow_cache((cudaStream_t)stream, std::max<size_t>(need, 256), &ws, &bytes);
+    if (st) return st;
+    return rtcdf_sort_batched_device_ws(in, out, seg_offsets, seg_minVal, seg_maxVal, num_segments,
+                                        max_total_keys, max_R, ws, bytes, stream);
+} catch (...) {
+    return RTCDF_ERR_NO_MEMORY;
+}
+
+}  // extern "C"

@@ -292,6 +292,15 @@ rtcdf_status cached_workspace(cudaStream_t s, size_t need, void **ptr, size_t *b
     return RTCDF_OK;
 }
 
+// The status code for a status word: a wait that ran out makes every other
+// finding unreliable, so it comes first.
+rtcdf_status status_of_bits(uint32_t v) {
+    if (v & kDevTimeout) return RTCDF_ERR_TIMEOUT;
+    if (v & kDevBadSegment) return RTCDF_ERR_INVALID_ARG;
+    if (v & kDevKeyOutOfRange) return RTCDF_ERR_KEY_OUT_OF_RANGE;
+    return RTCDF_OK;
+}
+
 rtcdf_status read_status(void *ws, cudaStream_t s, int32_t *out) {
     uint32_t v = 0;
     Ctl *ctl = (Ctl *)ws;
@@ -299,10 +308,7 @@ rtcdf_status read_status(void *ws, cudaStream_t s, int32_t *out) {
     if (cudaMemsetAsync(&ctl->status, 0, 4, s) != cudaSuccess) return RTCDF_ERR_CUDA;
     if (cudaStreamSynchronize(s) != cudaSuccess) return RTCDF_ERR_CUDA;
     if (out) *out = (int32_t)v;
-    // A wait that ran out makes every other finding unreliable: report it first.
-    if (v & kDevTimeout) return RTCDF_ERR_TIMEOUT;
-    if (v & kDevKeyOutOfRange) return RTCDF_ERR_KEY_OUT_OF_RANGE;
-    return RTCDF_OK;
+    return status_of_bits(v);
 }
 
 }  // namespace
@@ -507,11 +513,20 @@ rtcdf_status rtcdf_status_get(rtcdf_stream_t stream, int32_t *device_status) {
         auto it = g_ws.find(std::make_pair(dev, (cudaStream_t)stream));
         if (it != g_ws.end()) ws = it->second.ptr;
     }
-    if (!ws) {
-        if (device_status) *device_status = 0;
-        return RTCDF_OK;
+    // The single-array sorts' workspace and the segmented sorts' one (both
+    // start with their status word).
+    void *bws = batch_stream_workspace((cudaStream_t)stream);
+    int32_t bits = 0, b2 = 0;
+    if (ws) {
+        const rtcdf_status st = read_status(ws, (cudaStream_t)stream, &bits);
+        if (st == RTCDF_ERR_CUDA) return st;
     }
-    return read_status(ws, (cudaStream_t)stream, device_status);
+    if (bws) {
+        const rtcdf_status st = read_status(bws, (cudaStream_t)stream, &b2);
+        if (st == RTCDF_ERR_CUDA) return st;
+    }
+    if (device_status) *device_status = bits | b2;
+    return status_of_bits((uint32_t)(bits | b2));
 }
 
 rtcdf_status rtcdf_ws_status_get(void *workspace, rtcdf_stream_t stream, int32_t *device_status) {

@@ -17,6 +17,11 @@ bool tune_lookup(uint64_t n, uint32_t R, rtcdf_params *out);
 // Device status bits (mirror RTCDF_DEV_* in rtcdf.h).
 constexpr uint32_t kDevKeyOutOfRange = 0x1;
 constexpr uint32_t kDevTimeout = 0x2;
+constexpr uint32_t kDevBadSegment = 0x4;
+
+// The library-owned workspace of rtcdf_sort_batched for `s` on the current
+// device, or null (devplan.cu).
+void *batch_stream_workspace(cudaStream_t s);
 
 // Local-CDF scan: one CTA of kScanThreads threads scans kScanChunk histogram
 // bins (kScanItems per thread); chunks are chained by a decoupled lookback.

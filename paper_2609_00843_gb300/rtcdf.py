@@ -25,6 +25,7 @@ ERR_NO_MEMORY = 5
 ERR_TIMEOUT = 6
 DEV_KEY_OUT_OF_RANGE = 0x1
 DEV_TIMEOUT = 0x2
+DEV_BAD_SEGMENT = 0x4
 MAX_R = 1 << 24
 STATIC_MAX_R = 1 << 16
 
@@ -143,9 +144,11 @@ def lib():
             L.rtcdf_batch_status_get.argtypes = [vp, vp, ctypes.POINTER(i32)]
             L.rtcdf_sort_batched_profiled.argtypes = [vp, vp, vp, vp, sz, vp, vp]
             L.rtcdf_sort_batched_profiled.restype = ctypes.c_int
-            L.rtcdf_sort_batched.argtypes = [vp, vp, vp, vp, vp, i32, vp]
-            L.rtcdf_sort_batched_device.argtypes = [vp, vp, vp, vp, vp, i32, vp]
-            L.rtcdf_sort_batched_device.restype = ctypes.c_int
+            L.rtcdf_sort_batched_host.argtypes = [vp, vp, vp, vp, vp, i32, vp]
+            L.rtcdf_sort_batched.argtypes = [vp, vp, vp, vp, vp, i32, u64, i64, vp]
+            L.rtcdf_sort_batched_device_ws.argtypes = [vp, vp, vp, vp, vp, i32, u64, i64, vp, sz, vp]
+            L.rtcdf_batch_device_workspace_size.argtypes = [i32, u64, i64, ctypes.POINTER(sz)]
+            L.rtcdf_batch_reserve.argtypes = [i32, u64, i64, vp]
             L.rtcdf_tune_n_class.argtypes = [u64]
             L.rtcdf_tune_n_class.restype = i32
             L.rtcdf_tune_set.argtypes = [ctypes.POINTER(TuneEntry), i32]
@@ -165,7 +168,9 @@ def lib():
                       "rtcdf_plan", "rtcdf_sort_static", "rtcdf_sort_host", "rtcdf_batch_plan_create",
                       "rtcdf_batch_plan_destroy", "rtcdf_batch_workspace_size",
                       "rtcdf_batch_plan_info", "rtcdf_sort_batched_ws", "rtcdf_batch_status_get",
-                      "rtcdf_sort_batched", "rtcdf_hist_accumulate", "rtcdf_fill_from_counts"):
+                      "rtcdf_sort_batched", "rtcdf_hist_accumulate", "rtcdf_fill_from_counts",
+                      "rtcdf_sort_batched_host", "rtcdf_sort_batched_device_ws",
+                      "rtcdf_batch_device_workspace_size", "rtcdf_batch_reserve"):
                 getattr(L, f).restype = ctypes.c_int
             L.rtcdf_status_str.argtypes = [ctypes.c_int]
             L.rtcdf_status_str.restype = ctypes.c_char_p
@@ -294,19 +299,42 @@ def rtcdf_batch_status_get(ws_ptr: int, stream: int = 0) -> tuple[int, int]:
     return rc, bits.value
 
 
-def rtcdf_sort_batched(in_ptr: int, out_ptr: int, seg_offsets, seg_minVal, seg_maxVal,
-                       stream: int = 0) -> int:
+def rtcdf_sort_batched_host(in_ptr: int, out_ptr: int, seg_offsets, seg_minVal, seg_maxVal,
+                            stream: int = 0) -> int:
+    """One-shot segmented sort over host metadata (synchronises)."""
     o, op = _i64_array(seg_offsets)
     mn, mnp = _i64_array(seg_minVal)
     mx, mxp = _i64_array(seg_maxVal)
-    return lib().rtcdf_sort_batched(in_ptr, out_ptr, op, mnp, mxp, len(mn), stream)
+    return lib().rtcdf_sort_batched_host(in_ptr, out_ptr, op, mnp, mxp, len(mn), stream)
 
 
-def rtcdf_sort_batched_device(in_ptr: int, out_ptr: int, d_offsets_ptr: int, d_min_ptr: int,
-                              d_max_ptr: int, num_segments: int, stream: int = 0) -> int:
-    """rtcdf_sort_batched with int64 segment metadata in device memory."""
-    return lib().rtcdf_sort_batched_device(in_ptr, out_ptr, d_offsets_ptr, d_min_ptr, d_max_ptr,
-                                           num_segments, stream)
+def rtcdf_sort_batched(in_ptr: int, out_ptr: int, d_offsets_ptr: int, d_min_ptr: int, d_max_ptr: int,
+                       num_segments: int, max_total_keys: int, max_R: int, stream: int = 0) -> int:
+    """Segmented sort with int64 metadata in device memory, planned on the
+    device (asynchronous; library-owned workspace per stream)."""
+    return lib().rtcdf_sort_batched(in_ptr, out_ptr, d_offsets_ptr, d_min_ptr, d_max_ptr, num_segments,
+                                    max_total_keys, max_R, stream)
+
+
+def rtcdf_sort_batched_device_ws(in_ptr: int, out_ptr: int, d_offsets_ptr: int, d_min_ptr: int,
+                                 d_max_ptr: int, num_segments: int, max_total_keys: int, max_R: int,
+                                 ws_ptr: int, ws_bytes: int, stream: int = 0) -> int:
+    """rtcdf_sort_batched with a caller workspace (no allocation; capturable)."""
+    return lib().rtcdf_sort_batched_device_ws(in_ptr, out_ptr, d_offsets_ptr, d_min_ptr, d_max_ptr,
+                                              num_segments, max_total_keys, max_R, ws_ptr, ws_bytes,
+                                              stream)
+
+
+def rtcdf_batch_device_workspace_size(num_segments: int, max_total_keys: int, max_R: int) -> int:
+    out = ctypes.c_size_t(0)
+    rc = lib().rtcdf_batch_device_workspace_size(num_segments, max_total_keys, max_R, ctypes.byref(out))
+    if rc != OK:
+        raise RtcdfError(rc, "rtcdf_batch_device_workspace_size")
+    return out.value
+
+
+def rtcdf_batch_reserve(num_segments: int, max_total_keys: int, max_R: int, stream: int = 0) -> int:
+    return lib().rtcdf_batch_reserve(num_segments, max_total_keys, max_R, stream)
 
 
 def make_requests(n, minVal, maxVal, dist, seed, arrival_s):

@@ -6,13 +6,23 @@
 // keys and positions exactly once, and the per-segment workspace regions are
 // disjoint; the output launch issues its items by non-increasing estimated
 // cost (length x (1/4 + min(R, n) / n): vectors plus the runs crossed when
-// every value is present).  Usage: planner_check <seed> <segments>; prints
-// "OK" or the first violation.
+// every value is present).  The same shapes go through the host emulation of
+// the device planner (devplan_host: the rules the planner kernels apply): its
+// lists hold the right kinds in the right order, every segment's scan chunks
+// ascend, the items cover every segment's keys and positions exactly once, the
+// list lengths stay within the bounds the workspace was sized for, and every
+// segment's regions lie inside its own slot.
+// Usage: planner_check <seed> <segments>; prints "OK" or the first violation.
+// planner_check --emit <file> reads bounds and metadata ("S N maxR", then S+1
+// offsets, S minVal, S maxVal) and prints the layout, the list lengths, the
+// descriptors and the items of the emulated device plan (compared with the
+// GPU planner's workspace by a GPU test).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
 #include <random>
+#include <string>
 #include <vector>
 
 #include "batched.h"
@@ -128,7 +138,149 @@ static int check(const std::vector<SegSpec> &spec, const BatchTuning &tun) {
     return 0;
 }
 
+// Invariants of the device plan (host emulation) for the shapes of `spec`.
+static int check_dev(const std::vector<SegSpec> &spec, const BatchTuning &tun, uint32_t max_R) {
+    const uint32_t S = (uint32_t)spec.size();
+    std::vector<int64_t> offs(S + 1), mn(S), mx(S);
+    uint64_t N = 0;
+    for (uint32_t s = 0; s < S; s++) {
+        offs[s] = (int64_t)spec[s].in_off;
+        mn[s] = spec[s].minVal;
+        mx[s] = spec[s].maxVal;
+        N = spec[s].in_off + spec[s].n;
+    }
+    offs[S] = (int64_t)N;
+    const DevBounds b{S, max_R, N + 12345};
+    DevLayout L;
+    if (devplan_layout(b, tun, &L)) return fail("dev layout", 0, 0);
+    std::vector<BatchSeg> segs;
+    std::vector<DevPfx> pfx;
+    DevPlanHdr hdr;
+    std::vector<BatchItem> items;
+    const int rc = devplan_host(offs.data(), mn.data(), mx.data(), b, tun, L, &segs, &pfx, &hdr, &items);
+    bool any_bad = false;
+    for (uint32_t s = 0; s < S; s++) any_bad |= mx[s] - mn[s] > (int64_t)max_R;
+    if (any_bad) return rc ? 0 : fail("dev plan accepted a range above max_R", 0, 0);
+    if (rc) return fail("dev plan rejected", rc, 0);
+    if (hdr.n_first != hdr.n_hist + hdr.n_small1) return fail("dev first list", hdr.n_first, hdr.n_hist);
+    const size_t total = (size_t)hdr.n_first + hdr.n_scan + hdr.n_small2 + hdr.n_fill;
+    if (items.size() != total) return fail("dev item count", (long)items.size(), (long)total);
+    if (hdr.n_first > L.first_bound || hdr.n_scan > L.scan_bound || hdr.n_small2 > L.small2_bound ||
+        hdr.n_fill > L.fill_bound)
+        return fail("dev bounds", hdr.n_first, hdr.n_scan);
+    std::vector<uint32_t> small_seen(S, 0), next_chunk(S, 0), next_fill(S, 0);
+    std::vector<std::vector<std::pair<uint64_t, uint64_t>>> hist_rng(S);
+    for (size_t q = 0; q < items.size(); q++) {
+        const BatchItem &it = items[q];
+        if (it.seg >= S) return fail("dev segment index", (long)q, it.seg);
+        const BatchSeg &g = segs[it.seg];
+        const size_t e0 = hdr.n_hist, e1 = hdr.n_first, e2 = e1 + hdr.n_scan, e3 = e2 + hdr.n_small2;
+        const uint32_t want = q < e0 ? kItemHist : q < e1 ? kItemSmall : q < e2 ? kItemScan : q < e3 ? kItemSmall
+                                                                                                 : kItemFill;
+        if (it.kind != want) return fail("dev item kind", (long)q, it.kind);
+        switch (it.kind) {
+            case kItemHist:
+                if (it.tile >= g.m) return fail("dev tile index", (long)q, it.tile);
+                hist_rng[it.seg].push_back({it.a * 1024 + it.tile, it.b});
+                break;
+            case kItemSmall:
+                if ((q >= e2) != (g.R <= tun.small_scan_max_R)) return fail("dev small list by range", (long)q, g.R);
+                small_seen[it.seg]++;
+                break;
+            case kItemScan:
+                if (it.a != next_chunk[it.seg]) return fail("dev scan chunk order", (long)q, (long)it.a);
+                next_chunk[it.seg]++;
+                break;
+            case kItemFill:
+                if (it.aux != next_fill[it.seg] || it.a != (uint64_t)it.aux * g.fill_chunk ||
+                    it.b != std::min<uint64_t>(g.n, (uint64_t)(it.aux + 1) * g.fill_chunk))
+                    return fail("dev fill item", (long)q, it.aux);
+                next_fill[it.seg]++;
+                break;
+        }
+    }
+    for (uint32_t s = 0; s < S; s++) {
+        const BatchSeg &g = segs[s];
+        if (g.n != spec[s].n || g.off != spec[s].in_off || (int64_t)g.minVal != spec[s].minVal)
+            return fail("dev descriptor", s, g.n);
+        if (spec[s].n == 0) {
+            if (small_seen[s] || next_chunk[s] || next_fill[s] || !hist_rng[s].empty())
+                return fail("dev empty segment has items", s, 0);
+            continue;
+        }
+        if (g.m == 0) {
+            if (small_seen[s] != 1) return fail("dev small segment not exactly once", s, small_seen[s]);
+            continue;
+        }
+        if (small_seen[s]) return fail("dev large segment in one CTA", s, 0);
+        if (next_chunk[s] != g.scan_chunks) return fail("dev scan chunks", s, next_chunk[s]);
+        if (next_fill[s] != g.fill_items || (uint64_t)g.fill_items * g.fill_chunk < g.n)
+            return fail("dev fill coverage", s, next_fill[s]);
+        std::vector<std::vector<std::pair<uint64_t, uint64_t>>> per_tile(g.m);
+        for (auto &r : hist_rng[s]) per_tile[r.first % 1024].push_back({r.first / 1024, r.second});
+        for (uint32_t t = 0; t < g.m; t++) {
+            auto &v = per_tile[t];
+            std::sort(v.begin(), v.end());
+            uint64_t at = 0;
+            for (auto &r : v) {
+                if (r.first != at || r.second <= r.first) return fail("dev hist key ranges", s, t);
+                at = r.second;
+            }
+            if (at != g.n) return fail("dev hist keys not covered", s, t);
+        }
+        // regions inside the segment's own slot, the start runs inside the pool
+        const size_t slot = L.slots + (size_t)s * L.slot_words;
+        if (g.hist_off != slot || g.state_off != slot + L.slot_state) return fail("dev slot", s, (long)g.hist_off);
+        if (g.hist_off + (size_t)g.scan_chunks * kBatchScanChunk > g.state_off) return fail("dev hist region", s, 0);
+        if (g.state_off + 2 * (size_t)g.scan_chunks > g.run_end_off) return fail("dev state region", s, 0);
+        if (g.run_end_off + g.R > g.run_val_off || g.run_val_off + g.R > slot + L.slot_words)
+            return fail("dev run tables", s, 0);
+        if (g.state_off % 2 || g.hist_off % 4) return fail("dev alignment", s, 0);
+        if (g.start_run_off < L.start || g.start_run_off + g.fill_items > L.start + L.fill_bound)
+            return fail("dev start runs", s, (long)g.start_run_off);
+        if (slot + L.slot_words > L.total_words) return fail("dev workspace size", s, 0);
+    }
+    return 0;
+}
+
+// --emit: the emulated device plan for the bounds and metadata in a file.
+static int emit(const char *path) {
+    FILE *f = std::fopen(path, "r");
+    if (!f) return fail("cannot open", 0, 0);
+    unsigned long long S = 0, N = 0, maxR = 0;
+    if (std::fscanf(f, "%llu %llu %llu", &S, &N, &maxR) != 3) return fail("header", 0, 0);
+    std::vector<int64_t> offs(S + 1), mn(S), mx(S);
+    for (auto *v : {&offs, &mn, &mx})
+        for (auto &x : *v)
+            if (std::fscanf(f, "%lld", (long long *)&x) != 1) return fail("metadata", 0, 0);
+    std::fclose(f);
+    const DevBounds b{(uint32_t)S, (uint32_t)maxR, N};
+    const BatchTuning tun;
+    DevLayout L;
+    if (devplan_layout(b, tun, &L)) return fail("layout", 0, 0);
+    std::vector<BatchSeg> segs;
+    std::vector<DevPfx> pfx;
+    DevPlanHdr hdr;
+    std::vector<BatchItem> items;
+    const int rc = devplan_host(offs.data(), mn.data(), mx.data(), b, tun, L, &segs, &pfx, &hdr, &items);
+    std::printf("layout %zu %zu %zu %zu %zu %zu\n", L.ctl, L.hdr, L.segs, L.pfx, L.items, L.total_words);
+    std::printf("rc %d\n", rc);
+    std::printf("hdr %u %u %u %u %u %u\n", hdr.n_first, hdr.n_scan, hdr.n_small2, hdr.n_fill, hdr.n_hist,
+                hdr.n_small1);
+    for (const BatchSeg &g : segs)
+        std::printf("seg %llu %u %u %d %u %u %u %u %u %u %u %llu %llu %llu %llu %llu\n",
+                    (unsigned long long)g.off, g.n, g.R, g.minVal, g.T, g.m, g.hist_items, g.fill_items,
+                    g.fill_chunk, g.scan_chunks, g.single_hist, (unsigned long long)g.hist_off,
+                    (unsigned long long)g.run_end_off, (unsigned long long)g.run_val_off,
+                    (unsigned long long)g.start_run_off, (unsigned long long)g.state_off);
+    for (const BatchItem &it : items)
+        std::printf("item %u %u %llu %llu %u %u\n", it.kind, it.seg, (unsigned long long)it.a,
+                    (unsigned long long)it.b, it.tile, it.aux);
+    return 0;
+}
+
 int main(int argc, char **argv) {
+    if (argc > 2 && std::string(argv[1]) == "--emit") return emit(argv[2]);
     const unsigned seed = argc > 1 ? (unsigned)atoi(argv[1]) : 1;
     const int S = argc > 2 ? atoi(argv[2]) : 500;
     std::mt19937_64 rng(seed);
@@ -150,6 +302,11 @@ int main(int argc, char **argv) {
     tunings[5].small_scan_max_R = kSmallInScanCapR;
     for (auto &t : tunings)
         if (check(spec, t)) return 1;
+    // The device planner's rules, with bounds that hold and with one that
+    // some segment breaks.
+    for (auto &t : tunings)
+        for (uint32_t max_R : {1u << 20, 60000u})
+            if (check_dev(spec, t, max_R)) return 1;
     std::printf("OK\n");
     return 0;
 }

@@ -183,3 +183,37 @@ def test_sharded_entry_points_reject_bad_arguments_on_host():
     assert f(1 << 20, 100, 0, 128, 0, 100, (1 << 20) + 64, ws, wsb, 0) == rtcdf.ERR_INVALID_ARG  # out on counts
     assert f(1 << 20, 100, 0, 128, 0, 100, ws + 256, ws, wsb, 0) == rtcdf.ERR_INVALID_ARG  # out on workspace
     assert f(1 << 20, 100, 0, 128, 40, 40, 0, 0, 0, 0) == rtcdf.OK           # empty window
+
+
+def test_device_planned_segmented_sort_rejects_bad_arguments_on_host():
+    # All returned before any CUDA call.
+    size = rtcdf.rtcdf_batch_device_workspace_size
+    assert 0 < size(10, 1000, 100) < size(10, 1000, 1 << 20) < size(20, 1000, 1 << 20)
+    assert size(10, 1000, 100) < size(10, 10**9, 100)
+    for bad in ((10, 1000, 0), (10, 1000, (1 << 20) + 1)):
+        with pytest.raises(rtcdf.RtcdfError):
+            size(*bad)
+    f = rtcdf.rtcdf_sort_batched_device_ws
+    inp, out, o, a, b, ws = 1 << 24, 1 << 26, 1 << 20, (1 << 20) + 4096, (1 << 20) + 8192, 1 << 28
+    wsb = size(3, 1000, 100)
+    ok = dict(S=3, N=1000, R=100)
+
+    def call(i=inp, q=out, oo=o, aa=a, bb=b, S=3, N=1000, R=100, w=ws, wb=wsb):
+        return f(i, q, oo, aa, bb, S, N, R, w, wb, 0)
+    assert call(S=-1) == rtcdf.ERR_INVALID_ARG
+    assert call(R=0) == rtcdf.ERR_RANGE and call(R=(1 << 20) + 1) == rtcdf.ERR_RANGE
+    assert call(N=1 << 40) == rtcdf.ERR_INVALID_ARG
+    assert call(S=0) == rtcdf.OK and call(N=0) == rtcdf.OK      # nothing to sort
+    assert call(i=0) == rtcdf.ERR_INVALID_ARG and call(oo=0) == rtcdf.ERR_INVALID_ARG
+    assert call(w=0) == rtcdf.ERR_INVALID_ARG
+    assert call(i=inp + 2) == rtcdf.ERR_INVALID_ARG              # keys 4-byte aligned
+    assert call(oo=o + 4) == rtcdf.ERR_INVALID_ARG               # metadata 8-byte aligned
+    assert call(w=ws + 128) == rtcdf.ERR_INVALID_ARG             # workspace 256-byte aligned
+    assert call(q=inp + 400) == rtcdf.ERR_INVALID_ARG            # partial overlap
+    assert call(wb=wsb - 4) == rtcdf.ERR_NO_MEMORY
+    g = rtcdf.rtcdf_sort_batched
+    assert g(inp, out, o, a, b, -1, 1000, 100, 0) == rtcdf.ERR_INVALID_ARG
+    assert g(inp, out, o, a, b, 3, 1000, 0, 0) == rtcdf.ERR_RANGE
+    assert g(inp, out, o, a, b, 0, 1000, 100, 0) == rtcdf.OK
+    assert g(0, out, o, a, b, 3, 1000, 100, 0) == rtcdf.ERR_INVALID_ARG
+    assert ok

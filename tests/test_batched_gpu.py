@@ -117,7 +117,7 @@ def test_one_shot_entry_point_and_in_place():
     mins = [0, -10, 7, 4]
     x, offs, mn, mx = make_segments(lengths, Rs, mins, [0, 1, 0, 2], [1, 2, 3, 4])
     a = x.cpu().numpy().copy()
-    rc = rtcdf.rtcdf_sort_batched(x.data_ptr(), x.data_ptr(), offs, mn, mx, stream_handle())
+    rc = rtcdf.rtcdf_sort_batched_host(x.data_ptr(), x.data_ptr(), offs, mn, mx, stream_handle())
     assert rc == rtcdf.OK
     b = x.cpu().numpy()
     for s in range(len(lengths)):
@@ -206,21 +206,6 @@ def test_benchmark_batched_workload_every_segment():
         torch.cuda.synchronize()
     assert rtcdf.rtcdf_batch_status_get(ws.data_ptr(), st.cuda_stream) == (rtcdf.OK, 0)
     check_segments(x, out, offs, mns, mxs)
-
-
-def test_device_resident_metadata():
-    lengths = [70_000, 5, 300_000, 0, 12_345]
-    Rs = [1 << 12, 3, 1 << 17, 2, 500]
-    mins = [-100, 0, 1 << 20, 7, -(1 << 30)]
-    x, offs, mn, mx = make_segments(lengths, Rs, mins, [0, 1, 2, 0, 1], [5, 6, 7, 8, 9])
-    d_offs = torch.tensor(offs, dtype=torch.int64, device="cuda")
-    d_mn = torch.tensor(mn, dtype=torch.int64, device="cuda")
-    d_mx = torch.tensor(mx, dtype=torch.int64, device="cuda")
-    out = torch.empty_like(x)
-    rc = rtcdf.rtcdf_sort_batched_device(x.data_ptr(), out.data_ptr(), d_offs.data_ptr(), d_mn.data_ptr(),
-                                         d_mx.data_ptr(), len(lengths), stream_handle())
-    assert rc == rtcdf.OK, rtcdf.rtcdf_status_str(rc)
-    check_segments(x, out, offs, mn, mx)
 
 
 def test_plans_chained_on_one_stream_read_each_others_output():
