@@ -193,7 +193,7 @@ def test_gpu_planner_writes_what_the_host_emulation_computes(emitter, tmp_path):
     L, mn, R, dist, seeds = gen.batched_segments(gen.derive_seed(32), 700, n_lo=1, n_hi=3e5, r_hi=2 ** 18)
     mn = mn.astype(np.int64)
     x, offs, mns, mxs = make_layout(L, R, mn, dist, seeds)
-    S, N, max_R = len(L), x.numel() + 1000, 1 << 18
+    S, N, max_R = len(L), x.numel(), 1 << 18
     meta = tmp_path / "meta.txt"
     meta.write_text(f"{S} {N} {max_R}\n" + " ".join(map(str, offs)) + "\n" + " ".join(map(str, mns)) + "\n"
                     + " ".join(map(str, mxs)) + "\n")
