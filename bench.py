@@ -584,8 +584,10 @@ def serving_comparison(count: int, budget_gb: float = 32.0, max_large: int = 0):
     budget.  The arrival rate is rho x the throughput of sequential
     per-request calls (measured first with every request present at t=0),
     rho in {0.5, 0.9, 1.5}; each trace is served sequentially and by the
-    continuous-batching server.  Latency = completion - arrival; a request's keys are written into
-    its device slot by the generator at admission (data arrival)."""
+    continuous-batching server (large requests on high-priority streams;
+    at rho = 0.5 also without).  Latency = completion - arrival; a request's
+    keys are written into its device slot by the generator at admission (data
+    arrival)."""
     import numpy as np
     from paper_2609_00843_gb300 import gen, rtcdf
     seed = gen.derive_seed(5)
@@ -593,10 +595,10 @@ def serving_comparison(count: int, budget_gb: float = 32.0, max_large: int = 0):
     mx = mn + R
     fill = gen.fill_function_address()
 
-    def cfg():
+    def cfg(prio=1):
         return rtcdf.ServerConfig(budget_bytes=int(budget_gb * (1 << 30)), num_streams=4,
                                   max_batch=256, single_min_keys=1 << 22, fill=fill, digests=0,
-                                  max_large_inflight=max_large)
+                                  max_large_inflight=max_large, large_priority=prio)
     zero = np.zeros(count)
     r0 = rtcdf.make_requests(n, mn, mx, dist, seeds, zero)
     _, st0 = rtcdf.rtcdf_serve_sequential(cfg(), r0, count)
@@ -631,6 +633,14 @@ def serving_comparison(count: int, budget_gb: float = 32.0, max_large: int = 0):
                          "peak_GB": round(st.peak_bytes / 1e9, 2)}
         row["p99_ratio_sequential_vs_server"] = round(
             row["sequential"]["p99_latency_ms"] / max(1e-9, row["server"]["p99_latency_ms"]), 3)
+        if rho == 0.5:
+            # the same server with large requests on default-priority streams
+            res, st = rtcdf.rtcdf_serve_trace(cfg(prio=0), reqs, count)
+            lat = np.array([res[i].done_s - arr[i] for i in range(count)])
+            row["server_default_priority"] = {
+                "p50_latency_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
+                "p99_latency_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
+                "all_ok": all(res[i].status == 0 for i in range(count))}
         out["load"][str(rho)] = row
     main = out["load"]["0.9"]
     out["sequential"], out["server"] = main["sequential"], main["server"]

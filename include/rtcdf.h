@@ -494,6 +494,12 @@ typedef struct {
                                    completed, before its memory is released.  The
                                    copy is synchronous and holds up the serving
                                    loop: leave this NULL when timing. */
+    int32_t large_priority;     /* nonzero: requests of at least single_min_keys
+                                   keys are written and sorted on streams of the
+                                   device's highest stream priority (batches keep
+                                   the default priority), so a large sort runs
+                                   about as fast as alone while batches fill in */
+    int32_t reserved2;
 } rtcdf_server_config;
 
 typedef struct {

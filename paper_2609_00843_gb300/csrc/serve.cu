@@ -173,23 +173,37 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
     Slab alloc(cfg->budget_bytes);
     size_t ws_bytes = 0;
     rtcdf_workspace_size(maxR, &ws_bytes);
-    std::vector<size_t> ws_off(K);
+    // With large_priority, large requests get K streams of their own at the
+    // device's highest stream priority ([K, 2K)), batches the default ones
+    // ([0, K)): the block scheduler then issues a large sort's CTAs before
+    // the batches' whenever both wait, so it runs about as fast as alone
+    // while batches fill the gaps.  Stream priority is a property of the
+    // process's streams, not a device setting.
+    const bool prio = cfg->large_priority != 0;
+    const int NS = prio ? 2 * K : K;
+    int prio_least = 0, prio_greatest = 0;
+    if (prio) check(cudaDeviceGetStreamPriorityRange(&prio_least, &prio_greatest), RTCDF_ERR_CUDA);
+    auto make_stream = [&](cudaStream_t *st, bool high) {
+        if (high) check(cudaStreamCreateWithPriority(st, cudaStreamNonBlocking, prio_greatest), RTCDF_ERR_CUDA);
+        else check(cudaStreamCreateWithFlags(st, cudaStreamNonBlocking), RTCDF_ERR_CUDA);
+    };
+    std::vector<size_t> ws_off(NS);
     std::vector<cudaStream_t> &streams = res.streams;
-    streams.assign(K, nullptr);
-    for (int k = 0; k < K; k++) {
+    streams.assign(NS, nullptr);
+    for (int k = 0; k < NS; k++) {
         if (!alloc.alloc(ws_bytes, &ws_off[k])) return RTCDF_ERR_NO_MEMORY;
         check(cudaMemset(slab + ws_off[k], 0, ws_bytes), RTCDF_ERR_CUDA);
-        check(cudaStreamCreateWithFlags(&streams[k], cudaStreamNonBlocking), RTCDF_ERR_CUDA);
+        make_stream(&streams[k], k >= K);
     }
     // Inputs are written on their own streams (round robin), so writing the
     // next arrivals overlaps the sorts already running.  Each request's write
     // is marked by an event (from a pool, returned when the request retires):
-    // a launch waits for its own requests' inputs only.
+    // a launch waits for its own requests' inputs only.  With large_priority
+    // a large request's keys are written on high-priority streams too.
     std::vector<cudaStream_t> &fill_streams = res.fill_streams;
-    fill_streams.assign(K, nullptr);
-    for (int k = 0; k < K; k++)
-        check(cudaStreamCreateWithFlags(&fill_streams[k], cudaStreamNonBlocking), RTCDF_ERR_CUDA);
-    int fill_rr = 0;
+    fill_streams.assign(NS, nullptr);
+    for (int k = 0; k < NS; k++) make_stream(&fill_streams[k], k >= K);
+    int fill_rr = 0, fill_rr_hi = 0;
     std::vector<cudaEvent_t> &ev_pool = res.ev_pool, &req_ev = res.req_ev;
     req_ev.assign((size_t)count, nullptr);
     auto take_event = [&]() {
@@ -223,7 +237,7 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
     }
     std::deque<int64_t> pending;            // admitted, input enqueued
     std::vector<Launch> &inflight = res.inflight;
-    std::vector<bool> stream_busy(K, false);
+    std::vector<bool> stream_busy(NS, false);
     int64_t next = 0, done = 0;
     uint64_t launches_batched = 0, launches_single = 0, batched_requests = 0;
     int max_inflight = 0;
@@ -241,7 +255,7 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
             const rtcdf_request &r = reqs[next];
             size_t off = 0;
             const size_t bytes = (size_t)r.n * 8 + 512;
-            if ((size_t)r.n * 8 + 512 + reserve > cfg->budget_bytes - (size_t)K * ws_bytes) {
+            if ((size_t)r.n * 8 + 512 + reserve > cfg->budget_bytes - (size_t)NS * ws_bytes) {
                 results[next].status = RTCDF_ERR_NO_MEMORY;  // can never fit
                 results[next].admit_s = results[next].done_s = secs(t0);
                 next++, done++;
@@ -254,8 +268,14 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
             slot_off[next] = off;
             slot_bytes[next] = bytes;
             int32_t *in = reinterpret_cast<int32_t *>(slab + off);
-            const int fs = fill_rr;
-            fill_rr = (fill_rr + 1) % K;
+            int fs;
+            if (prio && r.n >= cfg->single_min_keys) {
+                fs = K + fill_rr_hi;
+                fill_rr_hi = (fill_rr_hi + 1) % K;
+            } else {
+                fs = fill_rr;
+                fill_rr = (fill_rr + 1) % K;
+            }
             if (r.n) {
                 if (cfg->fill(in, r.n, 0, r.minVal, r.maxVal - r.minVal, r.dist, r.seed,
                               (rtcdf_stream_t)fill_streams[fs]) != 0) {
@@ -275,17 +295,19 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
         }
         // 2. Launch pending requests on free streams.
         while (!pending.empty() && !err) {
+            // A large request alone (while fewer than max_large of them run),
+            // or every small pending request together.
+            const int64_t head = pending.front();
+            const bool take_large = reqs[head].n >= cfg->single_min_keys && large_inflight < max_large;
+            const int k_lo = (prio && take_large) ? K : 0, k_hi = prio ? k_lo + K : K;
             int k = -1;
-            for (int j = 0; j < K; j++)
+            for (int j = k_lo; j < k_hi; j++)
                 if (!stream_busy[j]) { k = j; break; }
             if (k < 0) break;
             cudaStream_t s = streams[k];
             Launch L;
             L.stream = k;
-            // A large request alone (while fewer than max_large of them run),
-            // or every small pending request together.
-            const int64_t head = pending.front();
-            if (reqs[head].n >= cfg->single_min_keys && large_inflight < max_large) {
+            if (take_large) {
                 pending.pop_front();
                 L.reqs.push_back(head);
                 L.large = true;

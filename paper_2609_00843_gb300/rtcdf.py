@@ -78,7 +78,8 @@ class ServerConfig(ctypes.Structure):
     _fields_ = [("budget_bytes", ctypes.c_uint64), ("num_streams", ctypes.c_int32),
                 ("max_batch", ctypes.c_int32), ("single_min_keys", ctypes.c_uint64),
                 ("fill", ctypes.c_void_p), ("digests", ctypes.c_int32),
-                ("max_large_inflight", ctypes.c_int32), ("outputs", ctypes.c_void_p)]
+                ("max_large_inflight", ctypes.c_int32), ("outputs", ctypes.c_void_p),
+                ("large_priority", ctypes.c_int32), ("reserved2", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):

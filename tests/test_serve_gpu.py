@@ -28,10 +28,11 @@ def trace(count, seed, n_hi=3e6, rate=20000.0, r_hi=2 ** 18):
     return n, mn, R, dist, seeds, arr
 
 
-def config(budget, digests=True, streams=4, max_batch=64, single_min=1 << 21, max_large=0):
+def config(budget, digests=True, streams=4, max_batch=64, single_min=1 << 21, max_large=0, prio=0):
     return rtcdf.ServerConfig(budget_bytes=budget, num_streams=streams, max_batch=max_batch,
                               single_min_keys=single_min, fill=gen.fill_function_address(),
-                              digests=1 if digests else 0, max_large_inflight=max_large)
+                              digests=1 if digests else 0, max_large_inflight=max_large,
+                              large_priority=prio)
 
 
 def output_buffers(n, chosen):
@@ -103,6 +104,25 @@ def test_served_outputs_equal_oracle_element_by_element():
     assert st.launches_batched > 0 and st.max_inflight > 1
     for i in range(count):
         assert res[i].status == 0, i
+    assert_outputs_match_oracle(bufs, n, mn, R, dist, seeds)
+
+
+def test_large_requests_on_high_priority_streams_match():
+    """Large requests written and sorted on high-priority streams, batches on
+    default ones: every result equals the one served alone, and a sample of
+    the large outputs equals the oracle element by element."""
+    count = 300
+    n, mn, R, dist, seeds, arr = trace(count, gen.derive_seed(55), n_hi=8e6, rate=20000.0)
+    reqs = rtcdf.make_requests(n, mn, mn + R, dist, seeds, arr)
+    big = np.nonzero(n >= (1 << 21))[0]
+    bufs, ptrs = output_buffers(n, list(big[:10]))
+    cfg = config(4 << 30, prio=1)
+    cfg.outputs = ctypes.cast(ptrs, ctypes.c_void_p)
+    mix, st = rtcdf.rtcdf_serve_trace(cfg, reqs, count)
+    alone, _ = rtcdf.rtcdf_serve_sequential(config(4 << 30), reqs, count)
+    assert st.launches_single > 0 and st.launches_batched > 0
+    for i in range(count):
+        assert mix[i].status == 0 and mix[i].digest == alone[i].digest, i
     assert_outputs_match_oracle(bufs, n, mn, R, dist, seeds)
 
 
