@@ -226,8 +226,14 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
     // stream's previous launch has completed).
     const size_t stage_bytes = 64u << 20;
     std::vector<char *> &stage = res.stage;
-    stage.assign(K, nullptr);
-    for (int k = 0; k < K; k++) check(cudaMallocHost(&stage[k], stage_bytes), RTCDF_ERR_NO_MEMORY);
+    // Every launch stream has one; a high-priority stream only ever uploads
+    // the digest entry of its single request, so a small one does.
+    stage.assign(NS, nullptr);
+    std::vector<size_t> stage_cap(NS, 0);
+    for (int k = 0; k < NS; k++) {
+        stage_cap[k] = k < K ? stage_bytes : (size_t)4096;
+        check(cudaMallocHost(&stage[k], stage_cap[k]), RTCDF_ERR_NO_MEMORY);
+    }
     check(cudaDeviceSynchronize(), RTCDF_ERR_CUDA);
 
     std::vector<size_t> slot_off(count, 0), slot_bytes(count, 0);
@@ -356,7 +362,7 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
             const size_t dig_b = dg.size() * sizeof(DigestSeg);
             const size_t tab_b = (dig_at + dig_b + 255) / 256 * 256;
             const size_t wsb = hp.ws_words * 4;
-            if (tab_b > stage_bytes) { err = RTCDF_ERR_NO_MEMORY; break; }
+            if (tab_b > stage_cap[k]) { err = RTCDF_ERR_NO_MEMORY; break; }
             if (tab_b + wsb > 0 && !alloc.alloc(tab_b + wsb, &L.ws_off)) {
                 if (inflight.empty() && L.reqs.size() > 1) {
                     // Nothing will free memory: retry with the first request alone.
