@@ -578,6 +578,57 @@ def batched_comparison(args, stream, num_segments=4096):
     return res
 
 
+def sharded_comparison(cases, outs, n, rank, world, stream, steps):
+    """The sweep's arrays sorted across the job's ranks: rank r holds the
+    slice [r*n/N, (r+1)*n/N) of every array (the same global arrays on every
+    rank), counts it (rtcdf_hist_accumulate), takes part in one sum
+    all-reduce of the R counts per array (NCCL across GPUs), and writes the
+    same window of the sorted array (rtcdf_fill_from_counts).  With one rank
+    there is no exchange: the time shows what the split calls cost against
+    rtcdf_sort.  Every window is checked against the unsharded sort on rank 0
+    with one rank, and the counts' total against n with several."""
+    import torch
+    from paper_2609_00843_gb300 import dist as rdist, gen, rtcdf
+    lo, hi = rdist.slice_bounds(n, world, rank)
+    sh = stream.cuda_stream
+    srt = rdist.ShardedSorter(max(c["R"] for c in cases), stream=stream)
+    ins, wins = [], []
+    for c in cases:
+        x = torch.empty(hi - lo, dtype=torch.int32, device="cuda")
+        gen.keys_device(x.data_ptr(), hi - lo, MIN_SWEEP, c["R"], c["dist"], c["seed"], first=lo, stream=sh)
+        ins.append(x)
+        wins.append(torch.empty(hi - lo, dtype=torch.int32, device="cuda"))
+    stream.synchronize()
+
+    def step():
+        for i, c in enumerate(cases):
+            srt.sort(ins[i], n, MIN_SWEEP, MIN_SWEEP + c["R"], wins[i], rank=rank, world=world)
+    for _ in range(2):
+        step()
+    torch.cuda.synchronize()
+    rdist.barrier()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    rdist.barrier()
+    ms = rdist.max_over_ranks(e0.elapsed_time(e1) / steps, device="cuda")
+    rc, bits = srt.status()
+    ok = rc == rtcdf.OK and bits == 0
+    if world == 1 and outs:
+        ok = ok and all(bool(torch.equal(wins[i], outs[i])) for i in range(len(cases)))
+    del ins, wins
+    return {"note": "each array sorted across the ranks: slice counts, one sum all-reduce of R counts, "
+                    "own window of the output; 1 rank = no exchange",
+            "ranks": world, "ms_per_step": round(ms, 4),
+            "GKeys_s": round(n * len(cases) / (ms * 1e-3) / 1e9, 2),
+            "exchange": "torch.distributed all_reduce (NCCL)" if world > 1 else "none",
+            "windows_ok": bool(ok)}
+
+
 def serving_comparison(count: int, budget_gb: float = 32.0, max_large: int = 0):
     """Serving workload: a Poisson stream of sort requests, n log-uniform in
     [1e4, 1e8], R log-uniform in [2^7, 2^18], mixed shapes, 32 GB admission
@@ -662,6 +713,8 @@ def main():
     ap.add_argument("--no-batched", action="store_true", help="skip the batched-vs-looped comparison")
     ap.add_argument("--batched-segments", type=int, default=4096)
     ap.add_argument("--no-serve", action="store_true", help="skip the serving comparison")
+    ap.add_argument("--no-sharded", action="store_true",
+                    help="skip the sharded sort (each array split across the ranks)")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--e2e-steps", type=int, default=5)
     ap.add_argument("--streams", type=int, default=3,
@@ -977,6 +1030,11 @@ def main():
         line["e2e"]["frac_of_link_bound"] = round(e_val / world / bound, 4)
         del d_tmp
         del pin_in, pin_out
+
+    # Every array split across the job's ranks (one all-reduce of the counts).
+    if not args.no_sharded:
+        line["sharded"] = sharded_comparison(cases, outs if world == 1 else [], n, rank, world, stream,
+                                             max(3, min(args.steps, 10)))
 
     # On-GPU comparison: CUB DeviceRadixSort restricted to bits [0, ceil(log2 R))
     # on keys normalised to uint32 (normalise / denormalise timed apart).
