@@ -571,58 +571,36 @@ __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs 
             if (tid == 0) prof_item(a, kItemSmall, ts, 0);
         }
     };
-    if (!DEV) {
-        // The in-CTA segments come first in the grid (dispatched first;
-        // spreading them among the scan chunks was measured slower).
-        if (blockIdx.x < n_small2) {
-            // An in-CTA segment: independent of the first launch, so no wait.
-            asm volatile("griddepcontrol.launch_dependents;");
-            small_item(blockIdx.x);
-            return;
-        }
-        // The ticket and the chunk's descriptors come from plan data, not from
-        // the first launch: fetched before waiting for it.  (The ticket counter
-        // was reset by the previous run's output launch, which finished before
-        // this plan's first launch began.)
-        if (tid == 0) s_ticket = atomicAdd(&a.ctl->scan_ticket, 1u);
-        __syncthreads();
-        if (s_ticket >= n_scan) {
-            // Only with a workspace whose ticket was not zero: the chunk this
-            // ticket stood for is never published, so the output launch must
-            // not trust the run tables.
-            if (tid == 0) atomicOr(&a.ctl->status, kDevTimeout);
-            return;
-        }
-        const BatchItem it = a.items[n_first + s_ticket];
-        const BatchSeg g = a.segs[it.seg];
-        asm volatile("griddepcontrol.wait;" ::: "memory");
+    // Device-built lists: the grid is sized by their bounds; the CTAs past
+    // the lists' lengths exit at once (about half a microsecond per thousand).
+    if (DEV && blockIdx.x >= n_small2 + n_scan) return;
+    // The in-CTA segments come first in the grid (dispatched first; spreading
+    // them among the scan chunks was measured slower).
+    if (blockIdx.x < n_small2) {
+        // An in-CTA segment: independent of the first launch, so no wait.
         asm volatile("griddepcontrol.launch_dependents;");
-        const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
-        scan_chunk(a, it, g, s_warp, s_prefix, s_total, s_wait, s_buf, t0);
+        small_item(blockIdx.x);
         return;
     }
-    // Device-built lists: a fixed grid takes the in-CTA segments (grid-stride,
-    // no wait), then the chunks by ticket.  A CTA takes its next ticket only
-    // after finishing its chunk, so every chunk a lookback waits for belongs
-    // to a running CTA.
+    // The ticket and the chunk's descriptors come from plan data, not from
+    // the first launch: fetched before waiting for it.  (The ticket counter
+    // was reset by the previous run's output launch, which finished before
+    // this plan's first launch began.)
+    if (tid == 0) s_ticket = atomicAdd(&a.ctl->scan_ticket, 1u);
+    __syncthreads();
+    if (s_ticket >= n_scan) {
+        // Only with a workspace whose ticket was not zero: the chunk this
+        // ticket stood for is never published, so the output launch must not
+        // trust the run tables.
+        if (tid == 0) atomicOr(&a.ctl->status, kDevTimeout);
+        return;
+    }
+    const BatchItem it = a.items[n_first + s_ticket];
+    const BatchSeg g = a.segs[it.seg];
+    asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
-    for (uint32_t i = blockIdx.x; i < n_small2; i += gridDim.x) {
-        small_item(i);
-        __syncthreads();
-    }
-    for (;;) {
-        if (tid == 0) s_ticket = atomicAdd(&a.ctl->scan_ticket, 1u);
-        __syncthreads();
-        const uint32_t tk = s_ticket;
-        __syncthreads();
-        if (tk >= n_scan) break;
-        const BatchItem it = a.items[n_first + tk];
-        const BatchSeg g = a.segs[it.seg];
-        asm volatile("griddepcontrol.wait;" ::: "memory");
-        const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
-        scan_chunk(a, it, g, s_warp, s_prefix, s_total, s_wait, s_buf, t0);
-        __syncthreads();
-    }
+    const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
+    scan_chunk(a, it, g, s_warp, s_prefix, s_total, s_wait, s_buf, t0);
 }
 
 // Output CTAs of 512 threads: four resident per SM, so that one CTA's
@@ -738,27 +716,25 @@ __global__ void __launch_bounds__(kFillCtaThreads) seg_fill_kernel(BatchArgs a) 
     __shared__ uint32_t s_end[kSegFillRuns];
     __shared__ int32_t s_val[kSegFillRuns];
     const uint32_t tid = threadIdx.x;
-    if (!DEV) {
-        // The item and its segment are plan data: fetched before waiting for
-        // the scan launch.
-        const BatchItem it = a.items[a.n_first + a.n_scan + a.n_small2 + blockIdx.x];
-        const BatchSeg g = a.segs[it.seg];
-        asm volatile("griddepcontrol.wait;" ::: "memory");
-        const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
-        if (blockIdx.x == 0 && tid == 0) a.ctl->scan_ticket = 0;
-        fill_item(a, it, g, s_end, s_val, t0);
+    const uint32_t base = DEV ? a.dev_counts[0] + a.dev_counts[1] + a.dev_counts[2]
+                              : a.n_first + a.n_scan + a.n_small2;
+    if (DEV && blockIdx.x >= a.dev_counts[3]) {
+        // Past the device-built list (the grid is sized by its bound); the
+        // first CTA still resets the scan ticket, even for an empty list.
+        if (blockIdx.x == 0) {
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            if (tid == 0) a.ctl->scan_ticket = 0;
+        }
         return;
     }
-    const uint32_t base = a.dev_counts[0] + a.dev_counts[1] + a.dev_counts[2], n_fill = a.dev_counts[3];
+    // The item and its segment are plan data: fetched before waiting for the
+    // scan launch.
+    const BatchItem it = a.items[base + blockIdx.x];
+    const BatchSeg g = a.segs[it.seg];
     asm volatile("griddepcontrol.wait;" ::: "memory");
+    const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
     if (blockIdx.x == 0 && tid == 0) a.ctl->scan_ticket = 0;
-    for (uint32_t i = blockIdx.x; i < n_fill; i += gridDim.x) {
-        const BatchItem it = a.items[base + i];
-        const BatchSeg g = a.segs[it.seg];
-        const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
-        fill_item(a, it, g, s_end, s_val, t0);
-        __syncthreads();
-    }
+    fill_item(a, it, g, s_end, s_val, t0);
 }
 
 namespace {

@@ -12,9 +12,11 @@
 //      their exclusive prefixes -- a block-wide scan per 1024 segments;
 //   2. devplan_items_kernel (one thread per item): the list and the segment
 //      of an item index (a binary search in the prefixes), then the item.
-// The three launches then run over these lists with fixed grids whose CTAs
-// take items by ticket or by grid stride (seg_*_kernel<true>), since the list
-// lengths are known only on the device.
+// The three launches then run over these lists (seg_*_kernel<true>); their
+// lengths are known only on the device, so the first launch is a fixed grid
+// whose CTAs take items by ticket, and the scan and output launches have one
+// CTA per item of the lists' bounds, the CTAs past a list's length exiting at
+// once (about half a microsecond per thousand, measured).
 //
 // The workspace is sized from host-known bounds (segment count, total keys,
 // widest range).  Every segment owns a fixed slot for its histogram, lookback
@@ -361,11 +363,13 @@ rtcdf_status rtcdf_sort_batched_device_ws(const int32_t *in, int32_t *out, const
     a.ctl = reinterpret_cast<BatchCtl *>(ws + L.ctl);
     a.seg_ctl = reinterpret_cast<BatchSegCtl *>(ws + L.segctl);
     a.dev_counts = ws + L.hdr;  // n_first, n_scan, n_small2, n_fill
-    // Resident CTAs per launch: two first-launch CTAs, six scan CTAs and four
-    // output CTAs per SM.
+    // The first launch: two resident CTAs per SM taking items by ticket; the
+    // scan and output launches: one CTA per item of the lists' bounds.
+    if (L.scan_bound + L.small2_bound > 0x7fffffffull || L.fill_bound > 0x7fffffffull)
+        return RTCDF_ERR_INVALID_ARG;
     const uint32_t first = (uint32_t)std::min<uint64_t>(L.first_bound, 2ull * sms);
-    const uint32_t scan = (uint32_t)std::min<uint64_t>(L.scan_bound + L.small2_bound, 6ull * sms);
-    const uint32_t fill = (uint32_t)std::min<uint64_t>(L.fill_bound, 4ull * sms);
+    const uint32_t scan = (uint32_t)(L.scan_bound + L.small2_bound);
+    const uint32_t fill = (uint32_t)L.fill_bound;
     if (launch_batched_dev(a, std::max(first, 1u), std::max(scan, 1u), std::max(fill, 1u), s) != cudaSuccess)
         return RTCDF_ERR_CUDA;
     return RTCDF_OK;
