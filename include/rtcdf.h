@@ -499,7 +499,10 @@ typedef struct {
                                    device's highest stream priority (batches keep
                                    the default priority), so a large sort runs
                                    about as fast as alone while batches fill in */
-    int32_t reserved2;
+    int32_t serial_below;       /* > 0: while fewer than this many admitted
+                                   requests wait for a launch, launch only when
+                                   nothing is in flight (first come, first served
+                                   on an idle device); 0 = always overlap */
 } rtcdf_server_config;
 
 typedef struct {

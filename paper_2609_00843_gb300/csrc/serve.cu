@@ -301,6 +301,10 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
         }
         // 2. Launch pending requests on free streams.
         while (!pending.empty() && !err) {
+            // Under light load (fewer than serial_below requests waiting) one
+            // launch at a time, first come first served: each sort then runs
+            // on an otherwise idle device.  More waiting requests overlap.
+            if (cfg->serial_below > 0 && !inflight.empty() && (int64_t)pending.size() < cfg->serial_below) break;
             // A large request alone (while fewer than max_large of them run),
             // or every small pending request together.
             const int64_t head = pending.front();
