@@ -635,10 +635,11 @@ def serving_comparison(count: int, budget_gb: float = 32.0, max_large: int = 0):
     budget.  The arrival rate is rho x the throughput of sequential
     per-request calls (measured first with every request present at t=0),
     rho in {0.5, 0.9, 1.5}; each trace is served sequentially and by the
-    continuous-batching server (large requests on high-priority streams;
-    at rho = 0.5 also without).  Latency = completion - arrival; a request's
-    keys are written into its device slot by the generator at admission (data
-    arrival)."""
+    continuous-batching server.  Latency = completion - arrival; a request's
+    keys are written into its device slot by the generator (data arrival):
+    sequentially right before its sort; in the server on its launch's stream
+    right before the sort (and, at rho = 0.5, also at admission for
+    comparison)."""
     import numpy as np
     from paper_2609_00843_gb300 import gen, rtcdf
     seed = gen.derive_seed(5)
@@ -646,10 +647,17 @@ def serving_comparison(count: int, budget_gb: float = 32.0, max_large: int = 0):
     mx = mn + R
     fill = gen.fill_function_address()
 
-    def cfg(prio=1):
+    def cfg(adaptive=True):
+        # The serving policy: keys written on the launch's stream right before
+        # its sort, one large launch at a time until four large requests wait
+        # (then every stream).  adaptive=False: the previous policy (keys
+        # written at admission on separate streams, large launches on every
+        # stream), for comparison at rho = 0.5.
         return rtcdf.ServerConfig(budget_bytes=int(budget_gb * (1 << 30)), num_streams=4,
                                   max_batch=256, single_min_keys=1 << 22, fill=fill, digests=0,
-                                  max_large_inflight=max_large, large_priority=prio)
+                                  max_large_inflight=1 if adaptive else max_large,
+                                  fill_at_launch=1 if adaptive else 0,
+                                  large_queue_burst=4 if adaptive else 0)
     zero = np.zeros(count)
     r0 = rtcdf.make_requests(n, mn, mx, dist, seeds, zero)
     _, st0 = rtcdf.rtcdf_serve_sequential(cfg(), r0, count)
@@ -685,10 +693,10 @@ def serving_comparison(count: int, budget_gb: float = 32.0, max_large: int = 0):
         row["p99_ratio_sequential_vs_server"] = round(
             row["sequential"]["p99_latency_ms"] / max(1e-9, row["server"]["p99_latency_ms"]), 3)
         if rho == 0.5:
-            # the same server with large requests on default-priority streams
-            res, st = rtcdf.rtcdf_serve_trace(cfg(prio=0), reqs, count)
+            # the previous policy: keys written at admission, large launches on every stream
+            res, st = rtcdf.rtcdf_serve_trace(cfg(adaptive=False), reqs, count)
             lat = np.array([res[i].done_s - arr[i] for i in range(count)])
-            row["server_default_priority"] = {
+            row["server_admission_writes"] = {
                 "p50_latency_ms": round(float(np.percentile(lat, 50)) * 1e3, 3),
                 "p99_latency_ms": round(float(np.percentile(lat, 99)) * 1e3, 3),
                 "all_ok": all(res[i].status == 0 for i in range(count))}

@@ -499,10 +499,15 @@ typedef struct {
                                    device's highest stream priority (batches keep
                                    the default priority), so a large sort runs
                                    about as fast as alone while batches fill in */
-    int32_t serial_below;       /* > 0: while fewer than this many admitted
-                                   requests wait for a launch, launch only when
-                                   nothing is in flight (first come, first served
-                                   on an idle device); 0 = always overlap */
+    int32_t reserved2;
+    int32_t fill_at_launch;     /* nonzero: a request's keys are written by `fill`
+                                   on its launch's stream right before the sort
+                                   (as rtcdf_serve_sequential does); 0: at
+                                   admission, on separate streams, overlapping
+                                   the sorts in flight */
+    int32_t large_queue_burst;  /* > 0: max_large_inflight applies only while fewer
+                                   than this many large requests wait; with more
+                                   waiting, large launches may use every stream */
 } rtcdf_server_config;
 
 typedef struct {

@@ -251,6 +251,7 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
     int batch_cap = cfg->max_batch;
     const int max_large = cfg->max_large_inflight > 0 ? cfg->max_large_inflight : K;
     int large_inflight = 0;
+    int64_t pending_large = 0;  // admitted large requests not launched yet
     const Clock::time_point t0 = Clock::now();
 
     while (done < count && !err) {
@@ -282,7 +283,7 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
                 fs = fill_rr;
                 fill_rr = (fill_rr + 1) % K;
             }
-            if (r.n) {
+            if (r.n && !cfg->fill_at_launch) {
                 if (cfg->fill(in, r.n, 0, r.minVal, r.maxVal - r.minVal, r.dist, r.seed,
                               (rtcdf_stream_t)fill_streams[fs]) != 0) {
                     err = RTCDF_ERR_CUDA;
@@ -296,19 +297,21 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
             }
             results[next].admit_s = secs(t0);
             pending.push_back(next);
+            if (r.n >= cfg->single_min_keys) pending_large++;
             next++;
             progressed = true;
         }
         // 2. Launch pending requests on free streams.
         while (!pending.empty() && !err) {
-            // Under light load (fewer than serial_below requests waiting) one
-            // launch at a time, first come first served: each sort then runs
-            // on an otherwise idle device.  More waiting requests overlap.
-            if (cfg->serial_below > 0 && !inflight.empty() && (int64_t)pending.size() < cfg->serial_below) break;
             // A large request alone (while fewer than max_large of them run),
             // or every small pending request together.
             const int64_t head = pending.front();
-            const bool take_large = reqs[head].n >= cfg->single_min_keys && large_inflight < max_large;
+            // The limit on large launches in flight holds while the waiting
+            // large requests are fewer than large_queue_burst; a backlog
+            // lets them use every stream.
+            const int large_cap =
+                (cfg->large_queue_burst > 0 && pending_large >= cfg->large_queue_burst) ? K : max_large;
+            const bool take_large = reqs[head].n >= cfg->single_min_keys && large_inflight < large_cap;
             const int k_lo = (prio && take_large) ? K : 0, k_hi = prio ? k_lo + K : K;
             int k = -1;
             for (int j = k_lo; j < k_hi; j++)
@@ -319,6 +322,7 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
             L.stream = k;
             if (take_large) {
                 pending.pop_front();
+                pending_large--;
                 L.reqs.push_back(head);
                 L.large = true;
             } else {
@@ -334,6 +338,20 @@ rtcdf_status rtcdf_serve_trace(const rtcdf_server_config *cfg, const rtcdf_reque
             }
             for (int64_t i : L.reqs)  // inputs written before the sort reads them
                 if (req_ev[i]) cudaStreamWaitEvent(s, req_ev[i], 0);
+            if (cfg->fill_at_launch) {
+                // The keys are written on the launch's own stream right before
+                // its sort, as a one-at-a-time server writes them.
+                for (int64_t i : L.reqs) {
+                    if (!reqs[i].n) continue;
+                    int32_t *in = reinterpret_cast<int32_t *>(slab + slot_off[i]);
+                    if (cfg->fill(in, reqs[i].n, 0, reqs[i].minVal, reqs[i].maxVal - reqs[i].minVal, reqs[i].dist,
+                                  reqs[i].seed, (rtcdf_stream_t)s) != 0) {
+                        err = RTCDF_ERR_CUDA;
+                        break;
+                    }
+                }
+                if (err) break;
+            }
             const double launch_t = secs(t0);
             // A lone request (large, or small with nothing to batch it with --
             // light load) goes through the single-array pipeline, which needs

@@ -79,7 +79,8 @@ class ServerConfig(ctypes.Structure):
                 ("max_batch", ctypes.c_int32), ("single_min_keys", ctypes.c_uint64),
                 ("fill", ctypes.c_void_p), ("digests", ctypes.c_int32),
                 ("max_large_inflight", ctypes.c_int32), ("outputs", ctypes.c_void_p),
-                ("large_priority", ctypes.c_int32), ("serial_below", ctypes.c_int32)]
+                ("large_priority", ctypes.c_int32), ("reserved2", ctypes.c_int32),
+                ("fill_at_launch", ctypes.c_int32), ("large_queue_burst", ctypes.c_int32)]
 
 
 class Request(ctypes.Structure):

@@ -126,6 +126,26 @@ def test_large_requests_on_high_priority_streams_match():
     assert_outputs_match_oracle(bufs, n, mn, R, dist, seeds)
 
 
+def test_load_adaptive_policy_results_match():
+    """Keys written on the launch stream right before the sort, one large
+    launch at a time until a backlog of large requests forms: every result
+    equals the one served alone, and sampled outputs equal the oracle."""
+    count = 400
+    n, mn, R, dist, seeds, arr = trace(count, gen.derive_seed(56), n_hi=8e6, rate=40000.0)
+    reqs = rtcdf.make_requests(n, mn, mn + R, dist, seeds, arr)
+    chosen = list(np.nonzero(n <= 200_000)[0][:30]) + list(np.nonzero(n >= (1 << 21))[0][:8])
+    bufs, ptrs = output_buffers(n, chosen)
+    cfg = config(4 << 30, max_large=1)
+    cfg.fill_at_launch, cfg.large_queue_burst = 1, 3
+    cfg.outputs = ctypes.cast(ptrs, ctypes.c_void_p)
+    mix, st = rtcdf.rtcdf_serve_trace(cfg, reqs, count)
+    alone, _ = rtcdf.rtcdf_serve_sequential(config(4 << 30), reqs, count)
+    assert st.launches_single > 0 and st.launches_batched > 0
+    for i in range(count):
+        assert mix[i].status == 0 and mix[i].digest == alone[i].digest, i
+    assert_outputs_match_oracle(bufs, n, mn, R, dist, seeds)
+
+
 def test_small_budget_admission_waits_for_memory():
     count = 120
     n, mn, R, dist, seeds, arr = trace(count, gen.derive_seed(52), n_hi=4e6, rate=1e6)
