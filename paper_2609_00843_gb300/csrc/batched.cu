@@ -384,14 +384,14 @@ __global__ void __launch_bounds__(kSegThreads, 2) seg_first_kernel(BatchArgs a) 
         return;
     }
     __shared__ uint32_t s_idx;
-    const uint32_t n_first = a.dev_counts[0];
+    const uint32_t n_hist = a.dev_counts[4], n_small1 = a.dev_counts[5];
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(&a.ctl->first_ticket, 1u);
         __syncthreads();
-        const uint32_t idx = s_idx;
+        const uint32_t k = s_idx;
         __syncthreads();  // every thread has read s_idx (and the previous item's shared memory is free)
-        if (idx >= n_first) break;
-        first_item(a, idx, sm);
+        if (k >= n_hist + n_small1) break;
+        first_item(a, (uint32_t)devplan_first_pos(k, n_hist, n_small1, a.first_split), sm);
     }
 }
 
@@ -558,12 +558,14 @@ __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs 
     __shared__ unsigned long long s_wait;
     __shared__ uint32_t s_buf[kScanSmemWords];
     const int tid = threadIdx.x;
-    const uint32_t n_first = DEV ? a.dev_counts[0] : a.n_first;
+    // List lengths (device-built lists: from the device) and positions (the
+    // scan chunks at a.n_first, the in-CTA segments at a.n_first + a.n_scan:
+    // the host plan's lengths, or the device lists' bounds).
     const uint32_t n_scan = DEV ? a.dev_counts[1] : a.n_scan;
     const uint32_t n_small2 = DEV ? a.dev_counts[2] : a.n_small2;
     auto small_item = [&](uint32_t i) {
         const unsigned long long ts = (a.prof && tid == 0) ? global_ns() : 0ull;
-        const BatchItem it = a.items[n_first + n_scan + i];
+        const BatchItem it = a.items[a.n_first + a.n_scan + i];
         const BatchSeg g = a.segs[it.seg];
         do_small(a, g, s_buf, kScanSmemWords - 64, s_buf + kScanSmemWords - 64);
         if (a.prof) {
@@ -595,7 +597,7 @@ __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs 
         if (tid == 0) atomicOr(&a.ctl->status, kDevTimeout);
         return;
     }
-    const BatchItem it = a.items[n_first + s_ticket];
+    const BatchItem it = a.items[a.n_first + s_ticket];
     const BatchSeg g = a.segs[it.seg];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     asm volatile("griddepcontrol.launch_dependents;");
@@ -716,8 +718,16 @@ __global__ void __launch_bounds__(kFillCtaThreads) seg_fill_kernel(BatchArgs a) 
     __shared__ uint32_t s_end[kSegFillRuns];
     __shared__ int32_t s_val[kSegFillRuns];
     const uint32_t tid = threadIdx.x;
-    const uint32_t base = DEV ? a.dev_counts[0] + a.dev_counts[1] + a.dev_counts[2]
-                              : a.n_first + a.n_scan + a.n_small2;
+    // The output items sit after the other lists (their lengths for a host
+    // plan, their bounds for device-built lists).
+    const uint32_t base = a.n_first + a.n_scan + a.n_small2;
+    if (DEV && blockIdx.x == 0) {
+        // The first CTA leaves the device planner's ticket and lookback
+        // records zeroed for the next run (the planner finished before this
+        // run's first launch began).
+        for (uint32_t i = tid; i < a.plan_look_words; i += blockDim.x) a.plan_look[i] = 0;
+        if (tid == 0) a.ctl->plan_ticket = 0;
+    }
     if (DEV && blockIdx.x >= a.dev_counts[3]) {
         // Past the device-built list (the grid is sized by its bound); the
         // first CTA still resets the scan ticket, even for an empty list.

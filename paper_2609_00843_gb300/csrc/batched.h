@@ -66,7 +66,8 @@ struct BatchCtl {
     uint32_t scan_ticket;   // dynamic order of the scan CTAs (reset by the output launch)
     uint32_t first_ticket;  // device-built lists: items of the first launch taken so far
                             // (reset by the planner before the first launch)
-    uint32_t pad[61];
+    uint32_t plan_ticket;   // device planner: CTAs in start order (reset by the output launch)
+    uint32_t pad[60];
 };
 
 struct BatchArgs {
@@ -84,8 +85,17 @@ struct BatchArgs {
     // per item kind busy ns, items, first start, last end, dependency-wait ns.
     unsigned long long *prof = nullptr;
     // Lists built on the device: their lengths (n_first, n_scan, n_small2,
-    // n_fill) in device memory; null for a host-built plan.
+    // n_fill, n_hist, n_small1) in device memory; null for a host-built plan.
+    // The lists then sit at fixed offsets, their bounds: the first launch's
+    // histogram items at 0 and in-CTA segments at first_split, the scan
+    // chunks at n_first, the scan launch's in-CTA segments at n_first +
+    // n_scan, the output items at n_first + n_scan + n_small2 (the n_* of
+    // this struct holding the bounds).
     const uint32_t *dev_counts = nullptr;
+    uint32_t first_split = 0;
+    // The device planner's lookback records, zeroed by the output launch.
+    uint32_t *plan_look = nullptr;
+    uint32_t plan_look_words = 0;
 };
 
 cudaError_t launch_batched(const BatchArgs &a, cudaStream_t s);
@@ -157,10 +167,35 @@ enum : uint32_t { kListHist = 0, kListSmall1 = 1, kListScan = 2, kListSmall2 = 3
 // for max_R, so H and the state, zero between runs, stay where the next run
 // of any layout expects them.
 struct DevLayout {
-    size_t ctl, hdr, segctl, segs, pfx, items, start, slots, slot_words, total_words;
+    size_t ctl, hdr, segctl, segs, look, items, start, slots, slot_words, total_words;
     size_t slot_state, slot_run_end, slot_run_val;  // offsets inside a slot
-    uint64_t first_bound, scan_bound, small2_bound, fill_bound, item_bound;
+    uint64_t hist_bound, first_bound, scan_bound, small2_bound, fill_bound, item_bound;
+    uint32_t look_blocks;  // planner CTAs (1024 segments each)
 };
+
+// Position in the items array of list `list`'s element k (its base is the
+// bound-sum of the lists before it).
+__host__ __device__ inline uint64_t devplan_pos(const DevLayout &L, uint32_t list, uint64_t k) {
+    switch (list) {
+        case kListHist: return k;
+        case kListSmall1: return L.hist_bound + k;
+        case kListScan: return L.first_bound + k;
+        case kListSmall2: return L.first_bound + L.scan_bound + k;
+        default: return L.first_bound + L.scan_bound + L.small2_bound + k;
+    }
+}
+
+// The first launch's k-th ticket (k < nh + ns): the in-CTA segments spread
+// evenly among the histogram items -- in-CTA segment j at ticket
+// floor(j * (nh + ns) / ns) -- so that reads (histograms) and writes
+// (in-CTA sorts) overlap throughout.  Returns the items-array position.
+__host__ __device__ inline uint64_t devplan_first_pos(uint64_t k, uint64_t nh, uint64_t ns, uint64_t split) {
+    const uint64_t T = nh + ns;
+    if (ns == 0) return k;
+    const uint64_t j = (k * ns + T - 1) / T;  // in-CTA slots before ticket k: ceil(k * ns / T)
+    if (j < ns && j * T / ns == k) return split + j;
+    return k - j;
+}
 // 0, or RTCDF_ERR_RANGE / RTCDF_ERR_INVALID_ARG for bounds out of range.
 int devplan_layout(const DevBounds &b, const BatchTuning &t, DevLayout *L);
 

@@ -5,18 +5,20 @@
 // layouts -- without a round trip through the host.
 //
 // Each segment is still sorted by Algorithms 4-7 (Section 3); the plan is the
-// same three work lists as the host planner's (batch_api.cu), built by two
-// kernels:
-//   1. devplan_segments_kernel (one CTA): every segment's descriptor and its
-//      item counts per list (the rules of devplan_segment, batched.h), and
-//      their exclusive prefixes -- a block-wide scan per 1024 segments;
-//   2. devplan_items_kernel (one thread per item): the list and the segment
-//      of an item index (a binary search in the prefixes), then the item.
+// same three work lists as the host planner's (batch_api.cu), built by one
+// kernel: each CTA classifies 1024 segments (the rules of devplan_segment,
+// batched.h), scans their item counts per list, gets the counts of the
+// segments before its own from the CTAs before it (a decoupled lookback over
+// CTAs taken in start order, every wait bounded), and writes its segments'
+// descriptors and items.  The lists sit at fixed offsets (the bounds of the
+// lists before them), so no CTA needs the totals to place its items; the
+// last CTA writes the lists' lengths.
 // The three launches then run over these lists (seg_*_kernel<true>); their
 // lengths are known only on the device, so the first launch is a fixed grid
-// whose CTAs take items by ticket, and the scan and output launches have one
-// CTA per item of the lists' bounds, the CTAs past a list's length exiting at
-// once (about half a microsecond per thousand, measured).
+// whose CTAs take items by ticket (the in-CTA segments spread evenly among the
+// histogram items), and the scan and output launches have one CTA per item of
+// the lists' bounds, the CTAs past a list's length exiting at once (about
+// half a microsecond per thousand, measured).
 //
 // The workspace is sized from host-known bounds (segment count, total keys,
 // widest range).  Every segment owns a fixed slot for its histogram, lookback
@@ -47,117 +49,164 @@ struct DevPlanArgs {
     DevLayout L;
 };
 
-__global__ void __launch_bounds__(1024) devplan_segments_kernel(DevPlanArgs p) {
+// Lookback record of a planner CTA: state (0 none, 1 its own counts
+// published, 2 the counts of every segment up to its last published), its own
+// counts and the inclusive ones -- per list, and the number of segments that
+// broke the bounds.  Each array is written once, before the state that
+// announces it, so a reader never sees one being overwritten.
+struct DevLook {
+    uint32_t flag;
+    uint32_t own[6];
+    uint32_t incl[6];
+    uint32_t pad[3];
+};
+static_assert(sizeof(DevLook) == 64, "lookback record is 16 words");
+
+__device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
+    uint32_t v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+__global__ void __launch_bounds__(1024) devplan_kernel(DevPlanArgs p) {
+    __shared__ uint32_t s_ex[5][1024];  // exclusive prefix of each list's counts within the CTA
     __shared__ uint32_t s_warp[5][32];
-    __shared__ uint32_t s_tot[5], s_run[5];
+    __shared__ uint32_t s_tot[6], s_base[6];
+    __shared__ uint32_t s_blk;
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     BatchCtl *ctl = reinterpret_cast<BatchCtl *>(p.ws + p.L.ctl);
     BatchSeg *segs = reinterpret_cast<BatchSeg *>(p.ws + p.L.segs);
-    DevPfx *pfx = reinterpret_cast<DevPfx *>(p.ws + p.L.pfx);
+    BatchItem *items = reinterpret_cast<BatchItem *>(p.ws + p.L.items);
+    DevLook *look = reinterpret_cast<DevLook *>(p.ws + p.L.look);
+    // CTAs in start order, so a CTA only waits for CTAs already running.
     if (tid == 0) {
+        s_blk = atomicAdd(&ctl->plan_ticket, 1u);
         s_bad = 0;
-        ctl->first_ticket = 0;  // the previous run has finished (stream order)
     }
-    if (tid < 5) s_run[tid] = 0;
     __syncthreads();
-    const uint32_t S = p.b.S;
-    for (uint32_t c0 = 0; c0 < S; c0 += 1024) {
-        const uint32_t s = c0 + tid;
-        DevSegCount c{0, 0, 0, 0, 0};
-        BatchSeg g{};
-        if (s < S && !devplan_segment(p.offs[s], p.offs[s + 1], p.mn[s], p.mx[s], p.b, p.t, &g, &c)) s_bad = 1;
-        const uint32_t v[5] = {c.hist, c.small1, c.scan, c.small2, c.fill};
-        uint32_t inc[5];
-#pragma unroll
-        for (int f = 0; f < 5; f++) {
-            inc[f] = v[f];
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, inc[f], d);
-                if (lane >= d) inc[f] += y;
-            }
-            if (lane == 31) s_warp[f][warp] = inc[f];
-        }
-        __syncthreads();
-        if (warp < 5) {
-            const uint32_t x = s_warp[warp][lane];
-            uint32_t xi = x;
-#pragma unroll
-            for (int d = 1; d < 32; d <<= 1) {
-                const uint32_t y = __shfl_up_sync(0xffffffffu, xi, d);
-                if (lane >= d) xi += y;
-            }
-            s_warp[warp][lane] = xi - x;  // exclusive prefix of each warp
-            if (lane == 31) s_tot[warp] = xi;
-        }
-        __syncthreads();
-        if (s < S) {
-            uint32_t q[5];
-#pragma unroll
-            for (int f = 0; f < 5; f++) q[f] = s_run[f] + s_warp[f][warp] + inc[f] - v[f];
-            pfx[s] = DevPfx{q[0], q[1], q[2], q[3], q[4], {0, 0, 0}};
-            if (g.m > 0) {
-                const size_t slot = p.L.slots + (size_t)s * p.L.slot_words;
-                g.hist_off = slot;
-                g.state_off = slot + p.L.slot_state;
-                g.run_end_off = slot + p.L.slot_run_end;
-                g.run_val_off = slot + p.L.slot_run_val;
-                g.start_run_off = p.L.start + q[kListFill];
-            }
-            segs[s] = g;
-        }
-        __syncthreads();
-        if (tid < 5) s_run[tid] += s_tot[tid];
-        __syncthreads();
+    const uint32_t blk = s_blk;
+    if (blk >= p.L.look_blocks) {
+        // Only with a workspace whose ticket was not zero: the lists of this
+        // run are incomplete, so the output launch must not trust them.
+        if (tid == 0) atomicOr(&ctl->status, kDevTimeout);
+        return;
     }
+    if (blk == 0 && tid == 0) ctl->first_ticket = 0;  // the previous run has finished (stream order)
+    const uint32_t S = p.b.S, s = blk * 1024 + tid;
+    DevSegCount c{0, 0, 0, 0, 0};
+    BatchSeg g{};
+    if (s < S && !devplan_segment(p.offs[s], p.offs[s + 1], p.mn[s], p.mx[s], p.b, p.t, &g, &c)) s_bad = 1;
+    const uint32_t v[5] = {c.hist, c.small1, c.scan, c.small2, c.fill};
+    uint32_t inc[5];
+#pragma unroll
+    for (int f = 0; f < 5; f++) {
+        inc[f] = v[f];
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, inc[f], d);
+            if (lane >= d) inc[f] += y;
+        }
+        if (lane == 31) s_warp[f][warp] = inc[f];
+    }
+    __syncthreads();
+    if (warp < 5) {
+        const uint32_t x = s_warp[warp][lane];
+        uint32_t xi = x;
+#pragma unroll
+        for (int d = 1; d < 32; d <<= 1) {
+            const uint32_t y = __shfl_up_sync(0xffffffffu, xi, d);
+            if (lane >= d) xi += y;
+        }
+        s_warp[warp][lane] = xi - x;
+        if (lane == 31) s_tot[warp] = xi;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int f = 0; f < 5; f++) s_ex[f][tid] = s_warp[f][warp] + inc[f] - v[f];
     if (tid == 0) {
-        pfx[S] = DevPfx{s_run[0], s_run[1], s_run[2], s_run[3], s_run[4], {0, 0, 0}};
+        s_tot[5] = s_bad ? 1u : 0u;
+        // Counts of the segments before this CTA's: publish its own, then
+        // add the predecessors' until one has published its inclusive counts.
+        uint32_t pre[6] = {0, 0, 0, 0, 0, 0};
+        if (blk > 0) {
+            for (int i = 0; i < 6; i++) look[blk].own[i] = s_tot[i];
+            st_release_u32(&look[blk].flag, 1u);
+            int64_t j = (int64_t)blk - 1;
+            uint32_t spins = 0;
+            while (j >= 0) {
+                uint32_t f = ld_acquire_u32(&look[j].flag);
+                while (f == 0) {
+                    if (++spins > kMaxSpin) break;
+                    __nanosleep(64);
+                    f = ld_acquire_u32(&look[j].flag);
+                }
+                if (f == 0) {  // the wait ran out: mark the plan unusable
+                    atomicOr(&ctl->status, kDevTimeout);
+                    pre[5] += 1;
+                    break;
+                }
+                const uint32_t *src = f == 2 ? look[j].incl : look[j].own;
+                for (int i = 0; i < 6; i++) pre[i] += src[i];
+                if (f == 2) break;
+                j--;
+            }
+        }
+        for (int i = 0; i < 6; i++) {
+            s_base[i] = pre[i];
+            look[blk].incl[i] = pre[i] + s_tot[i];
+        }
+        st_release_u32(&look[blk].flag, 2u);
+    }
+    __syncthreads();
+    if (s < S) {
+        if (g.m > 0) {
+            const size_t slot = p.L.slots + (size_t)s * p.L.slot_words;
+            g.hist_off = slot;
+            g.state_off = slot + p.L.slot_state;
+            g.run_end_off = slot + p.L.slot_run_end;
+            g.run_val_off = slot + p.L.slot_run_val;
+            g.start_run_off = p.L.start + s_base[kListFill] + s_ex[kListFill][tid];
+        }
+        segs[s] = g;
+    }
+    __syncthreads();  // the descriptors are read back below, by other threads of the CTA
+    // This CTA's items of every list, all threads together: the owner of the
+    // k-th is the last segment whose prefix is at most k.
+    const uint32_t nseg = min(1024u, S - blk * 1024);
+    for (uint32_t f = 0; f < 5; f++) {
+        for (uint32_t k = tid; k < s_tot[f]; k += 1024) {
+            uint32_t lo = 0, hi = nseg;
+            while (hi - lo > 1) {
+                const uint32_t mid = (lo + hi) >> 1;
+                if (s_ex[f][mid] <= k) lo = mid;
+                else hi = mid;
+            }
+            const uint32_t sg = blk * 1024 + lo;
+            items[devplan_pos(p.L, f, (uint64_t)s_base[f] + k)] = devplan_item(f, sg, k - s_ex[f][lo], segs[sg], p.t);
+        }
+    }
+    if (blk == p.L.look_blocks - 1 && tid == 0) {
+        uint32_t t[6];
+        for (int i = 0; i < 6; i++) t[i] = s_base[i] + s_tot[i];
         DevPlanHdr *h = reinterpret_cast<DevPlanHdr *>(p.ws + p.L.hdr);
-        const uint64_t nf = (uint64_t)s_run[kListHist] + s_run[kListSmall1];
+        const uint64_t nf = (uint64_t)t[kListHist] + t[kListSmall1];
         // The bounds hold by construction; checked anyway, so that a list
         // never outgrows its region.
-        const bool bad = s_bad || nf > p.L.first_bound || s_run[kListScan] > p.L.scan_bound ||
-                         s_run[kListSmall2] > p.L.small2_bound || s_run[kListFill] > p.L.fill_bound;
-        h->n_hist = bad ? 0 : s_run[kListHist];
-        h->n_small1 = bad ? 0 : s_run[kListSmall1];
+        const bool bad = t[5] > 0 || t[kListHist] > p.L.hist_bound || t[kListSmall1] > p.L.first_bound - p.L.hist_bound ||
+                         t[kListScan] > p.L.scan_bound || t[kListSmall2] > p.L.small2_bound ||
+                         t[kListFill] > p.L.fill_bound;
+        h->n_hist = bad ? 0 : t[kListHist];
+        h->n_small1 = bad ? 0 : t[kListSmall1];
         h->n_first = bad ? 0 : (uint32_t)nf;
-        h->n_scan = bad ? 0 : s_run[kListScan];
-        h->n_small2 = bad ? 0 : s_run[kListSmall2];
-        h->n_fill = bad ? 0 : s_run[kListFill];
+        h->n_scan = bad ? 0 : t[kListScan];
+        h->n_small2 = bad ? 0 : t[kListSmall2];
+        h->n_fill = bad ? 0 : t[kListFill];
         if (bad) atomicOr(&ctl->status, kDevBadSegment);
     }
-}
-
-__global__ void __launch_bounds__(256) devplan_items_kernel(DevPlanArgs p) {
-    const uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x;
-    const DevPlanHdr *h = reinterpret_cast<const DevPlanHdr *>(p.ws + p.L.hdr);
-    const uint32_t nh = h->n_hist, nf = h->n_first, ns = h->n_scan, n2 = h->n_small2, nl = h->n_fill;
-    if (i >= (uint64_t)nf + ns + n2 + nl) return;
-    uint32_t list, k;
-    if (i < nh) {
-        list = kListHist, k = (uint32_t)i;
-    } else if (i < nf) {
-        list = kListSmall1, k = (uint32_t)(i - nh);
-    } else if (i < (uint64_t)nf + ns) {
-        list = kListScan, k = (uint32_t)(i - nf);
-    } else if (i < (uint64_t)nf + ns + n2) {
-        list = kListSmall2, k = (uint32_t)(i - nf - ns);
-    } else {
-        list = kListFill, k = (uint32_t)(i - nf - ns - n2);
-    }
-    // The segment whose items of this list include the k-th: the last s with
-    // prefix(s) <= k (prefix(0) = 0 <= k < prefix(S)).
-    const DevPfx *pfx = reinterpret_cast<const DevPfx *>(p.ws + p.L.pfx);
-    uint32_t lo = 0, hi = p.b.S;
-    while (hi - lo > 1) {
-        const uint32_t mid = lo + (hi - lo) / 2;
-        if (devplan_field(pfx[mid], list) <= k) lo = mid;
-        else hi = mid;
-    }
-    const BatchSeg *segs = reinterpret_cast<const BatchSeg *>(p.ws + p.L.segs);
-    BatchItem *items = reinterpret_cast<BatchItem *>(p.ws + p.L.items);
-    items[i] = devplan_item(list, lo, k - devplan_field(pfx[lo], list), segs[lo], p.t);
 }
 
 // Library-owned workspaces of rtcdf_sort_batched, per (device, stream).
@@ -213,7 +262,8 @@ int devplan_layout(const DevBounds &b, const BatchTuning &t, DevLayout *L) {
     const uint64_t S = b.S, N = b.max_total_keys;
     const uint64_t cpr = (b.max_R + kBatchScanChunk - 1) / kBatchScanChunk;  // scan chunks per segment
     const uint64_t m_max = (b.max_R + kBatchTileMax - 1) / kBatchTileMax;
-    L->first_bound = (N / t.hist_chunk + S) * m_max + S;
+    L->hist_bound = (N / t.hist_chunk + S) * m_max;
+    L->first_bound = L->hist_bound + S;
     L->scan_bound = S * cpr;
     L->small2_bound = S;
     L->fill_bound = N / t.fill_chunk + S;
@@ -223,7 +273,8 @@ int devplan_layout(const DevBounds &b, const BatchTuning &t, DevLayout *L) {
     L->hdr = w;      w += 64;
     L->segctl = w;   w += align64(S * sizeof(BatchSegCtl) / 4);
     L->segs = w;     w += align64(S * sizeof(BatchSeg) / 4);
-    L->pfx = w;      w += align64((S + 1) * sizeof(DevPfx) / 4);
+    L->look_blocks = (uint32_t)((S + 1023) / 1024);
+    L->look = w;     w += align64((uint64_t)L->look_blocks * 16);
     L->items = w;    w += align64(L->item_bound * sizeof(BatchItem) / 4);
     L->start = w;    w += align64(L->fill_bound);
     L->slots = w;
@@ -268,16 +319,18 @@ int devplan_host(const int64_t *offs, const int64_t *mn, const int64_t *mx, cons
     hdr->n_scan = run[2];
     hdr->n_small2 = run[3];
     hdr->n_fill = run[4];
-    if (hdr->n_first > L.first_bound || hdr->n_scan > L.scan_bound || hdr->n_small2 > L.small2_bound ||
-        hdr->n_fill > L.fill_bound)
+    if (hdr->n_hist > L.hist_bound || hdr->n_small1 > L.first_bound - L.hist_bound || hdr->n_scan > L.scan_bound ||
+        hdr->n_small2 > L.small2_bound || hdr->n_fill > L.fill_bound)
         return RTCDF_ERR_INVALID_ARG;
-    // The items in the order the items kernel writes them: [hist | small1 |
-    // scan | small2 | fill], each list in segment order.
+    // The items at the positions the planner writes them: each list in
+    // segment order from its own base (devplan_pos); unused positions stay
+    // zero here.
+    items->assign(L.item_bound, BatchItem{});
     const uint32_t lists[5] = {kListHist, kListSmall1, kListScan, kListSmall2, kListFill};
     for (uint32_t list : lists)
         for (uint32_t s = 0; s < S; s++)
             for (uint32_t k = devplan_field((*pfx)[s], list); k < devplan_field((*pfx)[s + 1], list); k++)
-                items->push_back(devplan_item(list, s, k - devplan_field((*pfx)[s], list), (*segs)[s], t));
+                (*items)[devplan_pos(L, list, k)] = devplan_item(list, s, k - devplan_field((*pfx)[s], list), (*segs)[s], t);
     return 0;
 }
 
@@ -343,11 +396,7 @@ rtcdf_status rtcdf_sort_batched_device_ws(const int32_t *in, int32_t *out, const
     p.t = tun;
     p.ws = ws;
     p.L = L;
-    devplan_segments_kernel<<<1, 1024, 0, s>>>(p);
-    if (cudaGetLastError() != cudaSuccess) return RTCDF_ERR_CUDA;
-    const uint64_t blocks = (L.item_bound + 255) / 256;
-    if (blocks > 0x7fffffffull) return RTCDF_ERR_INVALID_ARG;
-    devplan_items_kernel<<<(unsigned)blocks, 256, 0, s>>>(p);
+    devplan_kernel<<<L.look_blocks, 1024, 0, s>>>(p);
     if (cudaGetLastError() != cudaSuccess) return RTCDF_ERR_CUDA;
     BatchArgs a;
     a.in = in;
@@ -362,7 +411,10 @@ rtcdf_status rtcdf_sort_batched_device_ws(const int32_t *in, int32_t *out, const
     a.ws_u32 = ws;
     a.ctl = reinterpret_cast<BatchCtl *>(ws + L.ctl);
     a.seg_ctl = reinterpret_cast<BatchSegCtl *>(ws + L.segctl);
-    a.dev_counts = ws + L.hdr;  // n_first, n_scan, n_small2, n_fill
+    a.dev_counts = ws + L.hdr;  // n_first, n_scan, n_small2, n_fill, n_hist, n_small1
+    a.first_split = (uint32_t)L.hist_bound;
+    a.plan_look = ws + L.look;
+    a.plan_look_words = L.look_blocks * 16;
     // The first launch: two resident CTAs per SM taking items by ticket; the
     // scan and output launches: one CTA per item of the lists' bounds.
     if (L.scan_bound + L.small2_bound > 0x7fffffffull || L.fill_bound > 0x7fffffffull)

@@ -7,16 +7,19 @@
 // disjoint; the output launch issues its items by non-increasing estimated
 // cost (length x (1/4 + min(R, n) / n): vectors plus the runs crossed when
 // every value is present).  The same shapes go through the host emulation of
-// the device planner (devplan_host: the rules the planner kernels apply): its
-// lists hold the right kinds in the right order, every segment's scan chunks
+// the device planner (devplan_host: the rules the planner kernel applies): its
+// lists sit at their fixed bases and hold the right kinds in the right order,
+// the positions past a list's length stay unused, every segment's scan chunks
 // ascend, the items cover every segment's keys and positions exactly once, the
-// list lengths stay within the bounds the workspace was sized for, and every
-// segment's regions lie inside its own slot.
+// list lengths stay within the bounds the workspace was sized for, the first
+// launch's tickets map one-to-one onto its two lists with the in-CTA segments
+// evenly spread, and every segment's regions lie inside its own slot.
 // Usage: planner_check <seed> <segments>; prints "OK" or the first violation.
 // planner_check --emit <file> reads bounds and metadata ("S N maxR", then S+1
-// offsets, S minVal, S maxVal) and prints the layout, the list lengths, the
-// descriptors and the items of the emulated device plan (compared with the
-// GPU planner's workspace by a GPU test).
+// offsets, S minVal, S maxVal) and prints the layout, the lists' bounds and
+// lengths, the descriptors and the items array (every position, unused ones
+// zero) of the emulated device plan (compared with the GPU planner's
+// workspace by a GPU test).
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -163,41 +166,75 @@ static int check_dev(const std::vector<SegSpec> &spec, const BatchTuning &tun, u
     if (any_bad) return rc ? 0 : fail("dev plan accepted a range above max_R", 0, 0);
     if (rc) return fail("dev plan rejected", rc, 0);
     if (hdr.n_first != hdr.n_hist + hdr.n_small1) return fail("dev first list", hdr.n_first, hdr.n_hist);
-    const size_t total = (size_t)hdr.n_first + hdr.n_scan + hdr.n_small2 + hdr.n_fill;
-    if (items.size() != total) return fail("dev item count", (long)items.size(), (long)total);
-    if (hdr.n_first > L.first_bound || hdr.n_scan > L.scan_bound || hdr.n_small2 > L.small2_bound ||
-        hdr.n_fill > L.fill_bound)
+    if (items.size() != L.item_bound) return fail("dev items array", (long)items.size(), (long)L.item_bound);
+    if (L.first_bound != L.hist_bound + L.small2_bound) return fail("dev first bound", 0, 0);
+    if (hdr.n_hist > L.hist_bound || hdr.n_small1 > L.first_bound - L.hist_bound || hdr.n_scan > L.scan_bound ||
+        hdr.n_small2 > L.small2_bound || hdr.n_fill > L.fill_bound)
         return fail("dev bounds", hdr.n_first, hdr.n_scan);
+    // Each list sits at its fixed base (the bounds of the lists before it);
+    // the positions past a list's length stay unused.
+    const uint64_t list_base[5] = {0, L.hist_bound, L.first_bound, L.first_bound + L.scan_bound,
+                                   L.first_bound + L.scan_bound + L.small2_bound};
+    const uint64_t list_bound[5] = {L.hist_bound, L.first_bound - L.hist_bound, L.scan_bound, L.small2_bound,
+                                    L.fill_bound};
+    const uint32_t list_len[5] = {hdr.n_hist, hdr.n_small1, hdr.n_scan, hdr.n_small2, hdr.n_fill};
+    const uint32_t list_kind[5] = {kItemHist, kItemSmall, kItemScan, kItemSmall, kItemFill};
+    for (uint32_t f = 0; f < 5; f++)
+        if (devplan_pos(L, f, 0) != list_base[f]) return fail("dev list base", f, (long)devplan_pos(L, f, 0));
     std::vector<uint32_t> small_seen(S, 0), next_chunk(S, 0), next_fill(S, 0);
     std::vector<std::vector<std::pair<uint64_t, uint64_t>>> hist_rng(S);
-    for (size_t q = 0; q < items.size(); q++) {
-        const BatchItem &it = items[q];
-        if (it.seg >= S) return fail("dev segment index", (long)q, it.seg);
-        const BatchSeg &g = segs[it.seg];
-        const size_t e0 = hdr.n_hist, e1 = hdr.n_first, e2 = e1 + hdr.n_scan, e3 = e2 + hdr.n_small2;
-        const uint32_t want = q < e0 ? kItemHist : q < e1 ? kItemSmall : q < e2 ? kItemScan : q < e3 ? kItemSmall
-                                                                                                 : kItemFill;
-        if (it.kind != want) return fail("dev item kind", (long)q, it.kind);
-        switch (it.kind) {
-            case kItemHist:
-                if (it.tile >= g.m) return fail("dev tile index", (long)q, it.tile);
-                hist_rng[it.seg].push_back({it.a * 1024 + it.tile, it.b});
-                break;
-            case kItemSmall:
-                if ((q >= e2) != (g.R <= tun.small_scan_max_R)) return fail("dev small list by range", (long)q, g.R);
-                small_seen[it.seg]++;
-                break;
-            case kItemScan:
-                if (it.a != next_chunk[it.seg]) return fail("dev scan chunk order", (long)q, (long)it.a);
-                next_chunk[it.seg]++;
-                break;
-            case kItemFill:
-                if (it.aux != next_fill[it.seg] || it.a != (uint64_t)it.aux * g.fill_chunk ||
-                    it.b != std::min<uint64_t>(g.n, (uint64_t)(it.aux + 1) * g.fill_chunk))
-                    return fail("dev fill item", (long)q, it.aux);
-                next_fill[it.seg]++;
-                break;
+    for (uint32_t f = 0; f < 5; f++) {
+        for (uint64_t k = list_len[f]; k < list_bound[f]; k++) {
+            const BatchItem &u = items[list_base[f] + k];
+            if (u.kind || u.seg || u.a || u.b || u.tile || u.aux) return fail("dev unused position", f, (long)k);
         }
+        for (uint64_t k = 0; k < list_len[f]; k++) {
+            const size_t q = list_base[f] + k;
+            const BatchItem &it = items[q];
+            if (it.seg >= S) return fail("dev segment index", (long)q, it.seg);
+            const BatchSeg &g = segs[it.seg];
+            if (it.kind != list_kind[f]) return fail("dev item kind", (long)q, it.kind);
+            switch (it.kind) {
+                case kItemHist:
+                    if (it.tile >= g.m) return fail("dev tile index", (long)q, it.tile);
+                    hist_rng[it.seg].push_back({it.a * 1024 + it.tile, it.b});
+                    break;
+                case kItemSmall:
+                    if ((f == kListSmall2) != (g.R <= tun.small_scan_max_R))
+                        return fail("dev small list by range", (long)q, g.R);
+                    small_seen[it.seg]++;
+                    break;
+                case kItemScan:
+                    if (it.a != next_chunk[it.seg]) return fail("dev scan chunk order", (long)q, (long)it.a);
+                    next_chunk[it.seg]++;
+                    break;
+                case kItemFill:
+                    if (it.aux != next_fill[it.seg] || it.a != (uint64_t)it.aux * g.fill_chunk ||
+                        it.b != std::min<uint64_t>(g.n, (uint64_t)(it.aux + 1) * g.fill_chunk))
+                        return fail("dev fill item", (long)q, it.aux);
+                    next_fill[it.seg]++;
+                    break;
+            }
+        }
+    }
+    // The first launch's tickets: a bijection onto the histogram items and
+    // the in-CTA segments, each kept in list order, the in-CTA segments
+    // evenly spread (between consecutive ones at most ceil(T / ns) tickets).
+    {
+        const uint64_t nh = hdr.n_hist, ns = hdr.n_small1, T = nh + ns;
+        uint64_t next_h = 0, next_s = 0, last_s = 0;
+        for (uint64_t k = 0; k < T; k++) {
+            const uint64_t q = devplan_first_pos(k, nh, ns, L.hist_bound);
+            if (q < L.hist_bound) {
+                if (q != next_h++) return fail("dev first ticket (histogram)", (long)k, (long)q);
+            } else {
+                if (q != L.hist_bound + next_s) return fail("dev first ticket (in-CTA)", (long)k, (long)q);
+                if (next_s > 0 && (k - last_s) * ns > T + ns) return fail("dev first ticket spread", (long)k, 0);
+                last_s = k;
+                next_s++;
+            }
+        }
+        if (next_h != nh || next_s != ns) return fail("dev first tickets", (long)next_h, (long)next_s);
     }
     for (uint32_t s = 0; s < S; s++) {
         const BatchSeg &g = segs[s];
@@ -263,7 +300,10 @@ static int emit(const char *path) {
     DevPlanHdr hdr;
     std::vector<BatchItem> items;
     const int rc = devplan_host(offs.data(), mn.data(), mx.data(), b, tun, L, &segs, &pfx, &hdr, &items);
-    std::printf("layout %zu %zu %zu %zu %zu %zu\n", L.ctl, L.hdr, L.segs, L.pfx, L.items, L.total_words);
+    std::printf("layout %zu %zu %zu %zu %zu %zu\n", L.ctl, L.hdr, L.segs, L.look, L.items, L.total_words);
+    std::printf("bounds %llu %llu %llu %llu %llu\n", (unsigned long long)L.hist_bound,
+                (unsigned long long)L.first_bound, (unsigned long long)L.scan_bound,
+                (unsigned long long)L.small2_bound, (unsigned long long)L.fill_bound);
     std::printf("rc %d\n", rc);
     std::printf("hdr %u %u %u %u %u %u\n", hdr.n_first, hdr.n_scan, hdr.n_small2, hdr.n_fill, hdr.n_hist,
                 hdr.n_small1);

@@ -187,10 +187,13 @@ def emitter(tmp_path_factory):
 
 
 def test_gpu_planner_writes_what_the_host_emulation_computes(emitter, tmp_path):
-    """The planner kernels' descriptors, list lengths and items, read back from
+    """The planner kernel's descriptors, list lengths and items, read back from
     the workspace, equal the host emulation of the same rules (planner_check
-    --emit) field by field."""
-    L, mn, R, dist, seeds = gen.batched_segments(gen.derive_seed(32), 700, n_lo=1, n_hi=3e5, r_hi=2 ** 18)
+    --emit) field by field: 2600 segments, so three planner CTAs hand their
+    counts on through the lookback, every eleventh segment empty."""
+    L, mn, R, dist, seeds = gen.batched_segments(gen.derive_seed(32), 2600, n_lo=1, n_hi=1e5, r_hi=2 ** 18)
+    L = L.copy()
+    L[::11] = 0
     mn = mn.astype(np.int64)
     x, offs, mns, mxs = make_layout(L, R, mn, dist, seeds)
     S, N, max_R = len(L), x.numel(), 1 << 18
@@ -201,10 +204,12 @@ def test_gpu_planner_writes_what_the_host_emulation_computes(emitter, tmp_path):
     assert r.returncode == 0, r.stdout[-2000:] + r.stderr[-2000:]
     lines = r.stdout.splitlines()
     lay = [int(v) for v in lines[0].split()[1:]]
-    assert lines[1] == "rc 0"
-    hdr = [int(v) for v in lines[2].split()[1:]]
+    hist_b, first_b, scan_b, small2_b, fill_b = [int(v) for v in lines[1].split()[1:]]
+    assert lines[2] == "rc 0"
+    hdr = [int(v) for v in lines[3].split()[1:]]
     segs = [[int(v) for v in ln.split()[1:]] for ln in lines if ln.startswith("seg ")]
-    items = [[int(v) for v in ln.split()[1:]] for ln in lines if ln.startswith("item ")]
+    items = np.asarray([[int(v) for v in ln.split()[1:]] for ln in lines if ln.startswith("item ")],
+                       dtype=np.int64)
     wsb = rtcdf.rtcdf_batch_device_workspace_size(S, N, max_R)
     assert wsb == lay[5] * 4
     ws = torch.zeros(wsb // 4 + 64, dtype=torch.int32, device="cuda")
@@ -217,8 +222,10 @@ def test_gpu_planner_writes_what_the_host_emulation_computes(emitter, tmp_path):
     assert rtcdf.rtcdf_batch_status_get(ws.data_ptr(), s) == (rtcdf.OK, 0)
     check_segments(x, out, offs, mns, mxs)
     w = ws.cpu().numpy().view(np.uint32)
-    _, hdr_off, seg_off, _, item_off, _ = lay
+    _, hdr_off, seg_off, look_off, item_off, _ = lay
     assert w[hdr_off:hdr_off + 6].tolist() == hdr
+    # the output launch left the planner's lookback records zeroed for the next run
+    assert not w[look_off:look_off + 16 * ((S + 1023) // 1024)].any()
     seg_dt = np.dtype([("off", "<u8"), ("out_off", "<u8"), ("n", "<u4"), ("R", "<u4"), ("minVal", "<i4"),
                        ("T", "<u4"), ("m", "<u4"), ("hist_items", "<u4"), ("fill_items", "<u4"),
                        ("fill_chunk", "<u4"), ("scan_chunks", "<u4"), ("single_hist", "<u4"), ("hist_off", "<u8"),
@@ -235,7 +242,12 @@ def test_gpu_planner_writes_what_the_host_emulation_computes(emitter, tmp_path):
                         ("aux", "<u4")])
     it = w[item_off:item_off + len(items) * 8].view(item_dt)
     got = np.stack([it[f].astype(np.int64) for f in ("kind", "seg", "a", "b", "tile", "aux")], axis=1)
-    np.testing.assert_array_equal(got, np.asarray(items, dtype=np.int64))
+    # every list at its fixed base, compared up to its length
+    n_first, n_scan, n_small2, n_fill, n_hist, n_small1 = hdr
+    assert n_small1 > 0 and n_small2 > 0 and n_scan > 0 and n_hist > 0
+    for base, n in ((0, n_hist), (hist_b, n_small1), (first_b, n_scan), (first_b + scan_b, n_small2),
+                    (first_b + scan_b + small2_b, n_fill)):
+        np.testing.assert_array_equal(got[base:base + n], items[base:base + n])
 
 
 def test_benchmark_batched_workload_device_planned():
