@@ -385,13 +385,14 @@ __global__ void __launch_bounds__(kSegThreads, 2) seg_first_kernel(BatchArgs a) 
     }
     __shared__ uint32_t s_idx;
     const uint32_t n_hist = a.dev_counts[4], n_small1 = a.dev_counts[5];
+    const uint32_t nc[kHistClasses] = {a.dev_counts[6], a.dev_counts[7], a.dev_counts[8]};
     for (;;) {
         if (threadIdx.x == 0) s_idx = atomicAdd(&a.ctl->first_ticket, 1u);
         __syncthreads();
         const uint32_t k = s_idx;
         __syncthreads();  // every thread has read s_idx (and the previous item's shared memory is free)
         if (k >= n_hist + n_small1) break;
-        first_item(a, (uint32_t)devplan_first_pos(k, n_hist, n_small1, a.first_split), sm);
+        first_item(a, (uint32_t)devplan_first_pos(k, nc, n_small1, a.hist_bound), sm);
     }
 }
 
@@ -573,9 +574,34 @@ __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs 
             if (tid == 0) prof_item(a, kItemSmall, ts, 0);
         }
     };
-    // Device-built lists: the grid is sized by their bounds; the CTAs past
-    // the lists' lengths exit at once (about half a microsecond per thousand).
-    if (DEV && blockIdx.x >= n_small2 + n_scan) return;
+    if (DEV) {
+        // Device-built lists: a fixed grid whose CTAs take the in-CTA
+        // segments and then the scan chunks by ticket (a grid sized by the
+        // lists' bounds left tens of thousands of CTAs that only exit, about
+        // 0.04 ms, measured).  The planner zeroed the ticket counter.
+        asm volatile("griddepcontrol.launch_dependents;");
+        bool waited = false;
+        for (;;) {
+            if (tid == 0) s_ticket = atomicAdd(&a.ctl->scan_ticket, 1u);
+            __syncthreads();
+            const uint32_t t = s_ticket;
+            __syncthreads();  // every thread has read the ticket (and the previous item's shared memory is free)
+            if (t >= n_small2 + n_scan) break;
+            if (t < n_small2) {
+                small_item(t);
+                continue;
+            }
+            const BatchItem it = a.items[a.n_first + (t - n_small2)];
+            const BatchSeg g = a.segs[it.seg];
+            if (!waited) {
+                asm volatile("griddepcontrol.wait;" ::: "memory");
+                waited = true;
+            }
+            const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
+            scan_chunk(a, it, g, s_warp, s_prefix, s_total, s_wait, s_buf, t0);
+        }
+        return;
+    }
     // The in-CTA segments come first in the grid (dispatched first; spreading
     // them among the scan chunks was measured slower).
     if (blockIdx.x < n_small2) {

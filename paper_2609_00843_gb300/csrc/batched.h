@@ -85,14 +85,16 @@ struct BatchArgs {
     // per item kind busy ns, items, first start, last end, dependency-wait ns.
     unsigned long long *prof = nullptr;
     // Lists built on the device: their lengths (n_first, n_scan, n_small2,
-    // n_fill, n_hist, n_small1) in device memory; null for a host-built plan.
+    // n_fill, n_hist, n_small1, the three histogram lists) in device memory;
+    // null for a host-built plan.
     // The lists then sit at fixed offsets, their bounds: the first launch's
-    // histogram items at 0 and in-CTA segments at first_split, the scan
-    // chunks at n_first, the scan launch's in-CTA segments at n_first +
-    // n_scan, the output items at n_first + n_scan + n_small2 (the n_* of
-    // this struct holding the bounds).
+    // three histogram lists at 0, hist_bound and 2 * hist_bound and its
+    // in-CTA segments at 3 * hist_bound (devplan_pos), the scan chunks at
+    // n_first, the scan launch's in-CTA segments at n_first + n_scan, the
+    // output items at n_first + n_scan + n_small2 (the n_* of this struct
+    // holding the bounds).
     const uint32_t *dev_counts = nullptr;
-    uint32_t first_split = 0;
+    uint64_t hist_bound = 0;
     // The device planner's lookback records, zeroed by the output launch.
     uint32_t *plan_look = nullptr;
     uint32_t plan_look_words = 0;
@@ -144,23 +146,34 @@ struct DevBounds {
     uint64_t max_total_keys;    // seg_offsets[S] <= max_total_keys
 };
 
+// The lists, in items-array order.  The histogram items come in three
+// lists by size (keys >= hist_chunk / 2, >= hist_chunk / 4, fewer), which the
+// first launch takes in that order, so that it ends on short items (in
+// segment order, the last long items made a tail of about 0.1 ms, measured).
+enum : uint32_t {
+    kListHist0 = 0, kListHist1 = 1, kListHist2 = 2,
+    kListSmall1 = 3, kListScan = 4, kListSmall2 = 5, kListFill = 6,
+    kNumLists = 7
+};
+constexpr uint32_t kHistClasses = 3;
+
 // Items of one segment in each list.
 struct DevSegCount {
-    uint32_t hist, small1, scan, small2, fill;
+    uint32_t v[kNumLists];
 };
 
 // Exclusive prefixes of DevSegCount over the segments before s (8 words).
 struct DevPfx {
-    uint32_t hist, small1, scan, small2, fill, pad[3];
+    uint32_t v[kNumLists];
+    uint32_t pad;
 };
 
-// Lengths of the lists (the first four are BatchArgs::dev_counts).
+// Lengths of the lists (the first four are BatchArgs::dev_counts[0..3]).
 struct DevPlanHdr {
     uint32_t n_first, n_scan, n_small2, n_fill, n_hist, n_small1;
-    uint32_t pad[58];
+    uint32_t n_hist_class[kHistClasses];   // dev_counts[6..8]
+    uint32_t pad[55];
 };
-
-enum : uint32_t { kListHist = 0, kListSmall1 = 1, kListScan = 2, kListSmall2 = 3, kListFill = 4 };
 
 // Workspace layout of the device-planned sort (32-bit word offsets).  Every
 // segment owns a fixed slot [H | lookback state | run ends | run keys] sized
@@ -169,39 +182,48 @@ enum : uint32_t { kListHist = 0, kListSmall1 = 1, kListScan = 2, kListSmall2 = 3
 struct DevLayout {
     size_t ctl, hdr, segctl, segs, look, items, start, slots, slot_words, total_words;
     size_t slot_state, slot_run_end, slot_run_val;  // offsets inside a slot
-    uint64_t hist_bound, first_bound, scan_bound, small2_bound, fill_bound, item_bound;
+    uint64_t hist_bound;   // bound of each histogram list (all histogram items)
+    uint64_t first_bound, scan_bound, small2_bound, fill_bound, item_bound;
     uint32_t look_blocks;  // planner CTAs (1024 segments each)
 };
 
 // Position in the items array of list `list`'s element k (its base is the
 // bound-sum of the lists before it).
 __host__ __device__ inline uint64_t devplan_pos(const DevLayout &L, uint32_t list, uint64_t k) {
+    if (list < kHistClasses) return list * L.hist_bound + k;
     switch (list) {
-        case kListHist: return k;
-        case kListSmall1: return L.hist_bound + k;
+        case kListSmall1: return kHistClasses * L.hist_bound + k;
         case kListScan: return L.first_bound + k;
         case kListSmall2: return L.first_bound + L.scan_bound + k;
         default: return L.first_bound + L.scan_bound + L.small2_bound + k;
     }
 }
 
-// The first launch's k-th ticket (k < nh + ns): the in-CTA segments spread
-// evenly among the histogram items -- in-CTA segment j at ticket
-// floor(j * (nh + ns) / ns) -- so that reads (histograms) and writes
-// (in-CTA sorts) overlap throughout.  Returns the items-array position.
-__host__ __device__ inline uint64_t devplan_first_pos(uint64_t k, uint64_t nh, uint64_t ns, uint64_t split) {
-    const uint64_t T = nh + ns;
-    if (ns == 0) return k;
-    const uint64_t j = (k * ns + T - 1) / T;  // in-CTA slots before ticket k: ceil(k * ns / T)
-    if (j < ns && j * T / ns == k) return split + j;
-    return k - j;
+// The first launch's k-th ticket (k < nh + ns, nh = the histogram lists'
+// lengths nc[0..2] summed): the histogram lists one after another (largest
+// items first), and the in-CTA segments spread evenly among them --
+// in-CTA segment j at ticket floor(j * (nh + ns) / ns) -- so that reads
+// (histograms) and writes (in-CTA sorts) overlap throughout.  Returns the
+// items-array position.
+__host__ __device__ inline uint64_t devplan_first_pos(uint64_t k, const uint32_t *nc, uint64_t ns,
+                                                      uint64_t hist_bound) {
+    const uint64_t nh = (uint64_t)nc[0] + nc[1] + nc[2], T = nh + ns;
+    uint64_t h = k;
+    if (ns > 0) {
+        const uint64_t j = (k * ns + T - 1) / T;  // in-CTA slots before ticket k: ceil(k * ns / T)
+        if (j < ns && j * T / ns == k) return kHistClasses * hist_bound + j;  // list kListSmall1
+        h = k - j;
+    }
+    uint32_t c = 0;
+    while (c + 1 < kHistClasses && h >= nc[c]) h -= nc[c++];
+    return c * hist_bound + h;  // list c
 }
 // 0, or RTCDF_ERR_RANGE / RTCDF_ERR_INVALID_ARG for bounds out of range.
 int devplan_layout(const DevBounds &b, const BatchTuning &t, DevLayout *L);
 
-__host__ __device__ inline uint32_t devplan_field(const DevPfx &p, uint32_t list) {
-    return list == kListHist ? p.hist : list == kListSmall1 ? p.small1 : list == kListScan ? p.scan
-           : list == kListSmall2 ? p.small2 : p.fill;
+// Size class of a histogram item of `keys` keys.
+__host__ __device__ inline uint32_t devplan_hist_class(uint64_t keys, uint64_t hist_chunk) {
+    return keys >= hist_chunk / 2 ? 0u : keys >= hist_chunk / 4 ? 1u : 2u;
 }
 
 // Segment s from its metadata: its descriptor (workspace offsets left to the
@@ -209,7 +231,7 @@ __host__ __device__ inline uint32_t devplan_field(const DevPfx &p, uint32_t list
 // when it breaks the bounds or the limits of a segmented sort.
 __host__ __device__ inline bool devplan_segment(int64_t o0, int64_t o1, int64_t mn, int64_t mx, const DevBounds &b,
                                                 const BatchTuning &t, BatchSeg *g, DevSegCount *c) {
-    *c = DevSegCount{0, 0, 0, 0, 0};
+    for (uint32_t i = 0; i < kNumLists; i++) c->v[i] = 0;
     *g = BatchSeg{};
     if (o0 < 0 || o1 < o0 || (uint64_t)o1 > b.max_total_keys) return false;
     const uint64_t n = (uint64_t)(o1 - o0);
@@ -221,8 +243,8 @@ __host__ __device__ inline bool devplan_segment(int64_t o0, int64_t o1, int64_t 
     g->minVal = (int32_t)mn;
     if (n == 0) return true;
     if (g->n <= t.small_max_n && g->R <= kBatchSmallMaxR) {
-        if (g->R <= t.small_scan_max_R) c->small2 = 1;
-        else c->small1 = 1;
+        if (g->R <= t.small_scan_max_R) c->v[kListSmall2] = 1;
+        else c->v[kListSmall1] = 1;
         return true;
     }
     g->m = (g->R + kBatchTileMax - 1) / kBatchTileMax;
@@ -233,27 +255,33 @@ __host__ __device__ inline bool devplan_segment(int64_t o0, int64_t o1, int64_t 
     g->scan_chunks = (g->R + kBatchScanChunk - 1) / kBatchScanChunk;
     g->fill_chunk = t.fill_chunk;
     g->fill_items = (uint32_t)((n + t.fill_chunk - 1) / t.fill_chunk);
-    c->hist = g->hist_items;
-    c->scan = g->scan_chunks;
-    c->fill = g->fill_items;
+    // Whole chunks are class 0; the last chunk, when shorter, goes by its keys.
+    const uint64_t whole = n / t.hist_chunk, rest = n - whole * t.hist_chunk;
+    c->v[kListHist0] = (uint32_t)(whole * g->m);
+    if (rest) c->v[devplan_hist_class(rest, t.hist_chunk)] += g->m;
+    c->v[kListScan] = g->scan_chunks;
+    c->v[kListFill] = g->fill_items;
     return true;
 }
 
 // The k-th item of list `list` that belongs to segment s (k counted within the
-// segment), as build_host_plan lays it out.
+// segment): histogram items chunk-major over tiles (class 0: the whole chunks,
+// then the last chunk if it is in that class; classes 1 and 2: the last
+// chunk), scan chunks and output items ascending.
 __host__ __device__ inline BatchItem devplan_item(uint32_t list, uint32_t s, uint32_t k, const BatchSeg &g,
                                                   const BatchTuning &t) {
     BatchItem it{};
     it.seg = s;
+    if (list < kHistClasses) {
+        const uint32_t whole_items = list == kListHist0 ? (uint32_t)(g.n / t.hist_chunk) * g.m : 0u;
+        const uint32_t c = k < whole_items ? k / g.m : (uint32_t)(g.n / t.hist_chunk);
+        it.kind = kItemHist;
+        it.a = (uint64_t)c * t.hist_chunk;
+        it.b = ((uint64_t)c + 1) * t.hist_chunk < g.n ? ((uint64_t)c + 1) * t.hist_chunk : g.n;
+        it.tile = k < whole_items ? k % g.m : k - whole_items;
+        return it;
+    }
     switch (list) {
-        case kListHist: {
-            const uint32_t c = k / g.m;
-            it.kind = kItemHist;
-            it.a = (uint64_t)c * t.hist_chunk;
-            it.b = ((uint64_t)c + 1) * t.hist_chunk < g.n ? ((uint64_t)c + 1) * t.hist_chunk : g.n;
-            it.tile = k % g.m;
-            break;
-        }
         case kListScan:
             it.kind = kItemScan;
             it.a = k;

@@ -14,11 +14,13 @@
 // lists before them), so no CTA needs the totals to place its items; the
 // last CTA writes the lists' lengths.
 // The three launches then run over these lists (seg_*_kernel<true>); their
-// lengths are known only on the device, so the first launch is a fixed grid
-// whose CTAs take items by ticket (the in-CTA segments spread evenly among the
-// histogram items), and the scan and output launches have one CTA per item of
-// the lists' bounds, the CTAs past a list's length exiting at once (about
-// half a microsecond per thousand, measured).
+// lengths are known only on the device, so the first and scan launches are
+// fixed grids whose CTAs take items by ticket (the first launch: the three
+// histogram lists, largest items first, with the in-CTA segments spread
+// evenly among them; the scan launch: the narrow in-CTA segments, then the
+// chunks), and the output launch has one CTA per item of the list's bound,
+// the CTAs past the list's length exiting at once (about half a microsecond
+// per thousand, measured).
 //
 // The workspace is sized from host-known bounds (segment count, total keys,
 // widest range).  Every segment owns a fixed slot for its histogram, lookback
@@ -54,13 +56,15 @@ struct DevPlanArgs {
 // counts and the inclusive ones -- per list, and the number of segments that
 // broke the bounds.  Each array is written once, before the state that
 // announces it, so a reader never sees one being overwritten.
+constexpr uint32_t kLookCounts = kNumLists + 1;  // every list, and the segments that broke the bounds
 struct DevLook {
     uint32_t flag;
-    uint32_t own[6];
-    uint32_t incl[6];
-    uint32_t pad[3];
+    uint32_t own[kLookCounts];
+    uint32_t incl[kLookCounts];
+    uint32_t pad[32 - 1 - 2 * kLookCounts];
 };
-static_assert(sizeof(DevLook) == 64, "lookback record is 16 words");
+static_assert(sizeof(DevLook) == 128, "lookback record is 32 words");
+constexpr uint32_t kLookWords = sizeof(DevLook) / 4;
 
 __device__ __forceinline__ void st_release_u32(uint32_t *p, uint32_t v) {
     asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
@@ -72,9 +76,9 @@ __device__ __forceinline__ uint32_t ld_acquire_u32(const uint32_t *p) {
 }
 
 __global__ void __launch_bounds__(1024) devplan_kernel(DevPlanArgs p) {
-    __shared__ uint32_t s_ex[5][1024];  // exclusive prefix of each list's counts within the CTA
-    __shared__ uint32_t s_warp[5][32];
-    __shared__ uint32_t s_tot[6], s_base[6];
+    __shared__ uint32_t s_ex[kNumLists][1024];  // exclusive prefix of each list's counts within the CTA
+    __shared__ uint32_t s_warp[kNumLists][32];
+    __shared__ uint32_t s_tot[kLookCounts], s_base[kLookCounts];
     __shared__ uint32_t s_blk;
     __shared__ int s_bad;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -95,15 +99,18 @@ __global__ void __launch_bounds__(1024) devplan_kernel(DevPlanArgs p) {
         if (tid == 0) atomicOr(&ctl->status, kDevTimeout);
         return;
     }
-    if (blk == 0 && tid == 0) ctl->first_ticket = 0;  // the previous run has finished (stream order)
+    if (blk == 0 && tid == 0) {  // the previous run has finished (stream order)
+        ctl->first_ticket = 0;
+        ctl->scan_ticket = 0;
+    }
     const uint32_t S = p.b.S, s = blk * 1024 + tid;
-    DevSegCount c{0, 0, 0, 0, 0};
+    DevSegCount c{};
     BatchSeg g{};
     if (s < S && !devplan_segment(p.offs[s], p.offs[s + 1], p.mn[s], p.mx[s], p.b, p.t, &g, &c)) s_bad = 1;
-    const uint32_t v[5] = {c.hist, c.small1, c.scan, c.small2, c.fill};
-    uint32_t inc[5];
+    const uint32_t *v = c.v;
+    uint32_t inc[kNumLists];
 #pragma unroll
-    for (int f = 0; f < 5; f++) {
+    for (int f = 0; f < kNumLists; f++) {
         inc[f] = v[f];
 #pragma unroll
         for (int d = 1; d < 32; d <<= 1) {
@@ -113,7 +120,7 @@ __global__ void __launch_bounds__(1024) devplan_kernel(DevPlanArgs p) {
         if (lane == 31) s_warp[f][warp] = inc[f];
     }
     __syncthreads();
-    if (warp < 5) {
+    if (warp < kNumLists) {
         const uint32_t x = s_warp[warp][lane];
         uint32_t xi = x;
 #pragma unroll
@@ -126,14 +133,14 @@ __global__ void __launch_bounds__(1024) devplan_kernel(DevPlanArgs p) {
     }
     __syncthreads();
 #pragma unroll
-    for (int f = 0; f < 5; f++) s_ex[f][tid] = s_warp[f][warp] + inc[f] - v[f];
+    for (int f = 0; f < kNumLists; f++) s_ex[f][tid] = s_warp[f][warp] + inc[f] - v[f];
     if (tid == 0) {
-        s_tot[5] = s_bad ? 1u : 0u;
+        s_tot[kNumLists] = s_bad ? 1u : 0u;
         // Counts of the segments before this CTA's: publish its own, then
         // add the predecessors' until one has published its inclusive counts.
-        uint32_t pre[6] = {0, 0, 0, 0, 0, 0};
+        uint32_t pre[kLookCounts] = {};
         if (blk > 0) {
-            for (int i = 0; i < 6; i++) look[blk].own[i] = s_tot[i];
+            for (int i = 0; i < kLookCounts; i++) look[blk].own[i] = s_tot[i];
             st_release_u32(&look[blk].flag, 1u);
             int64_t j = (int64_t)blk - 1;
             uint32_t spins = 0;
@@ -146,16 +153,16 @@ __global__ void __launch_bounds__(1024) devplan_kernel(DevPlanArgs p) {
                 }
                 if (f == 0) {  // the wait ran out: mark the plan unusable
                     atomicOr(&ctl->status, kDevTimeout);
-                    pre[5] += 1;
+                    pre[kNumLists] += 1;
                     break;
                 }
                 const uint32_t *src = f == 2 ? look[j].incl : look[j].own;
-                for (int i = 0; i < 6; i++) pre[i] += src[i];
+                for (int i = 0; i < kLookCounts; i++) pre[i] += src[i];
                 if (f == 2) break;
                 j--;
             }
         }
-        for (int i = 0; i < 6; i++) {
+        for (int i = 0; i < kLookCounts; i++) {
             s_base[i] = pre[i];
             look[blk].incl[i] = pre[i] + s_tot[i];
         }
@@ -177,7 +184,7 @@ __global__ void __launch_bounds__(1024) devplan_kernel(DevPlanArgs p) {
     // This CTA's items of every list, all threads together: the owner of the
     // k-th is the last segment whose prefix is at most k.
     const uint32_t nseg = min(1024u, S - blk * 1024);
-    for (uint32_t f = 0; f < 5; f++) {
+    for (uint32_t f = 0; f < kNumLists; f++) {
         for (uint32_t k = tid; k < s_tot[f]; k += 1024) {
             uint32_t lo = 0, hi = nseg;
             while (hi - lo > 1) {
@@ -190,21 +197,22 @@ __global__ void __launch_bounds__(1024) devplan_kernel(DevPlanArgs p) {
         }
     }
     if (blk == p.L.look_blocks - 1 && tid == 0) {
-        uint32_t t[6];
-        for (int i = 0; i < 6; i++) t[i] = s_base[i] + s_tot[i];
+        uint32_t t[kLookCounts];
+        for (int i = 0; i < kLookCounts; i++) t[i] = s_base[i] + s_tot[i];
         DevPlanHdr *h = reinterpret_cast<DevPlanHdr *>(p.ws + p.L.hdr);
-        const uint64_t nf = (uint64_t)t[kListHist] + t[kListSmall1];
+        const uint64_t nh = (uint64_t)t[kListHist0] + t[kListHist1] + t[kListHist2];
         // The bounds hold by construction; checked anyway, so that a list
         // never outgrows its region.
-        const bool bad = t[5] > 0 || t[kListHist] > p.L.hist_bound || t[kListSmall1] > p.L.first_bound - p.L.hist_bound ||
-                         t[kListScan] > p.L.scan_bound || t[kListSmall2] > p.L.small2_bound ||
-                         t[kListFill] > p.L.fill_bound;
-        h->n_hist = bad ? 0 : t[kListHist];
+        bool bad = t[kNumLists] > 0 || nh > p.L.hist_bound || t[kListSmall1] > p.b.S ||
+                   t[kListScan] > p.L.scan_bound || t[kListSmall2] > p.L.small2_bound ||
+                   t[kListFill] > p.L.fill_bound;
+        h->n_hist = bad ? 0 : (uint32_t)nh;
         h->n_small1 = bad ? 0 : t[kListSmall1];
-        h->n_first = bad ? 0 : (uint32_t)nf;
+        h->n_first = bad ? 0 : (uint32_t)nh + t[kListSmall1];
         h->n_scan = bad ? 0 : t[kListScan];
         h->n_small2 = bad ? 0 : t[kListSmall2];
         h->n_fill = bad ? 0 : t[kListFill];
+        for (uint32_t c = 0; c < kHistClasses; c++) h->n_hist_class[c] = bad ? 0 : t[c];
         if (bad) atomicOr(&ctl->status, kDevBadSegment);
     }
 }
@@ -263,7 +271,7 @@ int devplan_layout(const DevBounds &b, const BatchTuning &t, DevLayout *L) {
     const uint64_t cpr = (b.max_R + kBatchScanChunk - 1) / kBatchScanChunk;  // scan chunks per segment
     const uint64_t m_max = (b.max_R + kBatchTileMax - 1) / kBatchTileMax;
     L->hist_bound = (N / t.hist_chunk + S) * m_max;
-    L->first_bound = L->hist_bound + S;
+    L->first_bound = kHistClasses * L->hist_bound + S;
     L->scan_bound = S * cpr;
     L->small2_bound = S;
     L->fill_bound = N / t.fill_chunk + S;
@@ -274,7 +282,7 @@ int devplan_layout(const DevBounds &b, const BatchTuning &t, DevLayout *L) {
     L->segctl = w;   w += align64(S * sizeof(BatchSegCtl) / 4);
     L->segs = w;     w += align64(S * sizeof(BatchSeg) / 4);
     L->look_blocks = (uint32_t)((S + 1023) / 1024);
-    L->look = w;     w += align64((uint64_t)L->look_blocks * 16);
+    L->look = w;     w += align64((uint64_t)L->look_blocks * kLookWords);
     L->items = w;    w += align64(L->item_bound * sizeof(BatchItem) / 4);
     L->start = w;    w += align64(L->fill_bound);
     L->slots = w;
@@ -295,42 +303,42 @@ int devplan_host(const int64_t *offs, const int64_t *mn, const int64_t *mx, cons
     pfx->assign((size_t)S + 1, DevPfx{});
     memset(hdr, 0, sizeof(*hdr));
     items->clear();
-    uint32_t run[5] = {0, 0, 0, 0, 0};
+    DevPfx run{};
     for (uint32_t s = 0; s < S; s++) {
         DevSegCount c;
         BatchSeg g;
         if (!devplan_segment(offs[s], offs[s + 1], mn[s], mx[s], b, t, &g, &c)) return RTCDF_ERR_INVALID_ARG;
-        (*pfx)[s] = DevPfx{run[0], run[1], run[2], run[3], run[4], {0, 0, 0}};
+        (*pfx)[s] = run;
         if (g.m > 0) {
             const size_t slot = L.slots + (size_t)s * L.slot_words;
             g.hist_off = slot;
             g.state_off = slot + L.slot_state;
             g.run_end_off = slot + L.slot_run_end;
             g.run_val_off = slot + L.slot_run_val;
-            g.start_run_off = L.start + run[kListFill];
+            g.start_run_off = L.start + run.v[kListFill];
         }
         (*segs)[s] = g;
-        run[0] += c.hist, run[1] += c.small1, run[2] += c.scan, run[3] += c.small2, run[4] += c.fill;
+        for (uint32_t f = 0; f < kNumLists; f++) run.v[f] += c.v[f];
     }
-    (*pfx)[S] = DevPfx{run[0], run[1], run[2], run[3], run[4], {0, 0, 0}};
-    hdr->n_hist = run[0];
-    hdr->n_small1 = run[1];
-    hdr->n_first = run[0] + run[1];
-    hdr->n_scan = run[2];
-    hdr->n_small2 = run[3];
-    hdr->n_fill = run[4];
-    if (hdr->n_hist > L.hist_bound || hdr->n_small1 > L.first_bound - L.hist_bound || hdr->n_scan > L.scan_bound ||
+    (*pfx)[S] = run;
+    hdr->n_hist = run.v[kListHist0] + run.v[kListHist1] + run.v[kListHist2];
+    for (uint32_t c = 0; c < kHistClasses; c++) hdr->n_hist_class[c] = run.v[c];
+    hdr->n_small1 = run.v[kListSmall1];
+    hdr->n_first = hdr->n_hist + hdr->n_small1;
+    hdr->n_scan = run.v[kListScan];
+    hdr->n_small2 = run.v[kListSmall2];
+    hdr->n_fill = run.v[kListFill];
+    if (hdr->n_hist > L.hist_bound || hdr->n_small1 > S || hdr->n_scan > L.scan_bound ||
         hdr->n_small2 > L.small2_bound || hdr->n_fill > L.fill_bound)
         return RTCDF_ERR_INVALID_ARG;
     // The items at the positions the planner writes them: each list in
     // segment order from its own base (devplan_pos); unused positions stay
     // zero here.
     items->assign(L.item_bound, BatchItem{});
-    const uint32_t lists[5] = {kListHist, kListSmall1, kListScan, kListSmall2, kListFill};
-    for (uint32_t list : lists)
+    for (uint32_t list = 0; list < kNumLists; list++)
         for (uint32_t s = 0; s < S; s++)
-            for (uint32_t k = devplan_field((*pfx)[s], list); k < devplan_field((*pfx)[s + 1], list); k++)
-                (*items)[devplan_pos(L, list, k)] = devplan_item(list, s, k - devplan_field((*pfx)[s], list), (*segs)[s], t);
+            for (uint32_t k = (*pfx)[s].v[list]; k < (*pfx)[s + 1].v[list]; k++)
+                (*items)[devplan_pos(L, list, k)] = devplan_item(list, s, k - (*pfx)[s].v[list], (*segs)[s], t);
     return 0;
 }
 
@@ -411,16 +419,17 @@ rtcdf_status rtcdf_sort_batched_device_ws(const int32_t *in, int32_t *out, const
     a.ws_u32 = ws;
     a.ctl = reinterpret_cast<BatchCtl *>(ws + L.ctl);
     a.seg_ctl = reinterpret_cast<BatchSegCtl *>(ws + L.segctl);
-    a.dev_counts = ws + L.hdr;  // n_first, n_scan, n_small2, n_fill, n_hist, n_small1
-    a.first_split = (uint32_t)L.hist_bound;
+    a.dev_counts = ws + L.hdr;  // n_first, n_scan, n_small2, n_fill, n_hist, n_small1, n_hist_class[3]
+    a.hist_bound = L.hist_bound;
     a.plan_look = ws + L.look;
-    a.plan_look_words = L.look_blocks * 16;
-    // The first launch: two resident CTAs per SM taking items by ticket; the
-    // scan and output launches: one CTA per item of the lists' bounds.
+    a.plan_look_words = L.look_blocks * kLookWords;
+    // The first and scan launches: two (1024 threads) and six (256 threads)
+    // resident CTAs per SM taking items by ticket; the output launch: one CTA
+    // per item of the list's bound.
     if (L.scan_bound + L.small2_bound > 0x7fffffffull || L.fill_bound > 0x7fffffffull)
         return RTCDF_ERR_INVALID_ARG;
     const uint32_t first = (uint32_t)std::min<uint64_t>(L.first_bound, 2ull * sms);
-    const uint32_t scan = (uint32_t)(L.scan_bound + L.small2_bound);
+    const uint32_t scan = (uint32_t)std::min<uint64_t>(L.scan_bound + L.small2_bound, 6ull * sms);
     const uint32_t fill = (uint32_t)L.fill_bound;
     if (launch_batched_dev(a, std::max(first, 1u), std::max(scan, 1u), std::max(fill, 1u), s) != cudaSuccess)
         return RTCDF_ERR_CUDA;

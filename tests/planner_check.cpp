@@ -9,11 +9,13 @@
 // every value is present).  The same shapes go through the host emulation of
 // the device planner (devplan_host: the rules the planner kernel applies): its
 // lists sit at their fixed bases and hold the right kinds in the right order,
-// the positions past a list's length stay unused, every segment's scan chunks
+// each of the three histogram lists only items of its size class, the
+// positions past a list's length stay unused, every segment's scan chunks
 // ascend, the items cover every segment's keys and positions exactly once, the
 // list lengths stay within the bounds the workspace was sized for, the first
-// launch's tickets map one-to-one onto its two lists with the in-CTA segments
-// evenly spread, and every segment's regions lie inside its own slot.
+// launch's tickets map one-to-one onto the histogram lists (one after another)
+// and the in-CTA segments (evenly spread), and every segment's regions lie
+// inside its own slot.
 // Usage: planner_check <seed> <segments>; prints "OK" or the first violation.
 // planner_check --emit <file> reads bounds and metadata ("S N maxR", then S+1
 // offsets, S minVal, S maxVal) and prints the layout, the lists' bounds and
@@ -166,24 +168,29 @@ static int check_dev(const std::vector<SegSpec> &spec, const BatchTuning &tun, u
     if (any_bad) return rc ? 0 : fail("dev plan accepted a range above max_R", 0, 0);
     if (rc) return fail("dev plan rejected", rc, 0);
     if (hdr.n_first != hdr.n_hist + hdr.n_small1) return fail("dev first list", hdr.n_first, hdr.n_hist);
+    if (hdr.n_hist != (uint64_t)hdr.n_hist_class[0] + hdr.n_hist_class[1] + hdr.n_hist_class[2])
+        return fail("dev histogram lists", hdr.n_hist, hdr.n_hist_class[0]);
     if (items.size() != L.item_bound) return fail("dev items array", (long)items.size(), (long)L.item_bound);
-    if (L.first_bound != L.hist_bound + L.small2_bound) return fail("dev first bound", 0, 0);
-    if (hdr.n_hist > L.hist_bound || hdr.n_small1 > L.first_bound - L.hist_bound || hdr.n_scan > L.scan_bound ||
+    if (L.first_bound != kHistClasses * L.hist_bound + L.small2_bound) return fail("dev first bound", 0, 0);
+    if (hdr.n_hist > L.hist_bound || hdr.n_small1 > S || hdr.n_scan > L.scan_bound ||
         hdr.n_small2 > L.small2_bound || hdr.n_fill > L.fill_bound)
         return fail("dev bounds", hdr.n_first, hdr.n_scan);
     // Each list sits at its fixed base (the bounds of the lists before it);
     // the positions past a list's length stay unused.
-    const uint64_t list_base[5] = {0, L.hist_bound, L.first_bound, L.first_bound + L.scan_bound,
-                                   L.first_bound + L.scan_bound + L.small2_bound};
-    const uint64_t list_bound[5] = {L.hist_bound, L.first_bound - L.hist_bound, L.scan_bound, L.small2_bound,
-                                    L.fill_bound};
-    const uint32_t list_len[5] = {hdr.n_hist, hdr.n_small1, hdr.n_scan, hdr.n_small2, hdr.n_fill};
-    const uint32_t list_kind[5] = {kItemHist, kItemSmall, kItemScan, kItemSmall, kItemFill};
-    for (uint32_t f = 0; f < 5; f++)
+    const uint64_t list_base[kNumLists] = {0, L.hist_bound, 2 * L.hist_bound, 3 * L.hist_bound, L.first_bound,
+                                           L.first_bound + L.scan_bound,
+                                           L.first_bound + L.scan_bound + L.small2_bound};
+    const uint64_t list_bound[kNumLists] = {L.hist_bound, L.hist_bound, L.hist_bound, S, L.scan_bound,
+                                            L.small2_bound, L.fill_bound};
+    const uint32_t list_len[kNumLists] = {hdr.n_hist_class[0], hdr.n_hist_class[1], hdr.n_hist_class[2],
+                                          hdr.n_small1, hdr.n_scan, hdr.n_small2, hdr.n_fill};
+    const uint32_t list_kind[kNumLists] = {kItemHist, kItemHist, kItemHist, kItemSmall, kItemScan, kItemSmall,
+                                           kItemFill};
+    for (uint32_t f = 0; f < kNumLists; f++)
         if (devplan_pos(L, f, 0) != list_base[f]) return fail("dev list base", f, (long)devplan_pos(L, f, 0));
     std::vector<uint32_t> small_seen(S, 0), next_chunk(S, 0), next_fill(S, 0);
     std::vector<std::vector<std::pair<uint64_t, uint64_t>>> hist_rng(S);
-    for (uint32_t f = 0; f < 5; f++) {
+    for (uint32_t f = 0; f < kNumLists; f++) {
         for (uint64_t k = list_len[f]; k < list_bound[f]; k++) {
             const BatchItem &u = items[list_base[f] + k];
             if (u.kind || u.seg || u.a || u.b || u.tile || u.aux) return fail("dev unused position", f, (long)k);
@@ -197,6 +204,8 @@ static int check_dev(const std::vector<SegSpec> &spec, const BatchTuning &tun, u
             switch (it.kind) {
                 case kItemHist:
                     if (it.tile >= g.m) return fail("dev tile index", (long)q, it.tile);
+                    // each histogram list holds the items of its size class
+                    if (devplan_hist_class(it.b - it.a, tun.hist_chunk) != f) return fail("dev histogram class", (long)q, f);
                     hist_rng[it.seg].push_back({it.a * 1024 + it.tile, it.b});
                     break;
                 case kItemSmall:
@@ -217,18 +226,25 @@ static int check_dev(const std::vector<SegSpec> &spec, const BatchTuning &tun, u
             }
         }
     }
-    // The first launch's tickets: a bijection onto the histogram items and
-    // the in-CTA segments, each kept in list order, the in-CTA segments
-    // evenly spread (between consecutive ones at most ceil(T / ns) tickets).
+    // The first launch's tickets: a bijection onto the three histogram lists
+    // (taken one after another, each in list order) and the in-CTA segments
+    // (in list order, evenly spread: between consecutive ones at most
+    // ceil(T / ns) tickets).
     {
         const uint64_t nh = hdr.n_hist, ns = hdr.n_small1, T = nh + ns;
         uint64_t next_h = 0, next_s = 0, last_s = 0;
+        const uint64_t hb = L.hist_bound;
+        auto hist_pos = [&](uint64_t h) {  // the h-th histogram item over the three lists
+            uint32_t c = 0;
+            while (c + 1 < kHistClasses && h >= hdr.n_hist_class[c]) h -= hdr.n_hist_class[c++];
+            return c * hb + h;
+        };
         for (uint64_t k = 0; k < T; k++) {
-            const uint64_t q = devplan_first_pos(k, nh, ns, L.hist_bound);
-            if (q < L.hist_bound) {
-                if (q != next_h++) return fail("dev first ticket (histogram)", (long)k, (long)q);
+            const uint64_t q = devplan_first_pos(k, hdr.n_hist_class, ns, hb);
+            if (q < kHistClasses * hb) {
+                if (q != hist_pos(next_h++)) return fail("dev first ticket (histogram)", (long)k, (long)q);
             } else {
-                if (q != L.hist_bound + next_s) return fail("dev first ticket (in-CTA)", (long)k, (long)q);
+                if (q != kHistClasses * hb + next_s) return fail("dev first ticket (in-CTA)", (long)k, (long)q);
                 if (next_s > 0 && (k - last_s) * ns > T + ns) return fail("dev first ticket spread", (long)k, 0);
                 last_s = k;
                 next_s++;
@@ -305,8 +321,8 @@ static int emit(const char *path) {
                 (unsigned long long)L.first_bound, (unsigned long long)L.scan_bound,
                 (unsigned long long)L.small2_bound, (unsigned long long)L.fill_bound);
     std::printf("rc %d\n", rc);
-    std::printf("hdr %u %u %u %u %u %u\n", hdr.n_first, hdr.n_scan, hdr.n_small2, hdr.n_fill, hdr.n_hist,
-                hdr.n_small1);
+    std::printf("hdr %u %u %u %u %u %u %u %u %u\n", hdr.n_first, hdr.n_scan, hdr.n_small2, hdr.n_fill, hdr.n_hist,
+                hdr.n_small1, hdr.n_hist_class[0], hdr.n_hist_class[1], hdr.n_hist_class[2]);
     for (const BatchSeg &g : segs)
         std::printf("seg %llu %u %u %d %u %u %u %u %u %u %u %llu %llu %llu %llu %llu\n",
                     (unsigned long long)g.off, g.n, g.R, g.minVal, g.T, g.m, g.hist_items, g.fill_items,

@@ -190,10 +190,14 @@ def test_gpu_planner_writes_what_the_host_emulation_computes(emitter, tmp_path):
     """The planner kernel's descriptors, list lengths and items, read back from
     the workspace, equal the host emulation of the same rules (planner_check
     --emit) field by field: 2600 segments, so three planner CTAs hand their
-    counts on through the lookback, every eleventh segment empty."""
+    counts on through the lookback, every eleventh segment empty, and items
+    in each of the three histogram lists."""
     L, mn, R, dist, seeds = gen.batched_segments(gen.derive_seed(32), 2600, n_lo=1, n_hi=1e5, r_hi=2 ** 18)
     L = L.copy()
     L[::11] = 0
+    # some segments with histogram items of each size class (a whole chunk
+    # of 2^19 keys and a short rest, 200000 keys, 300000 keys)
+    L[1::50], L[2::50], L[3::50] = 600_000, 200_000, 300_000
     mn = mn.astype(np.int64)
     x, offs, mns, mxs = make_layout(L, R, mn, dist, seeds)
     S, N, max_R = len(L), x.numel(), 1 << 18
@@ -223,9 +227,9 @@ def test_gpu_planner_writes_what_the_host_emulation_computes(emitter, tmp_path):
     check_segments(x, out, offs, mns, mxs)
     w = ws.cpu().numpy().view(np.uint32)
     _, hdr_off, seg_off, look_off, item_off, _ = lay
-    assert w[hdr_off:hdr_off + 6].tolist() == hdr
+    assert w[hdr_off:hdr_off + 9].tolist() == hdr
     # the output launch left the planner's lookback records zeroed for the next run
-    assert not w[look_off:look_off + 16 * ((S + 1023) // 1024)].any()
+    assert not w[look_off:look_off + 32 * ((S + 1023) // 1024)].any()
     seg_dt = np.dtype([("off", "<u8"), ("out_off", "<u8"), ("n", "<u4"), ("R", "<u4"), ("minVal", "<i4"),
                        ("T", "<u4"), ("m", "<u4"), ("hist_items", "<u4"), ("fill_items", "<u4"),
                        ("fill_chunk", "<u4"), ("scan_chunks", "<u4"), ("single_hist", "<u4"), ("hist_off", "<u8"),
@@ -243,10 +247,10 @@ def test_gpu_planner_writes_what_the_host_emulation_computes(emitter, tmp_path):
     it = w[item_off:item_off + len(items) * 8].view(item_dt)
     got = np.stack([it[f].astype(np.int64) for f in ("kind", "seg", "a", "b", "tile", "aux")], axis=1)
     # every list at its fixed base, compared up to its length
-    n_first, n_scan, n_small2, n_fill, n_hist, n_small1 = hdr
-    assert n_small1 > 0 and n_small2 > 0 and n_scan > 0 and n_hist > 0
-    for base, n in ((0, n_hist), (hist_b, n_small1), (first_b, n_scan), (first_b + scan_b, n_small2),
-                    (first_b + scan_b + small2_b, n_fill)):
+    n_first, n_scan, n_small2, n_fill, n_hist, n_small1, nh0, nh1, nh2 = hdr
+    assert n_small1 > 0 and n_small2 > 0 and n_scan > 0 and min(nh0, nh1, nh2) > 0
+    for base, n in ((0, nh0), (hist_b, nh1), (2 * hist_b, nh2), (3 * hist_b, n_small1), (first_b, n_scan),
+                    (first_b + scan_b, n_small2), (first_b + scan_b + small2_b, n_fill)):
         np.testing.assert_array_equal(got[base:base + n], items[base:base + n])
 
 
