@@ -358,6 +358,10 @@ __device__ __forceinline__ uint32_t next_after(const uint32_t *e, uint32_t lo, u
 
 }  // namespace
 
+__device__ __forceinline__ DevListBounds dev_lb(const BatchArgs &a) {
+    return DevListBounds{a.dev_bounds[0], a.dev_bounds[1], a.dev_bounds[2], a.dev_bounds[3], a.dev_bounds[4]};
+}
+
 __device__ __forceinline__ void first_item(const BatchArgs &a, uint32_t idx, uint32_t *sm) {
     const unsigned long long t0 = (a.prof && threadIdx.x == 0) ? global_ns() : 0ull;
     const BatchItem it = a.items[idx];
@@ -392,7 +396,7 @@ __global__ void __launch_bounds__(kSegThreads, 2) seg_first_kernel(BatchArgs a) 
         const uint32_t k = s_idx;
         __syncthreads();  // every thread has read s_idx (and the previous item's shared memory is free)
         if (k >= n_hist + n_small1) break;
-        first_item(a, (uint32_t)devplan_first_pos(k, nc, n_small1, a.hist_bound), sm);
+        first_item(a, (uint32_t)devplan_first_pos(k, nc, n_small1, dev_lb(a)), sm);
     }
 }
 
@@ -566,7 +570,7 @@ __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs 
     const uint32_t n_small2 = DEV ? a.dev_counts[2] : a.n_small2;
     auto small_item = [&](uint32_t i) {
         const unsigned long long ts = (a.prof && tid == 0) ? global_ns() : 0ull;
-        const BatchItem it = a.items[a.n_first + a.n_scan + i];
+        const BatchItem it = a.items[DEV ? devplan_pos(dev_lb(a), kListSmall2, i) : a.n_first + a.n_scan + i];
         const BatchSeg g = a.segs[it.seg];
         do_small(a, g, s_buf, kScanSmemWords - 64, s_buf + kScanSmemWords - 64);
         if (a.prof) {
@@ -591,7 +595,7 @@ __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs 
                 small_item(t);
                 continue;
             }
-            const BatchItem it = a.items[a.n_first + (t - n_small2)];
+            const BatchItem it = a.items[devplan_chain_pos(dev_lb(a), kListScan0, a.dev_counts + 9, 2, t - n_small2)];
             const BatchSeg g = a.segs[it.seg];
             if (!waited) {
                 asm volatile("griddepcontrol.wait;" ::: "memory");
@@ -744,9 +748,6 @@ __global__ void __launch_bounds__(kFillCtaThreads) seg_fill_kernel(BatchArgs a) 
     __shared__ uint32_t s_end[kSegFillRuns];
     __shared__ int32_t s_val[kSegFillRuns];
     const uint32_t tid = threadIdx.x;
-    // The output items sit after the other lists (their lengths for a host
-    // plan, their bounds for device-built lists).
-    const uint32_t base = a.n_first + a.n_scan + a.n_small2;
     if (DEV && blockIdx.x == 0) {
         // The first CTA leaves the device planner's ticket and lookback
         // records zeroed for the next run (the planner finished before this
@@ -764,8 +765,10 @@ __global__ void __launch_bounds__(kFillCtaThreads) seg_fill_kernel(BatchArgs a) 
         return;
     }
     // The item and its segment are plan data: fetched before waiting for the
-    // scan launch.
-    const BatchItem it = a.items[base + blockIdx.x];
+    // scan launch.  A host plan's output items sit after its other lists;
+    // device-built ones in two lists by cost, the expensive one first.
+    const BatchItem it = a.items[DEV ? devplan_chain_pos(dev_lb(a), kListFill0, a.dev_counts + 11, 2, blockIdx.x)
+                                     : a.n_first + a.n_scan + a.n_small2 + blockIdx.x];
     const BatchSeg g = a.segs[it.seg];
     asm volatile("griddepcontrol.wait;" ::: "memory");
     const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;

@@ -85,16 +85,12 @@ struct BatchArgs {
     // per item kind busy ns, items, first start, last end, dependency-wait ns.
     unsigned long long *prof = nullptr;
     // Lists built on the device: their lengths (n_first, n_scan, n_small2,
-    // n_fill, n_hist, n_small1, the three histogram lists) in device memory;
-    // null for a host-built plan.
-    // The lists then sit at fixed offsets, their bounds: the first launch's
-    // three histogram lists at 0, hist_bound and 2 * hist_bound and its
-    // in-CTA segments at 3 * hist_bound (devplan_pos), the scan chunks at
-    // n_first, the scan launch's in-CTA segments at n_first + n_scan, the
-    // output items at n_first + n_scan + n_small2 (the n_* of this struct
-    // holding the bounds).
+    // n_fill, n_hist, n_small1, then the lengths of the histogram, scan and
+    // output lists by class) in device memory; null for a host-built plan.
+    // The lists then sit at fixed offsets given by their bounds
+    // (devplan_pos).
     const uint32_t *dev_counts = nullptr;
-    uint64_t hist_bound = 0;
+    uint64_t dev_bounds[5] = {0, 0, 0, 0, 0};  // DevListBounds: hist, first, scan, small2, fill
     // The device planner's lookback records, zeroed by the output launch.
     uint32_t *plan_look = nullptr;
     uint32_t plan_look_words = 0;
@@ -146,33 +142,47 @@ struct DevBounds {
     uint64_t max_total_keys;    // seg_offsets[S] <= max_total_keys
 };
 
-// The lists, in items-array order.  The histogram items come in three
-// lists by size (keys >= hist_chunk / 2, >= hist_chunk / 4, fewer), which the
-// first launch takes in that order, so that it ends on short items (in
-// segment order, the last long items made a tail of about 0.1 ms, measured).
+// The lists, in items-array order.  Each kind of item comes in lists by
+// size, which the launches take largest first, so that a launch ends on
+// short items (in segment order, the last long histogram items made a tail
+// of about 0.1 ms, measured): histogram items by keys (>= hist_chunk / 2,
+// >= hist_chunk / 4, fewer), scan chunks by their segment's chain (at least
+// kLongChain chunks first), output items by estimated cost (length x (1/4 +
+// min(R, n) / n) at least fill_chunk / 2 first).
 enum : uint32_t {
     kListHist0 = 0, kListHist1 = 1, kListHist2 = 2,
-    kListSmall1 = 3, kListScan = 4, kListSmall2 = 5, kListFill = 6,
-    kNumLists = 7
+    kListSmall1 = 3,
+    kListScan0 = 4, kListScan1 = 5,
+    kListSmall2 = 6,
+    kListFill0 = 7, kListFill1 = 8,
+    kNumLists = 9
 };
 constexpr uint32_t kHistClasses = 3;
+constexpr uint32_t kLongChain = 8;
 
 // Items of one segment in each list.
 struct DevSegCount {
     uint32_t v[kNumLists];
 };
 
-// Exclusive prefixes of DevSegCount over the segments before s (8 words).
+// Exclusive prefixes of DevSegCount over the segments before s.
 struct DevPfx {
     uint32_t v[kNumLists];
-    uint32_t pad;
+    uint32_t pad[16 - kNumLists];
 };
 
 // Lengths of the lists (the first four are BatchArgs::dev_counts[0..3]).
 struct DevPlanHdr {
     uint32_t n_first, n_scan, n_small2, n_fill, n_hist, n_small1;
     uint32_t n_hist_class[kHistClasses];   // dev_counts[6..8]
-    uint32_t pad[55];
+    uint32_t n_scan_class[2];              // dev_counts[9..10]
+    uint32_t n_fill_class[2];              // dev_counts[11..12]
+    uint32_t pad[51];
+};
+
+// Bounds of the lists (each list of a kind has the kind's bound).
+struct DevListBounds {
+    uint64_t hist, first, scan, small2, fill;  // first = 3 * hist + (in-CTA segments: S)
 };
 
 // Workspace layout of the device-planned sort (32-bit word offsets).  Every
@@ -182,21 +192,32 @@ struct DevPlanHdr {
 struct DevLayout {
     size_t ctl, hdr, segctl, segs, look, items, start, slots, slot_words, total_words;
     size_t slot_state, slot_run_end, slot_run_val;  // offsets inside a slot
-    uint64_t hist_bound;   // bound of each histogram list (all histogram items)
-    uint64_t first_bound, scan_bound, small2_bound, fill_bound, item_bound;
+    DevListBounds lb;
+    uint64_t item_bound;
     uint32_t look_blocks;  // planner CTAs (1024 segments each)
 };
 
 // Position in the items array of list `list`'s element k (its base is the
 // bound-sum of the lists before it).
-__host__ __device__ inline uint64_t devplan_pos(const DevLayout &L, uint32_t list, uint64_t k) {
-    if (list < kHistClasses) return list * L.hist_bound + k;
+__host__ __device__ inline uint64_t devplan_pos(const DevListBounds &b, uint32_t list, uint64_t k) {
+    if (list < kHistClasses) return list * b.hist + k;
     switch (list) {
-        case kListSmall1: return kHistClasses * L.hist_bound + k;
-        case kListScan: return L.first_bound + k;
-        case kListSmall2: return L.first_bound + L.scan_bound + k;
-        default: return L.first_bound + L.scan_bound + L.small2_bound + k;
+        case kListSmall1: return kHistClasses * b.hist + k;
+        case kListScan0: return b.first + k;
+        case kListScan1: return b.first + b.scan + k;
+        case kListSmall2: return b.first + 2 * b.scan + k;
+        case kListFill0: return b.first + 2 * b.scan + b.small2 + k;
+        default: return b.first + 2 * b.scan + b.small2 + b.fill + k;
     }
+}
+
+// The h-th item over `nl` consecutive lists (first list `list0`, lengths n):
+// the lists taken one after another.
+__host__ __device__ inline uint64_t devplan_chain_pos(const DevListBounds &b, uint32_t list0, const uint32_t *n,
+                                                      uint32_t nl, uint64_t h) {
+    uint32_t c = 0;
+    while (c + 1 < nl && h >= n[c]) h -= n[c++];
+    return devplan_pos(b, list0 + c, h);
 }
 
 // The first launch's k-th ticket (k < nh + ns, nh = the histogram lists'
@@ -206,20 +227,25 @@ __host__ __device__ inline uint64_t devplan_pos(const DevLayout &L, uint32_t lis
 // (histograms) and writes (in-CTA sorts) overlap throughout.  Returns the
 // items-array position.
 __host__ __device__ inline uint64_t devplan_first_pos(uint64_t k, const uint32_t *nc, uint64_t ns,
-                                                      uint64_t hist_bound) {
+                                                      const DevListBounds &b) {
     const uint64_t nh = (uint64_t)nc[0] + nc[1] + nc[2], T = nh + ns;
     uint64_t h = k;
     if (ns > 0) {
         const uint64_t j = (k * ns + T - 1) / T;  // in-CTA slots before ticket k: ceil(k * ns / T)
-        if (j < ns && j * T / ns == k) return kHistClasses * hist_bound + j;  // list kListSmall1
+        if (j < ns && j * T / ns == k) return devplan_pos(b, kListSmall1, j);
         h = k - j;
     }
-    uint32_t c = 0;
-    while (c + 1 < kHistClasses && h >= nc[c]) h -= nc[c++];
-    return c * hist_bound + h;  // list c
+    return devplan_chain_pos(b, kListHist0, nc, kHistClasses, h);
 }
 // 0, or RTCDF_ERR_RANGE / RTCDF_ERR_INVALID_ARG for bounds out of range.
 int devplan_layout(const DevBounds &b, const BatchTuning &t, DevLayout *L);
+
+// List (0 or 1 of its kind) of an output item of `len` positions.
+__host__ __device__ inline uint32_t devplan_fill_class(uint64_t len, const BatchSeg &g) {
+    const uint32_t d = g.R < g.n ? g.R : g.n;  // min(R, n)
+    // len * (1/4 + d / n) >= fill_chunk / 2, in integers
+    return (uint64_t)len * ((uint64_t)g.n + 4ull * d) >= 2ull * g.fill_chunk * g.n ? 0u : 1u;
+}
 
 // Size class of a histogram item of `keys` keys.
 __host__ __device__ inline uint32_t devplan_hist_class(uint64_t keys, uint64_t hist_chunk) {
@@ -255,19 +281,24 @@ __host__ __device__ inline bool devplan_segment(int64_t o0, int64_t o1, int64_t 
     g->scan_chunks = (g->R + kBatchScanChunk - 1) / kBatchScanChunk;
     g->fill_chunk = t.fill_chunk;
     g->fill_items = (uint32_t)((n + t.fill_chunk - 1) / t.fill_chunk);
-    // Whole chunks are class 0; the last chunk, when shorter, goes by its keys.
+    // Whole histogram chunks are class 0; the last chunk, when shorter, goes
+    // by its keys.  Output items likewise: the whole ones share a class, the
+    // last one goes by its length.
     const uint64_t whole = n / t.hist_chunk, rest = n - whole * t.hist_chunk;
     c->v[kListHist0] = (uint32_t)(whole * g->m);
     if (rest) c->v[devplan_hist_class(rest, t.hist_chunk)] += g->m;
-    c->v[kListScan] = g->scan_chunks;
-    c->v[kListFill] = g->fill_items;
+    c->v[g->scan_chunks >= kLongChain ? kListScan0 : kListScan1] = g->scan_chunks;
+    const uint64_t fwhole = n / t.fill_chunk, frest = n - fwhole * t.fill_chunk;
+    c->v[kListFill0 + devplan_fill_class(t.fill_chunk, *g)] = (uint32_t)fwhole;
+    if (frest) c->v[kListFill0 + devplan_fill_class(frest, *g)] += 1;
     return true;
 }
 
 // The k-th item of list `list` that belongs to segment s (k counted within the
 // segment): histogram items chunk-major over tiles (class 0: the whole chunks,
 // then the last chunk if it is in that class; classes 1 and 2: the last
-// chunk), scan chunks and output items ascending.
+// chunk), scan chunks ascending, output items ascending (the whole ones in
+// their class, then the last one in its class).
 __host__ __device__ inline BatchItem devplan_item(uint32_t list, uint32_t s, uint32_t k, const BatchSeg &g,
                                                   const BatchTuning &t) {
     BatchItem it{};
@@ -282,16 +313,22 @@ __host__ __device__ inline BatchItem devplan_item(uint32_t list, uint32_t s, uin
         return it;
     }
     switch (list) {
-        case kListScan:
+        case kListScan0:
+        case kListScan1:
             it.kind = kItemScan;
             it.a = k;
             break;
-        case kListFill:
+        case kListFill0:
+        case kListFill1: {
+            const uint32_t fwhole = g.n / g.fill_chunk;
+            const uint32_t in_list = devplan_fill_class(g.fill_chunk, g) == list - kListFill0 ? fwhole : 0u;
+            const uint32_t f = k < in_list ? k : fwhole;  // else the last (shorter) item
             it.kind = kItemFill;
-            it.a = (uint64_t)k * g.fill_chunk;
-            it.b = ((uint64_t)k + 1) * g.fill_chunk < g.n ? ((uint64_t)k + 1) * g.fill_chunk : g.n;
-            it.aux = k;
+            it.a = (uint64_t)f * g.fill_chunk;
+            it.b = ((uint64_t)f + 1) * g.fill_chunk < g.n ? ((uint64_t)f + 1) * g.fill_chunk : g.n;
+            it.aux = f;
             break;
+        }
         default:
             it.kind = kItemSmall;
             break;

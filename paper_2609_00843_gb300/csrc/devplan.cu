@@ -176,7 +176,9 @@ __global__ void __launch_bounds__(1024) devplan_kernel(DevPlanArgs p) {
             g.state_off = slot + p.L.slot_state;
             g.run_end_off = slot + p.L.slot_run_end;
             g.run_val_off = slot + p.L.slot_run_val;
-            g.start_run_off = p.L.start + s_base[kListFill] + s_ex[kListFill][tid];
+            // the segment's output items, both lists: consecutive start-run slots
+            g.start_run_off = p.L.start + s_base[kListFill0] + s_ex[kListFill0][tid] + s_base[kListFill1] +
+                              s_ex[kListFill1][tid];
         }
         segs[s] = g;
     }
@@ -193,7 +195,7 @@ __global__ void __launch_bounds__(1024) devplan_kernel(DevPlanArgs p) {
                 else hi = mid;
             }
             const uint32_t sg = blk * 1024 + lo;
-            items[devplan_pos(p.L, f, (uint64_t)s_base[f] + k)] = devplan_item(f, sg, k - s_ex[f][lo], segs[sg], p.t);
+            items[devplan_pos(p.L.lb, f, (uint64_t)s_base[f] + k)] = devplan_item(f, sg, k - s_ex[f][lo], segs[sg], p.t);
         }
     }
     if (blk == p.L.look_blocks - 1 && tid == 0) {
@@ -201,18 +203,23 @@ __global__ void __launch_bounds__(1024) devplan_kernel(DevPlanArgs p) {
         for (int i = 0; i < kLookCounts; i++) t[i] = s_base[i] + s_tot[i];
         DevPlanHdr *h = reinterpret_cast<DevPlanHdr *>(p.ws + p.L.hdr);
         const uint64_t nh = (uint64_t)t[kListHist0] + t[kListHist1] + t[kListHist2];
+        const uint64_t ns = (uint64_t)t[kListScan0] + t[kListScan1], nf = (uint64_t)t[kListFill0] + t[kListFill1];
         // The bounds hold by construction; checked anyway, so that a list
         // never outgrows its region.
-        bool bad = t[kNumLists] > 0 || nh > p.L.hist_bound || t[kListSmall1] > p.b.S ||
-                   t[kListScan] > p.L.scan_bound || t[kListSmall2] > p.L.small2_bound ||
-                   t[kListFill] > p.L.fill_bound;
+        const DevListBounds &lb = p.L.lb;
+        bool bad = t[kNumLists] > 0 || nh > lb.hist || t[kListSmall1] > p.b.S || ns > lb.scan ||
+                   t[kListSmall2] > lb.small2 || nf > lb.fill;
         h->n_hist = bad ? 0 : (uint32_t)nh;
         h->n_small1 = bad ? 0 : t[kListSmall1];
         h->n_first = bad ? 0 : (uint32_t)nh + t[kListSmall1];
-        h->n_scan = bad ? 0 : t[kListScan];
+        h->n_scan = bad ? 0 : (uint32_t)ns;
         h->n_small2 = bad ? 0 : t[kListSmall2];
-        h->n_fill = bad ? 0 : t[kListFill];
-        for (uint32_t c = 0; c < kHistClasses; c++) h->n_hist_class[c] = bad ? 0 : t[c];
+        h->n_fill = bad ? 0 : (uint32_t)nf;
+        for (uint32_t c = 0; c < kHistClasses; c++) h->n_hist_class[c] = bad ? 0 : t[kListHist0 + c];
+        for (uint32_t c = 0; c < 2; c++) {
+            h->n_scan_class[c] = bad ? 0 : t[kListScan0 + c];
+            h->n_fill_class[c] = bad ? 0 : t[kListFill0 + c];
+        }
         if (bad) atomicOr(&ctl->status, kDevBadSegment);
     }
 }
@@ -270,12 +277,13 @@ int devplan_layout(const DevBounds &b, const BatchTuning &t, DevLayout *L) {
     const uint64_t S = b.S, N = b.max_total_keys;
     const uint64_t cpr = (b.max_R + kBatchScanChunk - 1) / kBatchScanChunk;  // scan chunks per segment
     const uint64_t m_max = (b.max_R + kBatchTileMax - 1) / kBatchTileMax;
-    L->hist_bound = (N / t.hist_chunk + S) * m_max;
-    L->first_bound = kHistClasses * L->hist_bound + S;
-    L->scan_bound = S * cpr;
-    L->small2_bound = S;
-    L->fill_bound = N / t.fill_chunk + S;
-    L->item_bound = L->first_bound + L->scan_bound + L->small2_bound + L->fill_bound;
+    DevListBounds &lb = L->lb;
+    lb.hist = (N / t.hist_chunk + S) * m_max;
+    lb.first = kHistClasses * lb.hist + S;
+    lb.scan = S * cpr;
+    lb.small2 = S;
+    lb.fill = N / t.fill_chunk + S;
+    L->item_bound = lb.first + 2 * lb.scan + lb.small2 + 2 * lb.fill;
     size_t w = 0;
     L->ctl = w;      w += 64;
     L->hdr = w;      w += 64;
@@ -284,7 +292,7 @@ int devplan_layout(const DevBounds &b, const BatchTuning &t, DevLayout *L) {
     L->look_blocks = (uint32_t)((S + 1023) / 1024);
     L->look = w;     w += align64((uint64_t)L->look_blocks * kLookWords);
     L->items = w;    w += align64(L->item_bound * sizeof(BatchItem) / 4);
-    L->start = w;    w += align64(L->fill_bound);
+    L->start = w;    w += align64(lb.fill);
     L->slots = w;
     L->slot_state = align64(cpr * kBatchScanChunk);
     L->slot_run_end = L->slot_state + align64(2 * cpr);
@@ -315,21 +323,25 @@ int devplan_host(const int64_t *offs, const int64_t *mn, const int64_t *mx, cons
             g.state_off = slot + L.slot_state;
             g.run_end_off = slot + L.slot_run_end;
             g.run_val_off = slot + L.slot_run_val;
-            g.start_run_off = L.start + run.v[kListFill];
+            g.start_run_off = L.start + run.v[kListFill0] + run.v[kListFill1];
         }
         (*segs)[s] = g;
         for (uint32_t f = 0; f < kNumLists; f++) run.v[f] += c.v[f];
     }
     (*pfx)[S] = run;
     hdr->n_hist = run.v[kListHist0] + run.v[kListHist1] + run.v[kListHist2];
-    for (uint32_t c = 0; c < kHistClasses; c++) hdr->n_hist_class[c] = run.v[c];
+    for (uint32_t c = 0; c < kHistClasses; c++) hdr->n_hist_class[c] = run.v[kListHist0 + c];
+    for (uint32_t c = 0; c < 2; c++) {
+        hdr->n_scan_class[c] = run.v[kListScan0 + c];
+        hdr->n_fill_class[c] = run.v[kListFill0 + c];
+    }
     hdr->n_small1 = run.v[kListSmall1];
     hdr->n_first = hdr->n_hist + hdr->n_small1;
-    hdr->n_scan = run.v[kListScan];
+    hdr->n_scan = run.v[kListScan0] + run.v[kListScan1];
     hdr->n_small2 = run.v[kListSmall2];
-    hdr->n_fill = run.v[kListFill];
-    if (hdr->n_hist > L.hist_bound || hdr->n_small1 > S || hdr->n_scan > L.scan_bound ||
-        hdr->n_small2 > L.small2_bound || hdr->n_fill > L.fill_bound)
+    hdr->n_fill = run.v[kListFill0] + run.v[kListFill1];
+    if (hdr->n_hist > L.lb.hist || hdr->n_small1 > S || hdr->n_scan > L.lb.scan || hdr->n_small2 > L.lb.small2 ||
+        hdr->n_fill > L.lb.fill)
         return RTCDF_ERR_INVALID_ARG;
     // The items at the positions the planner writes them: each list in
     // segment order from its own base (devplan_pos); unused positions stay
@@ -338,7 +350,7 @@ int devplan_host(const int64_t *offs, const int64_t *mn, const int64_t *mx, cons
     for (uint32_t list = 0; list < kNumLists; list++)
         for (uint32_t s = 0; s < S; s++)
             for (uint32_t k = (*pfx)[s].v[list]; k < (*pfx)[s + 1].v[list]; k++)
-                (*items)[devplan_pos(L, list, k)] = devplan_item(list, s, k - (*pfx)[s].v[list], (*segs)[s], t);
+                (*items)[devplan_pos(L.lb, list, k)] = devplan_item(list, s, k - (*pfx)[s].v[list], (*segs)[s], t);
     return 0;
 }
 
@@ -411,26 +423,28 @@ rtcdf_status rtcdf_sort_batched_device_ws(const int32_t *in, int32_t *out, const
     a.out = out;
     a.segs = reinterpret_cast<const BatchSeg *>(ws + L.segs);
     a.items = reinterpret_cast<const BatchItem *>(ws + L.items);
-    a.n_first = (uint32_t)std::min<uint64_t>(L.first_bound, UINT32_MAX);
-    a.n_scan = (uint32_t)std::min<uint64_t>(L.scan_bound, UINT32_MAX);
-    a.n_small2 = (uint32_t)std::min<uint64_t>(L.small2_bound, UINT32_MAX);
-    a.n_fill = (uint32_t)std::min<uint64_t>(L.fill_bound, UINT32_MAX);
+    // (the n_* of a device-built plan are unused: the lengths are on the
+    // device, the positions come from dev_bounds)
+    a.n_first = a.n_scan = a.n_small2 = a.n_fill = 0;
     a.num_segs = b.S;
     a.ws_u32 = ws;
     a.ctl = reinterpret_cast<BatchCtl *>(ws + L.ctl);
     a.seg_ctl = reinterpret_cast<BatchSegCtl *>(ws + L.segctl);
     a.dev_counts = ws + L.hdr;  // n_first, n_scan, n_small2, n_fill, n_hist, n_small1, n_hist_class[3]
-    a.hist_bound = L.hist_bound;
+    a.dev_bounds[0] = L.lb.hist;
+    a.dev_bounds[1] = L.lb.first;
+    a.dev_bounds[2] = L.lb.scan;
+    a.dev_bounds[3] = L.lb.small2;
+    a.dev_bounds[4] = L.lb.fill;
     a.plan_look = ws + L.look;
     a.plan_look_words = L.look_blocks * kLookWords;
     // The first and scan launches: two (1024 threads) and six (256 threads)
     // resident CTAs per SM taking items by ticket; the output launch: one CTA
     // per item of the list's bound.
-    if (L.scan_bound + L.small2_bound > 0x7fffffffull || L.fill_bound > 0x7fffffffull)
-        return RTCDF_ERR_INVALID_ARG;
-    const uint32_t first = (uint32_t)std::min<uint64_t>(L.first_bound, 2ull * sms);
-    const uint32_t scan = (uint32_t)std::min<uint64_t>(L.scan_bound + L.small2_bound, 6ull * sms);
-    const uint32_t fill = (uint32_t)L.fill_bound;
+    if (L.lb.fill > 0x7fffffffull) return RTCDF_ERR_INVALID_ARG;
+    const uint32_t first = (uint32_t)std::min<uint64_t>(L.lb.first, 2ull * sms);
+    const uint32_t scan = (uint32_t)std::min<uint64_t>(L.lb.scan + L.lb.small2, 6ull * sms);
+    const uint32_t fill = (uint32_t)L.lb.fill;
     if (launch_batched_dev(a, std::max(first, 1u), std::max(scan, 1u), std::max(fill, 1u), s) != cudaSuccess)
         return RTCDF_ERR_CUDA;
     return RTCDF_OK;

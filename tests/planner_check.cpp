@@ -171,30 +171,36 @@ static int check_dev(const std::vector<SegSpec> &spec, const BatchTuning &tun, u
     if (hdr.n_hist != (uint64_t)hdr.n_hist_class[0] + hdr.n_hist_class[1] + hdr.n_hist_class[2])
         return fail("dev histogram lists", hdr.n_hist, hdr.n_hist_class[0]);
     if (items.size() != L.item_bound) return fail("dev items array", (long)items.size(), (long)L.item_bound);
-    if (L.first_bound != kHistClasses * L.hist_bound + L.small2_bound) return fail("dev first bound", 0, 0);
-    if (hdr.n_hist > L.hist_bound || hdr.n_small1 > S || hdr.n_scan > L.scan_bound ||
-        hdr.n_small2 > L.small2_bound || hdr.n_fill > L.fill_bound)
+    const DevListBounds &lb = L.lb;
+    if (lb.first != kHistClasses * lb.hist + lb.small2) return fail("dev first bound", 0, 0);
+    if (hdr.n_hist > lb.hist || hdr.n_small1 > S || hdr.n_scan > lb.scan || hdr.n_small2 > lb.small2 ||
+        hdr.n_fill > lb.fill)
         return fail("dev bounds", hdr.n_first, hdr.n_scan);
+    if (hdr.n_scan != hdr.n_scan_class[0] + hdr.n_scan_class[1] || hdr.n_fill != hdr.n_fill_class[0] + hdr.n_fill_class[1])
+        return fail("dev class lengths", hdr.n_scan, hdr.n_fill);
     // Each list sits at its fixed base (the bounds of the lists before it);
     // the positions past a list's length stay unused.
-    const uint64_t list_base[kNumLists] = {0, L.hist_bound, 2 * L.hist_bound, 3 * L.hist_bound, L.first_bound,
-                                           L.first_bound + L.scan_bound,
-                                           L.first_bound + L.scan_bound + L.small2_bound};
-    const uint64_t list_bound[kNumLists] = {L.hist_bound, L.hist_bound, L.hist_bound, S, L.scan_bound,
-                                            L.small2_bound, L.fill_bound};
+    const uint64_t fb = lb.first + 2 * lb.scan + lb.small2;
+    const uint64_t list_base[kNumLists] = {0, lb.hist, 2 * lb.hist, 3 * lb.hist, lb.first, lb.first + lb.scan,
+                                           lb.first + 2 * lb.scan, fb, fb + lb.fill};
+    const uint64_t list_bound[kNumLists] = {lb.hist, lb.hist, lb.hist, S, lb.scan, lb.scan, lb.small2, lb.fill, lb.fill};
     const uint32_t list_len[kNumLists] = {hdr.n_hist_class[0], hdr.n_hist_class[1], hdr.n_hist_class[2],
-                                          hdr.n_small1, hdr.n_scan, hdr.n_small2, hdr.n_fill};
-    const uint32_t list_kind[kNumLists] = {kItemHist, kItemHist, kItemHist, kItemSmall, kItemScan, kItemSmall,
-                                           kItemFill};
+                                          hdr.n_small1, hdr.n_scan_class[0], hdr.n_scan_class[1], hdr.n_small2,
+                                          hdr.n_fill_class[0], hdr.n_fill_class[1]};
+    const uint32_t list_kind[kNumLists] = {kItemHist, kItemHist, kItemHist, kItemSmall, kItemScan, kItemScan,
+                                           kItemSmall, kItemFill, kItemFill};
+    if (fb + 2 * lb.fill != L.item_bound) return fail("dev item bound", 0, 0);
     for (uint32_t f = 0; f < kNumLists; f++)
-        if (devplan_pos(L, f, 0) != list_base[f]) return fail("dev list base", f, (long)devplan_pos(L, f, 0));
-    std::vector<uint32_t> small_seen(S, 0), next_chunk(S, 0), next_fill(S, 0);
+        if (devplan_pos(lb, f, 0) != list_base[f]) return fail("dev list base", f, (long)devplan_pos(lb, f, 0));
+    std::vector<uint32_t> small_seen(S, 0), next_chunk(S, 0);
+    std::vector<std::vector<uint32_t>> fill_aux(S);
     std::vector<std::vector<std::pair<uint64_t, uint64_t>>> hist_rng(S);
     for (uint32_t f = 0; f < kNumLists; f++) {
         for (uint64_t k = list_len[f]; k < list_bound[f]; k++) {
             const BatchItem &u = items[list_base[f] + k];
             if (u.kind || u.seg || u.a || u.b || u.tile || u.aux) return fail("dev unused position", f, (long)k);
         }
+        std::vector<int64_t> last_aux(S, -1);
         for (uint64_t k = 0; k < list_len[f]; k++) {
             const size_t q = list_base[f] + k;
             const BatchItem &it = items[q];
@@ -214,14 +220,21 @@ static int check_dev(const std::vector<SegSpec> &spec, const BatchTuning &tun, u
                     small_seen[it.seg]++;
                     break;
                 case kItemScan:
+                    // long chains in the first list; a segment's chunks ascend
+                    if ((f == kListScan0) != (g.scan_chunks >= kLongChain)) return fail("dev scan class", (long)q, f);
                     if (it.a != next_chunk[it.seg]) return fail("dev scan chunk order", (long)q, (long)it.a);
                     next_chunk[it.seg]++;
                     break;
                 case kItemFill:
-                    if (it.aux != next_fill[it.seg] || it.a != (uint64_t)it.aux * g.fill_chunk ||
+                    if (it.aux >= g.fill_items || it.a != (uint64_t)it.aux * g.fill_chunk ||
                         it.b != std::min<uint64_t>(g.n, (uint64_t)(it.aux + 1) * g.fill_chunk))
                         return fail("dev fill item", (long)q, it.aux);
-                    next_fill[it.seg]++;
+                    // each output list holds the items of its cost class; a
+                    // segment's items ascend within a list
+                    if (kListFill0 + devplan_fill_class(it.b - it.a, g) != f) return fail("dev fill class", (long)q, f);
+                    if ((int64_t)it.aux <= last_aux[it.seg]) return fail("dev fill order", (long)q, it.aux);
+                    last_aux[it.seg] = it.aux;
+                    fill_aux[it.seg].push_back(it.aux);
                     break;
             }
         }
@@ -233,14 +246,14 @@ static int check_dev(const std::vector<SegSpec> &spec, const BatchTuning &tun, u
     {
         const uint64_t nh = hdr.n_hist, ns = hdr.n_small1, T = nh + ns;
         uint64_t next_h = 0, next_s = 0, last_s = 0;
-        const uint64_t hb = L.hist_bound;
+        const uint64_t hb = lb.hist;
         auto hist_pos = [&](uint64_t h) {  // the h-th histogram item over the three lists
             uint32_t c = 0;
             while (c + 1 < kHistClasses && h >= hdr.n_hist_class[c]) h -= hdr.n_hist_class[c++];
             return c * hb + h;
         };
         for (uint64_t k = 0; k < T; k++) {
-            const uint64_t q = devplan_first_pos(k, hdr.n_hist_class, ns, hb);
+            const uint64_t q = devplan_first_pos(k, hdr.n_hist_class, ns, lb);
             if (q < kHistClasses * hb) {
                 if (q != hist_pos(next_h++)) return fail("dev first ticket (histogram)", (long)k, (long)q);
             } else {
@@ -257,7 +270,7 @@ static int check_dev(const std::vector<SegSpec> &spec, const BatchTuning &tun, u
         if (g.n != spec[s].n || g.off != spec[s].in_off || (int64_t)g.minVal != spec[s].minVal)
             return fail("dev descriptor", s, g.n);
         if (spec[s].n == 0) {
-            if (small_seen[s] || next_chunk[s] || next_fill[s] || !hist_rng[s].empty())
+            if (small_seen[s] || next_chunk[s] || !fill_aux[s].empty() || !hist_rng[s].empty())
                 return fail("dev empty segment has items", s, 0);
             continue;
         }
@@ -267,8 +280,15 @@ static int check_dev(const std::vector<SegSpec> &spec, const BatchTuning &tun, u
         }
         if (small_seen[s]) return fail("dev large segment in one CTA", s, 0);
         if (next_chunk[s] != g.scan_chunks) return fail("dev scan chunks", s, next_chunk[s]);
-        if (next_fill[s] != g.fill_items || (uint64_t)g.fill_items * g.fill_chunk < g.n)
-            return fail("dev fill coverage", s, next_fill[s]);
+        {
+            // every output item of the segment exactly once, over both lists
+            std::vector<uint32_t> &v = fill_aux[s];
+            std::sort(v.begin(), v.end());
+            for (uint32_t i = 0; i < v.size(); i++)
+                if (v[i] != i) return fail("dev fill items", s, v[i]);
+            if (v.size() != g.fill_items || (uint64_t)g.fill_items * g.fill_chunk < g.n)
+                return fail("dev fill coverage", s, (long)v.size());
+        }
         std::vector<std::vector<std::pair<uint64_t, uint64_t>>> per_tile(g.m);
         for (auto &r : hist_rng[s]) per_tile[r.first % 1024].push_back({r.first / 1024, r.second});
         for (uint32_t t = 0; t < g.m; t++) {
@@ -289,9 +309,18 @@ static int check_dev(const std::vector<SegSpec> &spec, const BatchTuning &tun, u
         if (g.run_end_off + g.R > g.run_val_off || g.run_val_off + g.R > slot + L.slot_words)
             return fail("dev run tables", s, 0);
         if (g.state_off % 2 || g.hist_off % 4) return fail("dev alignment", s, 0);
-        if (g.start_run_off < L.start || g.start_run_off + g.fill_items > L.start + L.fill_bound)
+        if (g.start_run_off < L.start || g.start_run_off + g.fill_items > L.start + lb.fill)
             return fail("dev start runs", s, (long)g.start_run_off);
         if (slot + L.slot_words > L.total_words) return fail("dev workspace size", s, 0);
+    }
+    {
+        // the segments' start-run slots do not overlap
+        std::vector<std::pair<size_t, size_t>> rs;
+        for (uint32_t s = 0; s < S; s++)
+            if (segs[s].m > 0) rs.push_back({segs[s].start_run_off, segs[s].start_run_off + segs[s].fill_items});
+        std::sort(rs.begin(), rs.end());
+        for (size_t i = 1; i < rs.size(); i++)
+            if (rs[i].first < rs[i - 1].second) return fail("dev start runs overlap", (long)i, (long)rs[i].first);
     }
     return 0;
 }
@@ -317,12 +346,13 @@ static int emit(const char *path) {
     std::vector<BatchItem> items;
     const int rc = devplan_host(offs.data(), mn.data(), mx.data(), b, tun, L, &segs, &pfx, &hdr, &items);
     std::printf("layout %zu %zu %zu %zu %zu %zu\n", L.ctl, L.hdr, L.segs, L.look, L.items, L.total_words);
-    std::printf("bounds %llu %llu %llu %llu %llu\n", (unsigned long long)L.hist_bound,
-                (unsigned long long)L.first_bound, (unsigned long long)L.scan_bound,
-                (unsigned long long)L.small2_bound, (unsigned long long)L.fill_bound);
+    std::printf("bounds %llu %llu %llu %llu %llu\n", (unsigned long long)L.lb.hist,
+                (unsigned long long)L.lb.first, (unsigned long long)L.lb.scan,
+                (unsigned long long)L.lb.small2, (unsigned long long)L.lb.fill);
     std::printf("rc %d\n", rc);
-    std::printf("hdr %u %u %u %u %u %u %u %u %u\n", hdr.n_first, hdr.n_scan, hdr.n_small2, hdr.n_fill, hdr.n_hist,
-                hdr.n_small1, hdr.n_hist_class[0], hdr.n_hist_class[1], hdr.n_hist_class[2]);
+    std::printf("hdr %u %u %u %u %u %u %u %u %u %u %u %u %u\n", hdr.n_first, hdr.n_scan, hdr.n_small2, hdr.n_fill,
+                hdr.n_hist, hdr.n_small1, hdr.n_hist_class[0], hdr.n_hist_class[1], hdr.n_hist_class[2],
+                hdr.n_scan_class[0], hdr.n_scan_class[1], hdr.n_fill_class[0], hdr.n_fill_class[1]);
     for (const BatchSeg &g : segs)
         std::printf("seg %llu %u %u %d %u %u %u %u %u %u %u %llu %llu %llu %llu %llu\n",
                     (unsigned long long)g.off, g.n, g.R, g.minVal, g.T, g.m, g.hist_items, g.fill_items,

@@ -191,7 +191,7 @@ def test_gpu_planner_writes_what_the_host_emulation_computes(emitter, tmp_path):
     the workspace, equal the host emulation of the same rules (planner_check
     --emit) field by field: 2600 segments, so three planner CTAs hand their
     counts on through the lookback, every eleventh segment empty, and items
-    in each of the three histogram lists."""
+    in each of the lists by size."""
     L, mn, R, dist, seeds = gen.batched_segments(gen.derive_seed(32), 2600, n_lo=1, n_hi=1e5, r_hi=2 ** 18)
     L = L.copy()
     L[::11] = 0
@@ -227,7 +227,7 @@ def test_gpu_planner_writes_what_the_host_emulation_computes(emitter, tmp_path):
     check_segments(x, out, offs, mns, mxs)
     w = ws.cpu().numpy().view(np.uint32)
     _, hdr_off, seg_off, look_off, item_off, _ = lay
-    assert w[hdr_off:hdr_off + 9].tolist() == hdr
+    assert w[hdr_off:hdr_off + 13].tolist() == hdr
     # the output launch left the planner's lookback records zeroed for the next run
     assert not w[look_off:look_off + 32 * ((S + 1023) // 1024)].any()
     seg_dt = np.dtype([("off", "<u8"), ("out_off", "<u8"), ("n", "<u4"), ("R", "<u4"), ("minVal", "<i4"),
@@ -247,10 +247,11 @@ def test_gpu_planner_writes_what_the_host_emulation_computes(emitter, tmp_path):
     it = w[item_off:item_off + len(items) * 8].view(item_dt)
     got = np.stack([it[f].astype(np.int64) for f in ("kind", "seg", "a", "b", "tile", "aux")], axis=1)
     # every list at its fixed base, compared up to its length
-    n_first, n_scan, n_small2, n_fill, n_hist, n_small1, nh0, nh1, nh2 = hdr
-    assert n_small1 > 0 and n_small2 > 0 and n_scan > 0 and min(nh0, nh1, nh2) > 0
-    for base, n in ((0, nh0), (hist_b, nh1), (2 * hist_b, nh2), (3 * hist_b, n_small1), (first_b, n_scan),
-                    (first_b + scan_b, n_small2), (first_b + scan_b + small2_b, n_fill)):
+    n_first, n_scan, n_small2, n_fill, n_hist, n_small1, nh0, nh1, nh2, ns0, ns1, nf0, nf1 = hdr
+    assert n_small1 > 0 and n_small2 > 0 and min(nh0, nh1, nh2, ns0, ns1, nf0, nf1) > 0
+    fb = first_b + 2 * scan_b + small2_b
+    for base, n in ((0, nh0), (hist_b, nh1), (2 * hist_b, nh2), (3 * hist_b, n_small1), (first_b, ns0),
+                    (first_b + scan_b, ns1), (first_b + 2 * scan_b, n_small2), (fb, nf0), (fb + fill_b, nf1)):
         np.testing.assert_array_equal(got[base:base + n], items[base:base + n])
 
 
