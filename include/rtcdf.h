@@ -555,10 +555,10 @@ rtcdf_status rtcdf_serve_sequential(const rtcdf_server_config *cfg, const rtcdf_
  * RTCDF_ERR_RANGE.  Nothing is allocated and no allocating routine is called.
  *
  * The first call on a device looks up the array's device address (once per
- * device, on the current device); make that first call before any CUDA graph
- * capture.  All calls on a device share the array and it keeps what the last
- * call left, so each call clears the part that must start at zero; calls that
- * overlap on the GPU (unordered streams) race and must not be issued.  This
+ * device, on the current device).  All calls on a device share the array and
+ * it keeps what the last call left, so each call clears the part that must
+ * start at zero; calls that overlap on the GPU (unordered streams) race and
+ * must not be issued.  This
  * entry point reports no device-detected error: neither a key outside
  * [minVal, maxVal) nor a bounded wait that ran out (which only overlapping
  * calls can cause) reaches the caller, and `out` is then unspecified.  The
