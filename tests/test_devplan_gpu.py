@@ -280,3 +280,64 @@ def test_benchmark_batched_workload_device_planned():
         torch.cuda.synchronize()
         assert rtcdf.rtcdf_batch_status_get(ws.data_ptr(), st.cuda_stream) == (rtcdf.OK, 0)
         check_segments(x, out, offs, mns, mxs)
+
+
+def _device_sort(x, offs, mns, mxs, max_R, ws=None):
+    """One device-planned sort on a caller workspace (a fresh zeroed one by
+    default); returns the output, the workspace and its status."""
+    S, N = len(mns), x.numel()
+    wsb = rtcdf.rtcdf_batch_device_workspace_size(S, N, max_R)
+    if ws is None:
+        ws = torch.zeros(wsb // 4 + 64, dtype=torch.int32, device="cuda")
+    out = torch.full_like(x, 0x7FFFFFFF)
+    s = stream_handle()
+    d_o, d_mn, d_mx = to_dev(offs), to_dev(mns), to_dev(mxs)
+    rc = rtcdf.rtcdf_sort_batched_device_ws(x.data_ptr(), out.data_ptr(), d_o.data_ptr(), d_mn.data_ptr(),
+                                            d_mx.data_ptr(), S, N, max_R, ws.data_ptr(), wsb, s)
+    assert rc == rtcdf.OK, rtcdf.rtcdf_status_str(rc)
+    return out, ws, rtcdf.rtcdf_batch_status_get(ws.data_ptr(), s)
+
+
+@pytest.mark.parametrize("S", [1, 1023, 1024, 1025, 2049])
+def test_segment_counts_around_a_planner_cta(S):
+    """Segment counts at and around the 1024 segments one planner CTA
+    classifies (the lists of later CTAs are placed after the counts they get
+    through the lookback), mixed small, large and empty segments, twice on the
+    same workspace: every segment against the oracle."""
+    L, mn, R, dist, seeds = gen.batched_segments(gen.derive_seed(40, S), S, n_lo=1, n_hi=3e5, r_hi=2 ** 17)
+    L = L.copy()
+    L[::7] = 0
+    x, offs, mns, mxs = make_layout(L, R, mn.astype(np.int64), dist, seeds)
+    out, ws, st = _device_sort(x, offs, mns, mxs, 1 << 17)
+    assert st == (rtcdf.OK, 0)
+    check_segments(x, out, offs, mns, mxs)
+    out2, _, st2 = _device_sort(x, offs, mns, mxs, 1 << 17, ws)
+    assert st2 == (rtcdf.OK, 0)
+    assert torch.equal(out, out2)
+
+
+@pytest.mark.parametrize("case", ["all_empty", "all_small", "one_large", "widest"])
+def test_degenerate_layouts(case):
+    """Layouts where some lists are empty: every segment empty (nothing to do;
+    the keys stay untouched), only in-CTA segments (no histogram, scan or
+    output items), one large segment alone, and one segment of the widest
+    range (2^20 values, 256 scan chunks in one lookback chain)."""
+    if case == "all_empty":
+        L, R = [0] * 300, [5] * 300
+    elif case == "all_small":
+        L, R = [100 + 37 * i for i in range(1500)], [1 + (i * 977) % 50000 for i in range(1500)]
+    elif case == "one_large":
+        L, R = [2_500_000], [70_000]
+    else:
+        L, R = [3_000_000], [1 << 20]
+    S = len(L)
+    mins = [(-1) ** i * (i * 1013) % 100_000 for i in range(S)]
+    x, offs, mns, mxs = make_layout(L, R, mins, [i % 3 for i in range(S)], [gen.derive_seed(41, i) for i in range(S)],
+                                    cap=max(1, sum(L)))
+    max_R = max(R)
+    out, ws, st = _device_sort(x, offs, mns, mxs, max_R)
+    assert st == (rtcdf.OK, 0)
+    if case == "all_empty":
+        assert int(out[0]) == 0x7FFFFFFF
+    else:
+        check_segments(x, out, offs, mns, mxs)
