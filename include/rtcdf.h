@@ -357,7 +357,12 @@ typedef struct {
     int32_t small_scan_max_R; /* in-CTA segments with R up to this are sorted by 256-thread CTAs
                                  of the scan launch, wider ones by 1024-thread CTAs of the first
                                  launch (1 .. 16768; default 16000) */
-    int32_t reserved[4];
+    int32_t small_by_time;    /* 0 or 1 (default): a segment the two limits above would sort
+                                 inside one CTA of the scan launch is split into work items
+                                 instead when its estimated in-CTA sort time exceeds the scan
+                                 launch's (only when the plan has large segments); -1: the
+                                 limits alone decide */
+    int32_t reserved[3];
 } rtcdf_batch_params;
 
 /* rtcdf_batch_plan_create with explicit work-item sizes (`params` may be NULL). */

@@ -6,6 +6,7 @@
 // and uploaded; running it needs no host work, so it can be captured in a
 // CUDA graph and replayed for new keys with the same segment shapes.
 #include <algorithm>
+#include <cmath>
 #include <cstring>
 #include <vector>
 
@@ -59,6 +60,8 @@ int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P, const BatchTun
     P->ctl_off = w;     w += words_align(sizeof(BatchCtl) / 4);
     P->segctl_off = w;  w += words_align((size_t)S * sizeof(BatchSegCtl) / 4);
     std::vector<uint32_t> large_ids, small_ids;
+    std::vector<uint8_t> in_cta(S, 0);
+    uint64_t chunks = 0;
     for (uint32_t s = 0; s < S; s++) {
         BatchSeg &g = P->segs[s];
         memset(&g, 0, sizeof(g));
@@ -69,7 +72,32 @@ int build_host_plan(const SegSpec *spec, uint32_t S, HostPlan *P, const BatchTun
         g.minVal = (int32_t)spec[s].minVal;
         P->total_keys += g.n;
         if (g.n == 0) continue;
-        if (g.n <= tun.small_max_n && g.R <= kBatchSmallMaxR) {
+        if (g.n <= tun.small_max_n && g.R <= kBatchSmallMaxR) in_cta[s] = 1;
+        else chunks += (g.R + kBatchScanChunk - 1) / kBatchScanChunk;
+    }
+    if (tun.small_by_time && chunks > 0) {
+        // The second launch's in-CTA segments (R <= small_scan_max_R) start
+        // with its scan chunks, and the output launch waits for both: one
+        // whose sort is estimated to outlast the launch (its chunks, in waves
+        // of six per SM, or the in-CTA sorts spread over all six-per-SM
+        // slots) goes the large way instead.  Estimates, measured per item:
+        // a 256-thread in-CTA sort 5 us + 1.05 ns per key + 1.9 ns per value,
+        // a wave of chunks 10 us.  (On 1024 segments of the benchmark's
+        // shapes: 0.336 -> 0.312 ms; on 4096, where the chunks take longer,
+        // none is moved.)
+        auto small_us = [](const BatchSeg &g) { return 5.0 + 1.05e-3 * g.n + 1.9e-3 * g.R; };
+        const double slots = 6.0 * std::max(1u, tun.sms);
+        double small_total = 0;
+        for (uint32_t s = 0; s < S; s++)
+            if (in_cta[s] && P->segs[s].R <= tun.small_scan_max_R) small_total += small_us(P->segs[s]);
+        const double launch_us = std::max(10.0 * (1.0 + std::ceil((double)chunks / slots)), small_total / slots);
+        for (uint32_t s = 0; s < S; s++)
+            if (in_cta[s] && P->segs[s].R <= tun.small_scan_max_R && small_us(P->segs[s]) > launch_us) in_cta[s] = 0;
+    }
+    for (uint32_t s = 0; s < S; s++) {
+        BatchSeg &g = P->segs[s];
+        if (g.n == 0) continue;
+        if (in_cta[s]) {
             small_ids.push_back(s);
             P->small_segs++;
             continue;
@@ -190,12 +218,14 @@ rtcdf_status rtcdf_batch_plan_create_ex(const int64_t *seg_offsets, const int64_
         if (params->hist_chunk < 0 || (params->hist_chunk > 0 && params->hist_chunk < 4096) ||
             params->fill_chunk < 0 || (params->fill_chunk > 0 && params->fill_chunk < 4096) ||
             params->small_max_n < 0 || params->small_max_n > (int32_t)kBatchSmallMaxN ||
-            params->small_scan_max_R < 0 || params->small_scan_max_R > (int32_t)kSmallInScanCapR)
+            params->small_scan_max_R < 0 || params->small_scan_max_R > (int32_t)kSmallInScanCapR ||
+            params->small_by_time < -1 || params->small_by_time > 1)
             return RTCDF_ERR_INVALID_ARG;
         if (params->hist_chunk) tun.hist_chunk = (uint64_t)params->hist_chunk;
         if (params->fill_chunk) tun.fill_chunk = (uint32_t)params->fill_chunk;
         if (params->small_max_n) tun.small_max_n = (uint32_t)params->small_max_n;
         if (params->small_scan_max_R) tun.small_scan_max_R = (uint32_t)params->small_scan_max_R;
+        if (params->small_by_time < 0) tun.small_by_time = 0;
     }
     *plan_out = nullptr;
     if (num_segments > 0 && (!seg_offsets || !seg_minVal || !seg_maxVal)) return RTCDF_ERR_INVALID_ARG;
@@ -212,6 +242,7 @@ rtcdf_status rtcdf_batch_plan_create_ex(const int64_t *seg_offsets, const int64_
     if (cudaGetDevice(&dev) != cudaSuccess) return RTCDF_ERR_CUDA;
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return RTCDF_ERR_CUDA;
+    tun.sms = (uint32_t)sms;
     HostPlan hp;
     const int rc = build_host_plan(spec.data(), S, &hp, tun);
     if (rc) return (rtcdf_status)rc;

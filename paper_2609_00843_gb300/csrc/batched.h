@@ -123,6 +123,8 @@ struct BatchTuning {
     uint32_t fill_chunk = 1u << 16;     // positions per FILL item
     uint32_t small_max_n = kBatchSmallMaxN;
     uint32_t small_scan_max_R = kSmallInScanMaxR;
+    uint32_t small_by_time = 1;         // host plan: in-CTA segments that would outlast the second launch go large
+    uint32_t sms = 152;                 // SMs of the device the plan is for
 };
 
 // 0, or the rtcdf_status for the first segment with a bad length or range

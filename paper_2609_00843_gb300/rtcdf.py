@@ -50,7 +50,7 @@ class Params(ctypes.Structure):
 class BatchParams(ctypes.Structure):
     _fields_ = [("hist_chunk", ctypes.c_int32), ("fill_chunk", ctypes.c_int32),
                 ("small_max_n", ctypes.c_int32), ("small_scan_max_R", ctypes.c_int32),
-                ("reserved", ctypes.c_int32 * 4)]
+                ("small_by_time", ctypes.c_int32), ("reserved", ctypes.c_int32 * 3)]
 
 
 class TuneEntry(ctypes.Structure):

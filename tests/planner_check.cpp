@@ -380,12 +380,13 @@ int main(int argc, char **argv) {
         spec[s] = SegSpec{off, off, n, mn, mn + R};
         off += n;
     }
-    BatchTuning tunings[6];
+    BatchTuning tunings[7];
     tunings[1].hist_chunk = 4096; tunings[1].fill_chunk = 4096; tunings[1].small_max_n = 100;
     tunings[2].hist_chunk = 1ull << 22; tunings[2].fill_chunk = 1u << 20; tunings[2].small_max_n = 1;
     tunings[3].hist_chunk = 5000; tunings[3].fill_chunk = 6000;
     tunings[4].small_scan_max_R = 1;
     tunings[5].small_scan_max_R = kSmallInScanCapR;
+    tunings[6].small_by_time = 0;
     for (auto &t : tunings)
         if (check(spec, t)) return 1;
     // The device planner's rules, with bounds that hold and with one that

@@ -111,7 +111,8 @@ def test_batched_plan_rejects_bad_metadata_on_host():
 
 @pytest.mark.parametrize("field,value", [("hist_chunk", 100), ("hist_chunk", -1), ("fill_chunk", 4095),
                                          ("small_max_n", 65536), ("small_max_n", -2),
-                                         ("small_scan_max_R", 16769), ("small_scan_max_R", -1)])
+                                         ("small_scan_max_R", 16769), ("small_scan_max_R", -1),
+                                         ("small_by_time", 2), ("small_by_time", -2)])
 def test_batched_plan_rejects_bad_work_item_sizes_on_host(field, value):
     import ctypes
     import numpy as np

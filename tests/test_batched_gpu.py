@@ -70,6 +70,29 @@ def test_mixed_small_and_large_segments():
     check_segments(x, out, offs, mn, mx)
 
 
+@pytest.mark.parametrize("by_time", [1, -1])
+def test_long_in_cta_sorts_split_when_they_would_outlast_the_scan_launch(by_time):
+    """A few large segments (so the plan has scan chunks) and narrow-range
+    segments of 65535 keys: with the time rule on, those whose estimated
+    in-CTA sort would outlast the scan launch are split into work items (fewer
+    in-CTA segments), with it off the limits alone keep them in one CTA; the
+    output is the same, every segment against the oracle."""
+    lengths = [300_000, 150_000] + [65_535] * 6 + [2_000] * 20
+    Rs = [5_000, 40_000] + [9_000, 16_000, 300, 12_000, 1, 16_000] + [700] * 20
+    mins = [(-1) ** i * 3_001 * i for i in range(len(lengths))]
+    x, offs, mn, mx = make_segments(lengths, Rs, mins, [i % 3 for i in range(len(lengths))],
+                                    [gen.derive_seed(35, i) for i in range(len(lengths))])
+    out = torch.full_like(x, 0x7FFFFFFF)
+    plan, ws, wsb, rc, bits = run_plan(x, out, offs, mn, mx, rtcdf.BatchParams(small_by_time=by_time))
+    assert (rc, bits) == (rtcdf.OK, 0)
+    small = plan.info()["small_segments"]
+    if by_time < 0:
+        assert small == 26
+    else:
+        assert 20 <= small < 26
+    check_segments(x, out, offs, mn, mx)
+
+
 def test_batched_workload_shapes_sample():
     """512 segments with the batched workload's shapes (lengths log-uniform in
     [1e3, 1e6], R log-uniform in [2^7, 2^16], minVal in [-2^20, 2^20], mixed
