@@ -579,28 +579,46 @@ __global__ void __launch_bounds__(kScanCtaThreads, 6) seg_scan_kernel(BatchArgs 
         }
     };
     if (DEV) {
-        // Device-built lists: a fixed grid whose CTAs take the in-CTA
-        // segments and then the scan chunks by ticket (a grid sized by the
-        // lists' bounds left tens of thousands of CTAs that only exit, about
-        // 0.04 ms, measured).  The planner zeroed the ticket counter.
-        asm volatile("griddepcontrol.launch_dependents;");
-        bool waited = false;
+        // Device-built lists, as for a host plan: the in-CTA segments by CTA
+        // index at the front of the grid, then one chunk per CTA by ticket;
+        // CTAs past the lists exit at once.  The grid is sized by the lists'
+        // bounds but capped (CTAs past the lists cost about half a
+        // microsecond per thousand); when the lists outgrow it, CTA b also
+        // takes in-CTA segments b + grid, b + 2 grid, ... and every CTA then
+        // loops over chunk tickets.  The two forms are separate code: with
+        // the chunk inside the loop (or the in-CTA segments taken by ticket
+        // too) every chunk ran about twice as slow, measured.
+        const uint32_t grid = gridDim.x;
+        if (grid >= n_small2 + n_scan) {
+            if (blockIdx.x >= n_small2 + n_scan) return;
+            if (blockIdx.x < n_small2) {
+                asm volatile("griddepcontrol.launch_dependents;");
+                small_item(blockIdx.x);
+                return;
+            }
+            if (tid == 0) s_ticket = atomicAdd(&a.ctl->scan_ticket, 1u);
+            __syncthreads();
+            const BatchItem it = a.items[devplan_chain_pos(dev_lb(a), kListScan0, a.dev_counts + 9, 2, s_ticket)];
+            const BatchSeg g = a.segs[it.seg];
+            asm volatile("griddepcontrol.wait;" ::: "memory");
+            asm volatile("griddepcontrol.launch_dependents;");
+            const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
+            scan_chunk(a, it, g, s_warp, s_prefix, s_total, s_wait, s_buf, t0);
+            return;
+        }
+        for (uint32_t j = blockIdx.x; j < n_small2; j += grid) {
+            small_item(j);
+            __syncthreads();  // the segment's shared memory is free
+        }
+        asm volatile("griddepcontrol.wait;" ::: "memory");
         for (;;) {
             if (tid == 0) s_ticket = atomicAdd(&a.ctl->scan_ticket, 1u);
             __syncthreads();
             const uint32_t t = s_ticket;
-            __syncthreads();  // every thread has read the ticket (and the previous item's shared memory is free)
-            if (t >= n_small2 + n_scan) break;
-            if (t < n_small2) {
-                small_item(t);
-                continue;
-            }
-            const BatchItem it = a.items[devplan_chain_pos(dev_lb(a), kListScan0, a.dev_counts + 9, 2, t - n_small2)];
+            __syncthreads();  // every thread has read the ticket (and the previous chunk's shared memory is free)
+            if (t >= n_scan) break;
+            const BatchItem it = a.items[devplan_chain_pos(dev_lb(a), kListScan0, a.dev_counts + 9, 2, t)];
             const BatchSeg g = a.segs[it.seg];
-            if (!waited) {
-                asm volatile("griddepcontrol.wait;" ::: "memory");
-                waited = true;
-            }
             const unsigned long long t0 = (a.prof && tid == 0) ? global_ns() : 0ull;
             scan_chunk(a, it, g, s_warp, s_prefix, s_total, s_wait, s_buf, t0);
         }

@@ -14,13 +14,14 @@
 // lists before them), so no CTA needs the totals to place its items; the
 // last CTA writes the lists' lengths.
 // The three launches then run over these lists (seg_*_kernel<true>); their
-// lengths are known only on the device, so the first and scan launches are
-// fixed grids whose CTAs take items by ticket (the first launch: the three
-// histogram lists, largest items first, with the in-CTA segments spread
-// evenly among them; the scan launch: the narrow in-CTA segments, then the
-// chunks), and the output launch has one CTA per item of the list's bound,
-// the CTAs past the list's length exiting at once (about half a microsecond
-// per thousand, measured).
+// lengths are known only on the device, so the launches take items by
+// ticket: the first launch from a fixed grid of two CTAs per SM looping
+// over the three histogram lists (largest items first) with the in-CTA
+// segments spread evenly among them; the scan launch one item per CTA (the
+// narrow in-CTA segments by CTA index, then the chunks by ticket) and the
+// output launch one CTA per item, from grids sized by the lists' bounds, the
+// CTAs past a list's length exiting at once (about half a microsecond per
+// thousand, measured).
 //
 // The workspace is sized from host-known bounds (segment count, total keys,
 // widest range).  Every segment owns a fixed slot for its histogram, lookback
@@ -42,6 +43,10 @@ namespace rtcdf {
 namespace {
 
 size_t align64(uint64_t words) { return (size_t)((words + 63) / 64 * 64); }
+
+// Largest scan-launch grid: its CTAs past the lists only exit, about half a
+// microsecond per thousand (so at most about 35 us of them).
+constexpr uint64_t kScanGridCap = 1u << 16;
 
 struct DevPlanArgs {
     const int64_t *offs, *mn, *mx;
@@ -438,12 +443,13 @@ rtcdf_status rtcdf_sort_batched_device_ws(const int32_t *in, int32_t *out, const
     a.dev_bounds[4] = L.lb.fill;
     a.plan_look = ws + L.look;
     a.plan_look_words = L.look_blocks * kLookWords;
-    // The first and scan launches: two (1024 threads) and six (256 threads)
-    // resident CTAs per SM taking items by ticket; the output launch: one CTA
-    // per item of the list's bound.
+    // The first launch: two resident CTAs per SM taking items by ticket; the
+    // scan launch: one CTA per item of the lists' bounds, at most
+    // kScanGridCap (CTAs loop when the lists are longer); the output launch:
+    // one CTA per item of the list's bound.
     if (L.lb.fill > 0x7fffffffull) return RTCDF_ERR_INVALID_ARG;
     const uint32_t first = (uint32_t)std::min<uint64_t>(L.lb.first, 2ull * sms);
-    const uint32_t scan = (uint32_t)std::min<uint64_t>(L.lb.scan + L.lb.small2, 6ull * sms);
+    const uint32_t scan = (uint32_t)std::min<uint64_t>(L.lb.scan + L.lb.small2, kScanGridCap);
     const uint32_t fill = (uint32_t)L.lb.fill;
     if (launch_batched_dev(a, std::max(first, 1u), std::max(scan, 1u), std::max(fill, 1u), s) != cudaSuccess)
         return RTCDF_ERR_CUDA;

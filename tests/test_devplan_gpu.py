@@ -341,3 +341,31 @@ def test_degenerate_layouts(case):
         assert int(out[0]) == 0x7FFFFFFF
     else:
         check_segments(x, out, offs, mns, mxs)
+
+
+def test_lists_longer_than_the_scan_grid():
+    """More in-CTA segments than the scan launch's capped grid (65536 CTAs):
+    66000 segments of a few keys and 100 of 70000 keys, all within 4096
+    values (a workspace slot per segment is sized by the widest range), so
+    that CTAs take several in-CTA segments each and then loop over the chunk
+    tickets.  Every segment is checked: the large ones and a sample of the
+    small ones against the oracle, all of them as sorted permutations of
+    their keys (one sort by segment and key)."""
+    n_small, n_large = 66_000, 100
+    L = np.concatenate([3 + (np.arange(n_small) * 7919) % 40, np.full(n_large, 70_000)]).astype(np.int64)
+    R = np.concatenate([1 + (np.arange(n_small) * 104729) % 4096, np.full(n_large, 4096)]).astype(np.int64)
+    perm = np.random.default_rng(gen.derive_seed(43)).permutation(len(L))  # large ones spread among the small
+    L, R = L[perm], R[perm]
+    S = len(L)
+    mins = ((np.arange(S) * 7777) % 200_000 - 100_000).astype(np.int64)
+    x, offs, mns, mxs = make_layout(L, R, mins, np.arange(S) % 3, [gen.derive_seed(44, i) for i in range(S)])
+    out, ws, st = _device_sort(x, offs, mns, mxs, 4096)
+    assert st == (rtcdf.OK, 0)
+    a = x.cpu().numpy()
+    b = out.cpu().numpy()
+    seg_of = np.repeat(np.arange(S), L)
+    order = np.lexsort((a, seg_of))
+    np.testing.assert_array_equal(b, a[order])
+    for s in list(np.nonzero(L == 70_000)[0]) + list(range(0, S, 997)):
+        lo, hi = int(offs[s]), int(offs[s + 1])
+        np.testing.assert_array_equal(b[lo:hi], oracle.counting_sort(a[lo:hi], int(mns[s]), int(mxs[s])))
