@@ -340,7 +340,7 @@ typedef struct {
     uint32_t small_segments;   /* sorted inside one CTA */
     uint32_t large_segments;   /* split into work items */
     uint32_t work_items;       /* CTAs over the three launches */
-    uint32_t workers;          /* CTAs resident at once per launch (two per SM) */
+    uint32_t workers;          /* CTAs of the first launch resident at once (one per SM) */
     uint32_t reserved;
     uint64_t total_keys;
     uint64_t workspace_bytes;

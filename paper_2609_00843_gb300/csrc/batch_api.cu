@@ -249,7 +249,7 @@ rtcdf_status rtcdf_batch_plan_create_ex(const int64_t *seg_offsets, const int64_
 
     rtcdf_batch_plan *p = new rtcdf_batch_plan();
     p->device = dev;
-    p->workers = sms * 2;  // resident 1024-thread CTAs per launch
+    p->workers = sms;  // resident 1024-thread CTAs of the first launch (one per SM)
     p->num_segs = S;
     p->num_items = (uint32_t)hp.items.size();
     p->n_first = hp.n_first;

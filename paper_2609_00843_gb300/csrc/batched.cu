@@ -377,8 +377,13 @@ __device__ __forceinline__ void first_item(const BatchArgs &a, uint32_t idx, uin
 // DEV: the lists were built on the device (their lengths are in
 // a.dev_counts) and the grid is a fixed number of CTAs that take items by
 // ticket; otherwise one CTA per item of the host-built plan.
+// One 1024-thread CTA per SM (the registers of a whole SM: 64 per thread):
+// with two per SM (32 registers per thread) the same items ran so much slower
+// that the segmented sort took 1.038 against 0.969 ms (host plan; the device-
+// planned form 1.12 against 1.035 ms), measured.  The shared memory stays at
+// kSegSmemBytes (a larger tile, 57344 bins in 224 KB, made it slower again).
 template <bool DEV>
-__global__ void __launch_bounds__(kSegThreads, 2) seg_first_kernel(BatchArgs a) {
+__global__ void __launch_bounds__(kSegThreads, 1) seg_first_kernel(BatchArgs a) {
     extern __shared__ uint32_t sm[];
     // The scan launch may be scheduled as soon as every CTA here has started;
     // it waits for this grid to finish before reading anything.

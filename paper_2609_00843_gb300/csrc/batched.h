@@ -10,7 +10,7 @@ namespace rtcdf {
 
 // Three launches per plan:
 //   1. histogram items of the large segments and whole in-CTA sorts of the
-//      small ones (1024 threads, 112 KB of shared memory each, two per SM);
+//      small ones (1024 threads, 112 KB of shared memory each, one per SM);
 //   2. local CDFs + offsets: one 256-thread CTA per 4096-bin chunk of a large
 //      segment's histogram, chained within the segment by a decoupled lookback,
 //      plus the in-CTA sorts of the small segments with R <= kSmallInScanMaxR

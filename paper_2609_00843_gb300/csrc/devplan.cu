@@ -15,7 +15,7 @@
 // last CTA writes the lists' lengths.
 // The three launches then run over these lists (seg_*_kernel<true>); their
 // lengths are known only on the device, so the launches take items by
-// ticket: the first launch from a fixed grid of two CTAs per SM looping
+// ticket: the first launch from a fixed grid of one CTA per SM looping
 // over the three histogram lists (largest items first) with the in-CTA
 // segments spread evenly among them; the scan launch one item per CTA (the
 // narrow in-CTA segments by CTA index, then the chunks by ticket) and the
@@ -443,12 +443,12 @@ rtcdf_status rtcdf_sort_batched_device_ws(const int32_t *in, int32_t *out, const
     a.dev_bounds[4] = L.lb.fill;
     a.plan_look = ws + L.look;
     a.plan_look_words = L.look_blocks * kLookWords;
-    // The first launch: two resident CTAs per SM taking items by ticket; the
+    // The first launch: one resident CTA per SM taking items by ticket; the
     // scan launch: one CTA per item of the lists' bounds, at most
     // kScanGridCap (CTAs loop when the lists are longer); the output launch:
     // one CTA per item of the list's bound.
     if (L.lb.fill > 0x7fffffffull) return RTCDF_ERR_INVALID_ARG;
-    const uint32_t first = (uint32_t)std::min<uint64_t>(L.lb.first, 2ull * sms);
+    const uint32_t first = (uint32_t)std::min<uint64_t>(L.lb.first, (uint64_t)sms);
     const uint32_t scan = (uint32_t)std::min<uint64_t>(L.lb.scan + L.lb.small2, kScanGridCap);
     const uint32_t fill = (uint32_t)L.lb.fill;
     if (launch_batched_dev(a, std::max(first, 1u), std::max(scan, 1u), std::max(fill, 1u), s) != cudaSuccess)
