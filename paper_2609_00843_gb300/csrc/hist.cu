@@ -58,10 +58,14 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
 
 // ADAPT (2 to 8 tiles): out-of-tile keys go to a trash word, and the m CTAs
 // that read the same vectors prefetch them into L2 two iterations ahead --
-// unless a sample of the input (one vector per warp) shows one tile holding
-// more than 2/m of the keys without holding nearly all of them: the CTAs of
-// such tiles then run at unequal speeds and the prefetches cost more than
-// they save.  The choice changes only the speed, never the counts.
+// unless the input is long (more than 2^28 keys) and a sample of it (one
+// vector per warp) shows one tile holding more than 2/m of the keys without
+// holding nearly all of them: the CTAs of such tiles then run at unequal
+// speeds, over a long input the heavy tile's CTAs fall so far behind that
+// the lines prefetched for them are gone, and the prefetches cost more than
+// they save (n = 1e9, R = 2^18, normal keys: 3.04 ms with them against 2.93
+// without; n = 1e8: 0.312 against 0.322 ms, measured).  The choice changes
+// only the speed, never the counts.
 template <bool STREAMING, int UNROLL, bool ADAPT>
 __global__ void __launch_bounds__(1024) hist_kernel(HistArgs a) {
     extern __shared__ uint32_t S[];
@@ -103,7 +107,7 @@ __global__ void __launch_bounds__(1024) hist_kernel(HistArgs a) {
             tot += s_tc[i];
             mx = max(mx, s_tc[i]);
         }
-        pf = tot > 0 && (mx * a.m <= 2 * tot || mx * 10 >= 9 * tot);
+        pf = tot > 0 && (a.nvec <= (1ull << 26) || mx * a.m <= 2 * tot || mx * 10 >= 9 * tot);
     }
     uint64_t vb = (uint64_t)q * nt;  // thread 0's vector of the iteration
     for (; v + (UNROLL - 1) * stride < nvec; v += UNROLL * stride, vb += UNROLL * stride) {
