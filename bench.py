@@ -8,7 +8,7 @@ uniform / normal / all-equal shapes of the paper's evaluation.  Inputs are
 generated on the device by the seeded generator and stay resident in HBM;
 each array (400 MB) is larger than L2, so no flush is needed between steps.
 The twelve arrays are independent, so the timed step sorts them on
-``--streams`` streams (default 3, round robin); the same steps on one stream
+``--streams`` streams (default 12, one per array; round robin when fewer); the same steps on one stream
 are reported beside it (``one_stream``), and the per-array figures
 (``per_config``) are single-stream.
 
@@ -725,7 +725,7 @@ def main():
                     help="skip the sharded sort (each array split across the ranks)")
     ap.add_argument("--serve-requests", type=int, default=20000)
     ap.add_argument("--e2e-steps", type=int, default=5)
-    ap.add_argument("--streams", type=int, default=3,
+    ap.add_argument("--streams", type=int, default=12,
                     help="streams the timed step spreads its independent arrays over")
     ap.add_argument("--no-single", action="store_true", help="skip the n=1e6 single-array config")
     ap.add_argument("--no-large", action="store_true", help="skip the n=1e9 configs")
