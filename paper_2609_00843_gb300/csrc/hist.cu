@@ -212,7 +212,9 @@ const void *hist_fn(int variant, int unroll) {
     }
 }
 
-// Eight loads in flight per thread when only one CTA fits on an SM.
+// The deep form (UNROLL = 8) when only one CTA fits on an SM: eight loads in
+// flight per thread in the one-tile and plain forms, a six-deep pipeline in
+// the 2-to-8-tile form.
 int hist_unroll(size_t smem) { return smem > 114 * 1024 ? 8 : 4; }
 
 cudaError_t launch_hist(const HistArgs &a, int threads, size_t smem, bool streaming,
