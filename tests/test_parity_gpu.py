@@ -264,6 +264,30 @@ def test_sparse_wide_ranges():
         assert_matches_oracle(x, gpu_sort(x, -3, -3 + (1 << 22)), -3, -3 + (1 << 22))
 
 
+@pytest.mark.parametrize("tiles", [7, 8, 9])
+def test_built_in_plan_at_the_tile_form_boundary(tiles):
+    """Built-in plan (explicit all-zero parameters: no tuning table) at the
+    ranges where the tile count steps around the boundary between the
+    two-to-eight-tile form (trash word, sampled prefetch, the sample's last
+    tile slot) and the plain predicated form of nine tiles and more: R =
+    tiles x T_max, the largest range with `tiles` tiles of the widest width
+    the device's opt-in shared memory allows, and R + 1, one tile more."""
+    t_max = (torch.cuda.get_device_properties(0).shared_memory_per_block_optin // 4) & ~1023
+    n, mn = 1_000_003, -77
+    for R in (tiles * t_max, tiles * t_max + 1):
+        ws_bytes = rtcdf.rtcdf_workspace_size(R)
+        ws = torch.zeros(ws_bytes // 4 + 64, dtype=torch.int32, device="cuda")
+        for dist in DISTS:
+            x = dev_keys(n, mn, R, dist, gen.derive_seed(18, R, dist))
+            out = torch.empty_like(x)
+            rc = rtcdf.rtcdf_sort_ex(x.data_ptr(), out.data_ptr(), n, mn, mn + R, rtcdf.Params(),
+                                     ws.data_ptr(), ws_bytes, None, stream_handle())
+            assert rc == rtcdf.OK
+            rc, bits = rtcdf.rtcdf_ws_status_get(ws.data_ptr(), stream_handle())
+            assert rc == rtcdf.OK and bits == 0
+            assert_matches_oracle(x, out, mn, mn + R)
+
+
 def test_host_and_device_generators_agree():
     for dist in DISTS:
         for R, mn in ((128, 0), (1 << 14, -1000), (1 << 18, (1 << 31) - (1 << 18)), (3, -(1 << 31))):
